@@ -1,0 +1,230 @@
+"""Plain FP64 CPU oracle: definitions from the paper, written out slowly.
+
+TEST INFRASTRUCTURE ONLY.  Loaded by the tests, the smoke check and the CPU
+baseline of the benchmark; never by the product path.  Shares no code with
+the CUDA library.
+
+Contents (each function cites the passage it follows):
+  * kernel kinds of Table 4b and the pairwise kernel value / matrix / matvec
+    (C, ``gvt_oracle.c``): the explicit O(n * nhat) product, Sec. 4.9 approach 1;
+  * Gaussian base kernel (C), Sec. 5.2 with the squared norm;
+  * explicit operators of Definition 1 (commutation P, unification Q, PQ) and
+    the sampling operator R of Sec. 3, as dense 0/1 matrices;
+  * kernel ridge regression, Eq. (linsystem): dense Cholesky solve and plain CG;
+  * the complete-data closed form through eigendecompositions (Sec. 1).
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against values
+the paper prints, closed forms, invariants or brute force.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+KINDS = ["kronecker", "gaussian", "linear", "poly2d", "cartesian",
+         "symmetric", "antisymmetric", "ranking", "mlpk"]
+HOMOGENEOUS = {"symmetric", "antisymmetric", "ranking", "mlpk"}
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = build_oracle()
+        lib = ctypes.CDLL(path)
+        i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        p = ctypes.c_void_p
+        lib.orc_kernel_value.argtypes = [i32, p, i64, p, i64, i64, i64, i64, i64, p]
+        lib.orc_kernel_value.restype = i32
+        lib.orc_kernel_matrix.argtypes = [i32, p, i64, p, i64, p, p, i64, p, p, i64, p]
+        lib.orc_kernel_matrix.restype = i32
+        lib.orc_pairwise_matvec.argtypes = [i32, p, i64, p, i64, p, p, i64, p, p, i64,
+                                            p, i64, p, i32]
+        lib.orc_pairwise_matvec.restype = i32
+        lib.orc_gaussian_kernel.argtypes = [p, i64, p, i64, i64, dbl, p, i32]
+        lib.orc_gaussian_kernel.restype = i32
+        lib.orc_compensated_sum.argtypes = [p, i64]
+        lib.orc_compensated_sum.restype = dbl
+        lib.orc_num_threads.argtypes = []
+        lib.orc_num_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kind_id(kind):
+    return KINDS.index(kind)
+
+
+def num_threads():
+    """Threads the C oracle uses by default (OpenMP)."""
+    return int(_load().orc_num_threads())
+
+
+def _mats(kind, M, N):
+    M = _f64(M)
+    N = M if (kind in HOMOGENEOUS or N is None) else _f64(N)
+    return M, N
+
+
+def kernel_value(kind, M, N, a, b, c, e):
+    """k((a,b),(c,e)) from Table 4b."""
+    M, N = _mats(kind, M, N)
+    out = np.zeros(1)
+    rc = _load().orc_kernel_value(kind_id(kind), _ptr(M), M.shape[1], _ptr(N), N.shape[1],
+                                  int(a), int(b), int(c), int(e), _ptr(out))
+    assert rc == 0
+    return float(out[0])
+
+
+def kernel_matrix(kind, M, N, d_out, t_out, d_in, t_in):
+    """Explicit block R(dhat,that) K_op R(d,t)^T with entries from Table 4b."""
+    M, N = _mats(kind, M, N)
+    d_out, t_out, d_in, t_in = map(_i32, (d_out, t_out, d_in, t_in))
+    K = np.zeros((len(d_out), len(d_in)))
+    rc = _load().orc_kernel_matrix(kind_id(kind), _ptr(M), M.shape[1], _ptr(N), N.shape[1],
+                                   _ptr(d_out), _ptr(t_out), len(d_out),
+                                   _ptr(d_in), _ptr(t_in), len(d_in), _ptr(K))
+    assert rc == 0
+    return K
+
+
+def pairwise_matvec(kind, M, N, d_out, t_out, d_in, t_in, v, nthreads=0):
+    """u = R(dhat,that) K_op R(d,t)^T v, as the plain double sum (Sec. 4.9, approach 1).
+
+    ``v`` is (n_in,) or (n_in, k); the result has the matching shape.
+    Compensated FP64 sums; O(n_in * n_out * k) kernel evaluations.
+    """
+    M, N = _mats(kind, M, N)
+    d_out, t_out, d_in, t_in = map(_i32, (d_out, t_out, d_in, t_in))
+    v = np.asarray(v, dtype=np.float64)
+    vec = v.ndim == 1
+    V = v.reshape(len(d_in), -1)
+    k = V.shape[1]
+    Vc = np.asfortranarray(V)
+    U = np.zeros((len(d_out), k), order="F")
+    rc = _load().orc_pairwise_matvec(kind_id(kind), _ptr(M), M.shape[1], _ptr(N), N.shape[1],
+                                     _ptr(d_out), _ptr(t_out), len(d_out),
+                                     _ptr(d_in), _ptr(t_in), len(d_in),
+                                     _ptr(Vc), k, _ptr(U), int(nthreads))
+    assert rc == 0
+    U = np.ascontiguousarray(U)
+    return U[:, 0] if vec else U
+
+
+def gaussian_kernel(X, Y=None, gamma=1.0, nthreads=0):
+    """K[a,b] = exp(-gamma ||X_a - Y_b||^2), Sec. 5.2 (squared norm reading)."""
+    X = _f64(X)
+    Y = X if Y is None else _f64(Y)
+    assert X.shape[1] == Y.shape[1]
+    K = np.zeros((X.shape[0], Y.shape[0]))
+    _load().orc_gaussian_kernel(_ptr(X), X.shape[0], _ptr(Y), Y.shape[0], X.shape[1],
+                                float(gamma), _ptr(K), int(nthreads))
+    return K
+
+
+def compensated_sum(x):
+    x = _f64(x)
+    return float(_load().orc_compensated_sum(_ptr(x), len(x)))
+
+
+# --------------------------------------------------------------------------
+# Operators of Definition 1 and the sampling operator of Sec. 3, as matrices.
+# Pairs are numbered in the natural (lexicographic) order: (x, y) -> x*|Y| + y.
+# --------------------------------------------------------------------------
+
+def commutation_P(nD, nT):
+    """P in R^{(T x D) x (D x T)}: P[(t,d),(dbar,tbar)] = 1 iff d=dbar and t=tbar."""
+    P = np.zeros((nT * nD, nD * nT))
+    for t in range(nT):
+        for d in range(nD):
+            P[t * nD + d, d * nT + t] = 1.0
+    return P
+
+
+def unification_Q(nD, nT):
+    """Q in R^{(D x T) x (D x D)}: Q[(d,t),(dbar,dbar')] = 1 iff d = dbar = dbar'."""
+    Q = np.zeros((nD * nT, nD * nD))
+    for d in range(nD):
+        for t in range(nT):
+            Q[d * nT + t, d * nD + d] = 1.0
+    return Q
+
+
+def sampling_R(d, t, nD, nT):
+    """R(d,t) in R^{n x (D x T)}: row i selects the pair (d_i, t_i) (Sec. 3)."""
+    R = np.zeros((len(d), nD * nT))
+    for i, (a, b) in enumerate(zip(d, t)):
+        R[i, int(a) * nT + int(b)] = 1.0
+    return R
+
+
+# --------------------------------------------------------------------------
+# Kernel ridge regression, Eq. (linsystem): (K + lambda I) a = y.
+# --------------------------------------------------------------------------
+
+def krr_solve_dense(K, y, lam):
+    """Solve (K + lam I) a = y by a dense Cholesky factorisation (library primitive)."""
+    from scipy.linalg import cho_factor, cho_solve
+    A = np.array(K, dtype=np.float64) + lam * np.eye(K.shape[0])
+    return cho_solve(cho_factor(A, lower=True), np.asarray(y, dtype=np.float64))
+
+
+def krr_complete_closed_form(M, N, Y, lam):
+    """Complete data (every (d,t) pair present, natural order): solve
+    (M kron N + lam I) vec(A) = vec(Y) through the eigendecompositions
+    M = U diag(s) U^T, N = V diag(w) V^T (the closed form for complete data
+    that Sec. 1 cites).  Y is q x m with Y[t, d] = y_(d,t); returns A, q x m.
+    """
+    s, U = np.linalg.eigh(np.asarray(M, dtype=np.float64))
+    w, V = np.linalg.eigh(np.asarray(N, dtype=np.float64))
+    C = V.T @ Y @ U                      # coordinates in the eigenbasis
+    C = C / (np.outer(w, s) + lam)       # (M kron N + lam I) is diagonal there
+    return V @ C @ U.T
+
+
+def cg_solve(matvec, y, lam, tol=1e-6, max_iter=10000, x0=None):
+    """Plain conjugate gradients for (K + lam I) a = y (K symmetric PSD).
+
+    ``matvec(p)`` returns K p.  Stops when ||y - (K+lam I)a||_2 / ||y||_2 <= tol
+    for the recursively updated residual.  Returns (a, iterations, rel_res).
+    """
+    y = np.asarray(y, dtype=np.float64)
+    a = np.zeros_like(y) if x0 is None else np.array(x0, dtype=np.float64)
+    r = y - (matvec(a) + lam * a) if x0 is not None else y.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    ynorm = float(np.sqrt(y @ y))
+    if ynorm == 0.0:
+        return a, 0, 0.0
+    it = 0
+    while np.sqrt(rr) / ynorm > tol and it < max_iter:
+        w = matvec(p) + lam * p
+        alpha = rr / float(p @ w)
+        a += alpha * p
+        r -= alpha * w
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return a, it, float(np.sqrt(rr) / ynorm)
+
+
+def relative_residual(matvec, a, y, lam):
+    """||y - (K + lam I) a||_2 / ||y||_2 with the oracle's own matvec."""
+    r = np.asarray(y, dtype=np.float64) - (matvec(a) + lam * np.asarray(a))
+    return float(np.linalg.norm(r) / np.linalg.norm(y))

@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs shaped like the paper's drug-target workloads.
+
+This module holds no arithmetic of the method: it draws features, pair index
+sequences, right-hand sides and labels with NumPy's ``default_rng``.  Both the
+CUDA path and the oracle build their kernel matrices from these features
+themselves.  The paper's data sets (Table 5) are not available, so these
+stand in for them:
+
+  small       m=64 drugs, q=48 targets, 16-d features, gamma=1/16; the 3072 grid
+              cells are permuted, the first 1000 are training pairs and the
+              next 500 (disjoint) are prediction pairs; v, y ~ N(0,1); lambda=1e-2.
+  homogeneous m=q=2000 objects, 64-d, gamma=1/64; 200k ordered pairs (d, d'),
+              d != d', uniform without replacement (5 % of the off-diagonal
+              cells, the shape of the heterodimer / kernel-filling sets).
+  merget      m=2000, q=250, 128-d, gamma=1/128; 120k pairs uniform without
+              replacement (24 %, the shape of the Merget set);
+              y = x_d^T B x_t / sqrt(128*128) + N(0, 0.1^2), B ~ N(0,1).
+  batched     256 problems, problem b drawn with seed+b: m, q ~ U{32..512},
+              density ~ U[0.05, 0.6], 32-d, gamma=1/32, labels as merget,
+              16 lambdas logspace(-4, 0).
+  zipf        m=q=20000, 256-d, gamma=1/256, 10M unique pairs whose drug and
+              target ranks follow a Zipf(1.1) law truncated to the id range,
+              mapped through a random permutation of ids (kernel-filling scale).
+"""
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+
+@dataclass
+class PairProblem:
+    name: str
+    m: int                      # drugs (rows/cols of M)
+    q: int                      # targets (rows/cols of N)
+    Xd: np.ndarray              # m x dim drug features
+    Xt: np.ndarray              # q x dim target features (same array as Xd when homogeneous)
+    gamma: float
+    d: np.ndarray               # training pair drug ids (int32)
+    t: np.ndarray               # training pair target ids (int32)
+    v: Optional[np.ndarray] = None
+    y: Optional[np.ndarray] = None
+    d_pred: Optional[np.ndarray] = None
+    t_pred: Optional[np.ndarray] = None
+    lambdas: List[float] = field(default_factory=list)
+    homogeneous: bool = False
+
+    @property
+    def n(self):
+        return int(len(self.d))
+
+
+def _uniform_cells(rng, n_cells, n):
+    return rng.choice(n_cells, size=n, replace=False)
+
+
+def small(seed=0):
+    """m=64, q=48, 16-d features, 1000 training + 500 disjoint prediction pairs."""
+    rng = np.random.default_rng(seed)
+    m, q, dim = 64, 48, 16
+    Xd = rng.standard_normal((m, dim))
+    Xt = rng.standard_normal((q, dim))
+    cells = rng.permutation(m * q)
+    tr, pr = cells[:1000], cells[1000:1500]
+    v = rng.standard_normal(1000)
+    y = rng.standard_normal(1000)
+    return PairProblem("small", m, q, Xd, Xt, 1.0 / dim,
+                       (tr // q).astype(np.int32), (tr % q).astype(np.int32),
+                       v=v, y=y, d_pred=(pr // q).astype(np.int32),
+                       t_pred=(pr % q).astype(np.int32), lambdas=[1e-2])
+
+
+def homogeneous(seed=0, m=2000, dim=64, n=200_000):
+    """m=q objects, ordered off-diagonal pairs (d, d'), d != d', uniform w/o replacement."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m, dim))
+    cells = _uniform_cells(rng, m * (m - 1), n)
+    d = cells // (m - 1)
+    r = cells % (m - 1)
+    t = r + (r >= d)
+    v = rng.standard_normal(n)
+    y = rng.standard_normal(n)
+    return PairProblem("homogeneous", m, m, X, X, 1.0 / dim,
+                       d.astype(np.int32), t.astype(np.int32), v=v, y=y,
+                       lambdas=[1e-2], homogeneous=True)
+
+
+def _bilinear_labels(rng, Xd, Xt, d, t, noise=0.1):
+    B = rng.standard_normal((Xd.shape[1], Xt.shape[1]))
+    sig = np.einsum("ij,jk,ik->i", Xd[d], B, Xt[t]) / np.sqrt(Xd.shape[1] * Xt.shape[1])
+    return sig + noise * rng.standard_normal(len(d))
+
+
+def merget(seed=0, m=2000, q=250, dim=128, n=120_000):
+    """Heterogeneous drug-target problem shaped like the Merget set (24 % dense)."""
+    rng = np.random.default_rng(seed)
+    Xd = rng.standard_normal((m, dim))
+    Xt = rng.standard_normal((q, dim))
+    cells = _uniform_cells(rng, m * q, n)
+    d = (cells // q).astype(np.int32)
+    t = (cells % q).astype(np.int32)
+    y = _bilinear_labels(rng, Xd, Xt, d, t)
+    v = rng.standard_normal(n)
+    return PairProblem("merget", m, q, Xd, Xt, 1.0 / dim, d, t, v=v, y=y,
+                       lambdas=[1e-4, 1e-2, 1.0])
+
+
+def batched_problem(b, seed=0, dim=32):
+    """Problem b of the batched set: m, q ~ U{32..512}, density ~ U[0.05, 0.6]."""
+    rng = np.random.default_rng(seed + b)
+    m = int(rng.integers(32, 513))
+    q = int(rng.integers(32, 513))
+    rho = float(rng.uniform(0.05, 0.6))
+    n = max(1, int(round(rho * m * q)))
+    Xd = rng.standard_normal((m, dim))
+    Xt = rng.standard_normal((q, dim))
+    cells = _uniform_cells(rng, m * q, n)
+    d = (cells // q).astype(np.int32)
+    t = (cells % q).astype(np.int32)
+    y = _bilinear_labels(rng, Xd, Xt, d, t)
+    return PairProblem("batched%d" % b, m, q, Xd, Xt, 1.0 / dim, d, t, y=y,
+                       lambdas=list(np.logspace(-4, 0, 16)))
+
+
+def batched(n_problems=256, seed=0):
+    return [batched_problem(b, seed) for b in range(n_problems)]
+
+
+def _zipf_ids(rng, size, n_ids, s, perm):
+    ranks = np.arange(1, n_ids + 1, dtype=np.float64)
+    cdf = np.cumsum(ranks ** (-s))
+    cdf /= cdf[-1]
+    r = np.searchsorted(cdf, rng.random(size), side="right")
+    return perm[np.minimum(r, n_ids - 1)]
+
+
+def zipf(seed=0, m=20000, dim=256, n=10_000_000, s=1.1, chunk=4_000_000):
+    """Homogeneous-sized problem with Zipf(s) degrees on drugs and targets.
+
+    Pairs are drawn in chunks and duplicates rejected until n unique remain.
+    """
+    rng = np.random.default_rng(seed)
+    Xd = rng.standard_normal((m, dim))
+    Xt = rng.standard_normal((m, dim))
+    perm_d = rng.permutation(m)
+    perm_t = rng.permutation(m)
+    seen = np.zeros(0, dtype=np.int64)
+    while len(seen) < n:
+        dd = _zipf_ids(rng, chunk, m, s, perm_d)
+        tt = _zipf_ids(rng, chunk, m, s, perm_t)
+        key = dd.astype(np.int64) * m + tt
+        _, first = np.unique(key, return_index=True)
+        key = key[np.sort(first)]                       # first occurrence, draw order
+        new = key[~np.isin(key, seen)]
+        seen = np.concatenate([seen, new[: n - len(seen)]])
+    d = (seen // m).astype(np.int32)
+    t = (seen % m).astype(np.int32)
+    y = _bilinear_labels(rng, Xd, Xt, d, t)
+    return PairProblem("zipf", m, m, Xd, Xt, 1.0 / dim, d, t, y=y, lambdas=[1e-2, 1e-4])
+
+
+def random_pairs(rng, n, m_ids, q_ids):
+    """n pairs drawn with replacement (duplicates allowed), for edge-case tests."""
+    return (rng.integers(0, m_ids, n).astype(np.int32),
+            rng.integers(0, q_ids, n).astype(np.int32))
