@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the generalized vec trick (GVT) path on one GB300 per rank.
+
+Workload (the homogeneous drug-drug configuration): m = q = 2000 objects,
+64-d N(0,1) features, Gaussian base kernel (gamma = 1/64), n = 200k ordered
+pairs drawn uniformly without replacement, v ~ N(0,1), FP32 on the GPU.
+One step applies all nine pairwise kernels of Table 4b (Kronecker, Gaussian,
+linear, poly2d, Cartesian, symmetric, anti-symmetric, ranking, MLPK; 27
+Kronecker terms of Corollary 1) to v over the training pairs: 9 calls of
+gvt_pairwise_kernel_matvec through the C ABI.
+
+value = pair-terms/s = sum over kernels of n * nhat * T_kernel / step time
+(implicit kernel-matrix entries applied per second).  L2 is flushed (512 MB
+write) before every timed step, outside the per-step CUDA events.
+
+Also reported: the roofline of the dominant stage (live CUDA events around
+each stage launch), the FP64 oracle on the host cores (cpu_baseline), an
+end-to-end number through the same API with host buffers, SM clocks during
+the timed region, and the KRR solve time (FP64 CG vs mixed-precision
+refinement) on the Merget-shaped problem.
+
+--impl reference times the FP64 oracle (plain C, OpenMP) on the host cores on
+a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KINDS = ["kronecker", "gaussian", "linear", "poly2d", "cartesian", "symmetric",
+         "antisymmetric", "ranking", "mlpk"]
+TERMS = {"kronecker": 1, "gaussian": 1, "linear": 2, "poly2d": 3, "cartesian": 2,
+         "symmetric": 2, "antisymmetric": 2, "ranking": 4, "mlpk": 10}
+METRIC = "GVT pair-terms/s and KRR-CG solve time at rel. residual 1e-6 vs plain FP64 CG"
+UNIT = "pair-terms/s"
+WORKLOAD = ("homogeneous drug-drug: m=q=2000, 64-d features, Gaussian base kernel gamma=1/64, "
+            "n=200k uniform ordered pairs, all 9 pairwise kernels (27 Kronecker terms), FP32")
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gvt", choices=["gvt", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def workload(seed):
+    from paper_2009_01054_gb300 import synth
+    return synth.homogeneous(seed)
+
+
+def pair_terms_per_step(n):
+    return float(n) * float(n) * sum(TERMS.values())
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------- oracle (CPU)
+def cpu_oracle_rate(p, seconds, rows_per_call=64, seed=0):
+    """FP64 oracle pair-terms/s on sampled output rows (each row against all inputs)."""
+    import numpy as np
+    import oracle as orc
+    M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    rng = np.random.default_rng(seed)
+    rows_done = 0
+    t0 = time.perf_counter()
+    while True:
+        idx = rng.choice(p.n, rows_per_call, replace=False)
+        for kind in KINDS:
+            orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, p.v)
+        rows_done += rows_per_call
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    rate = rows_done * float(p.n) * sum(TERMS.values()) / el
+    return rate, el, rows_done, orc.num_threads()
+
+
+def traffic_for(kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2009_01054_gb300", "csrc", "stages.cu"), "rb").read()
+        if rec.get("stages_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get("kernels", {}).get(kernel_name, {}).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as orc
+    from oracle.build import build_oracle
+    build_oracle()
+    p = workload(0)
+    M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    rows = 256
+    rng = np.random.default_rng(0)
+
+    def step():
+        idx = rng.choice(p.n, rows, replace=False)
+        for kind in KINDS:
+            orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, p.v)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    ms = el / max(args.steps, 1) * 1e3
+    val = rows * float(p.n) * sum(TERMS.values()) / (ms / 1e3)
+    sample = "%d sampled output pairs per step, each against all %d input pairs, 9 kernels" % (rows, p.n)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD + " (FP64 oracle, CPU)", "m": p.m, "n": p.n,
+                      "kernels": KINDS, "sample": sample},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gvt(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2009_01054_gb300 import build as gbuild
+    from paper_2009_01054_gb300 import gvt
+
+    gbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    p = workload(rank)
+    H = gvt.Handle()
+    X = torch.as_tensor(p.Xd, device=dev)
+    M = gvt.gaussian_kernel(H, X, gamma=p.gamma, dtype=torch.float32)
+    plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=dev)
+    U = torch.empty((len(KINDS), p.n), dtype=torch.float32, device=dev)
+    descs = [gvt.gvt_desc_make(k) for k in KINDS]
+    Mm = gvt.matrix(M, symmetric=True)
+    sp = gvt.stream_ptr()
+    stream = torch.cuda.current_stream()
+    vp = gvt.ptr(v)
+    up = [gvt.ptr(U[i]) for i in range(len(KINDS))]
+
+    def step():
+        for i, d in enumerate(descs):
+            gvt.gvt_pairwise_kernel_matvec(plan.p, d, Mm, Mm, vp, up[i], 1, gvt.GVT_F32, sp)
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    gvt.gvt_stats_enable(H.h, True)
+    l0 = gvt.gvt_launch_count()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = gvt.gvt_launch_count() - l0
+    barrier()
+    clk = clocks.stop()
+    stats = gvt.gvt_stats_read(H.h)
+    gvt.gvt_stats_enable(H.h, False)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t.item())
+    pts = pair_terms_per_step(p.n)
+    value = ws * pts / (step_ms_max / 1e3)
+
+    # ---- roofline of the dominant stage
+    peaks, peak_src = measured_peaks()
+    dom = max(("stage1", "stage2", "one_sided"), key=lambda k: stats[k]["ms"])
+    st = stats[dom]
+    per_launch_ms = st["ms"] / max(st["launches"], 1)
+    flops_l = st["flops"] / max(st["launches"], 1)
+    bytes_l = st["bytes"] / max(st["launches"], 1)
+    ai = flops_l / max(bytes_l, 1.0)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ridge = FP32_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
+    if ai > ridge:
+        achieved = flops_l / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        achieved = bytes_l / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": peak_src}
+    kname = {"stage1": "stage1_dense_kernel", "stage2": "stage2_dense_kernel",
+             "one_sided": "gemv_rows_kernel"}[dom]
+    roof.update({"kernel": kname, "traffic": traffic_for(kname), "ms_per_launch": per_launch_ms,
+                 "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
+                 "hbm_frac": (bytes_l / (per_launch_ms / 1e3) / 1e9) / hbm})
+    stage_summary = {k: {"launches": stats[k]["launches"] // K,
+                         "ms_per_step": stats[k]["ms"] / K,
+                         "tflops": (stats[k]["flops"] / max(stats[k]["ms"], 1e-9)) / 1e9,
+                         "gbs": (stats[k]["bytes"] / max(stats[k]["ms"], 1e-9)) / 1e6}
+                     for k in stats}
+
+    # ---- end to end through the same API with host buffers
+    vh = torch.as_tensor(p.v, dtype=torch.float32).pin_memory()
+    Uh = torch.empty((len(KINDS), p.n), dtype=torch.float32).pin_memory()
+    Ke = max(10, K // 5)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(Ke):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        v.copy_(vh, non_blocking=True)
+        step()
+        Uh.copy_(U, non_blocking=True)
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2) / Ke
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e = {"value": ws * pts / (float(t.item()) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(vh.numel() * 4), "d2h_bytes_per_step": int(Uh.numel() * 4),
+           "ms_per_step": float(t.item())}
+
+    # ---- KRR solve: plain FP64 CG vs mixed-precision refinement
+    solve = None
+    if not args.no_solve and rank == 0:
+        solve = bench_solve(H, gvt, torch, dev)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        rate, el, rows, cores = cpu_oracle_rate(p, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d sampled output pairs x all %d input pairs x 9 kernels, FP64, %.1f s"
+                         % (rows, p.n, el)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+               "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "m": p.m, "q": p.m, "n": p.n, "nhat": p.n,
+                          "kernels": KINDS, "kronecker_terms": sum(TERMS.values()),
+                          "pair_terms_per_step": pts,
+                          "l2": "flushed (512 MB write) before every timed step, outside the events",
+                          "parallelism": "replicas: independent problems per rank (seed = rank)"},
+               "roofline": roof, "stages": stage_summary, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": clk, "gpu_launches": launches, "solve": solve}
+        print(json.dumps(out), flush=True)
+    plan.close()
+    H.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def bench_solve(H, gvt, torch, dev, lam=1e-2):
+    """Merget-shaped KRR (m=2000, q=250, n=120k, Kronecker kernel): wall time to FP64
+    rel. residual 1e-6 for plain FP64 CG and for FP32-inner iterative refinement."""
+    from paper_2009_01054_gb300 import synth
+    p = synth.merget(0)
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=dev), gamma=p.gamma)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    y = torch.as_tensor(p.y, device=dev)
+    res = {"workload": "merget-shaped: m=2000, q=250, 128-d, n=120k (24%%), Kronecker of Gaussians, "
+                       "lambda=%g, target FP64 rel. residual 1e-6" % lam}
+    for name, mode in (("fp64_cg", gvt.GVT_SOLVE_FP64_CG), ("mixed_ir", gvt.GVT_SOLVE_MIXED_IR)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=10,
+                                       max_iter=20000)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3
+        res[name] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
+                     "refinements": int(info.refinements), "rel_residual": info.rel_residual}
+    if res["mixed_ir"]["ms"] > 0:
+        res["speedup_vs_fp64_cg"] = res["fp64_cg"]["ms"] / res["mixed_ir"]["ms"]
+    plan.close()
+    return res
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_gvt(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,306 @@
+/*
+ * gvt.h -- C ABI of the GB300 (sm_103a) generalized vec trick library.
+ *
+ * The library applies pairwise kernel matrices to vectors without forming
+ * them.  With training pairs (d_j, t_j), j < n, and output pairs
+ * (dhat_i, that_i), i < nhat, a drug kernel matrix M (the paper's D) and a
+ * target kernel matrix N (the paper's T), the basic operation is
+ *
+ *     u = R(dhat, that) (M kron N) R(d, t)^T v,
+ *     u_i = sum_j M[dhat_i, d_j] * N[that_i, t_j] * v_j            (Theorem 1)
+ *
+ * computed in O(qbar*n + m*nhat) by the two-stage generalized vec trick:
+ * stage 1 forms S = N W (W is q x m sparse with v_j at (t_j, d_j)), stage 2
+ * gathers u_i = <M[dhat_i, :], S[that_i, :]>.  Every pairwise kernel of
+ * Table 4b is a sum of such Kronecker terms with permuted index sequences
+ * (Corollary 1); the kernel ridge regression system (K + lambda I) a = y
+ * (Eq. linsystem, Eq. 1) is solved with conjugate gradients on top.
+ *
+ * Conventions shared by every entry point:
+ *  - Every data pointer is DEVICE memory owned by the caller unless stated;
+ *    the library never frees caller memory.  Work is enqueued on the given
+ *    stream (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *  - Matrices are row-major with a leading dimension ld >= cols (elements).
+ *  - Index sequences are int32, 0-based.  Counts are int64.
+ *  - Multi-column vectors are column-major: column c of an n x k block starts
+ *    at element c*n.
+ *  - Every function returns a gvt_status.  Nothing aborts, traps or throws
+ *    across the ABI.  gvt_last_error() returns a message for the last
+ *    failure on the calling thread.
+ *  - Entry points that need a result on the host (plan validation, solver
+ *    convergence) synchronise the given stream; all others are asynchronous.
+ */
+#ifndef GVT_H_
+#define GVT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gvt_status {
+    GVT_OK = 0,
+    GVT_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype or shape */
+    GVT_ERR_INDEX_OOB = 2,     /* an index sequence leaves the kernel matrix */
+    GVT_ERR_UNSUPPORTED = 3,   /* valid request the library does not implement */
+    GVT_ERR_ALLOC = 4,         /* device allocation failed */
+    GVT_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    GVT_ERR_BREAKDOWN = 6,     /* CG breakdown: p^T (K + lambda I) p <= 0 or not finite */
+    GVT_ERR_NOT_CONVERGED = 7, /* iteration limit reached; best iterate returned */
+    GVT_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} gvt_status;
+
+/* Element / arithmetic types.  A gvt_matrix and the vectors of a call share one dtype. */
+typedef enum gvt_dtype {
+    GVT_F64 = 0,
+    GVT_F32 = 1,
+    GVT_BF16 = 2
+} gvt_dtype;
+
+/* Pairwise kernels of Table 4b.  GAUSSIAN is the Kronecker product of two
+ * Gaussian base kernels (Sec. 4.3); the caller supplies those as M and N.
+ * SYMMETRIC, ANTISYMMETRIC, RANKING and MLPK are homogeneous (Table 4a):
+ * both pair components index M, N is ignored. */
+typedef enum gvt_kernel_kind {
+    GVT_KERNEL_KRONECKER = 0,
+    GVT_KERNEL_GAUSSIAN = 1,
+    GVT_KERNEL_LINEAR = 2,
+    GVT_KERNEL_POLY2D = 3,
+    GVT_KERNEL_CARTESIAN = 4,
+    GVT_KERNEL_SYMMETRIC = 5,
+    GVT_KERNEL_ANTISYMMETRIC = 6,
+    GVT_KERNEL_RANKING = 7,
+    GVT_KERNEL_MLPK = 8
+} gvt_kernel_kind;
+
+/* Kronecker factor of a term.  M_SQ / N_SQ are elementwise squares
+ * (D^{o2} in Theorem 2), ONES the all-ones operator 1, IDENTITY the
+ * identity operator I (Corollary 1). */
+typedef enum gvt_factor {
+    GVT_FACTOR_M = 0,
+    GVT_FACTOR_N = 1,
+    GVT_FACTOR_M_SQ = 2,
+    GVT_FACTOR_N_SQ = 3,
+    GVT_FACTOR_ONES = 4,
+    GVT_FACTOR_IDENTITY = 5
+} gvt_factor;
+
+/* Which component of a pair an index comes from. */
+typedef enum gvt_component {
+    GVT_FIRST = 0,   /* d (drug) */
+    GVT_SECOND = 1   /* t (target), or d' on a homogeneous domain */
+} gvt_component;
+
+/*
+ * One Kronecker term of a pairwise kernel.  It adds
+ *     coef * A[o_a(i), i_a(j)] * B[o_b(i), i_b(j)] * v_j
+ * to u_i, where A = factor_a, B = factor_b, o_x(i) is component out_x of
+ * output pair i and i_x(j) is component in_x of input pair j.  Choosing
+ * components other than (FIRST, SECOND) is the index remapping by the
+ * commutation / unification operators, R(d,t)P = R(t,d) and
+ * R(d,t)Q = R(d,d) (proof of Corollary 1).
+ */
+typedef struct gvt_term {
+    double coef;
+    int32_t factor_a, factor_b;   /* gvt_factor */
+    int32_t out_a, out_b;         /* gvt_component */
+    int32_t in_a, in_b;           /* gvt_component */
+} gvt_term;
+
+#define GVT_MAX_TERMS 16
+
+/* A pairwise kernel as a sum of Kronecker terms (Corollary 1). */
+typedef struct gvt_desc {
+    int32_t kind;          /* gvt_kernel_kind, or -1 for a caller-built sum */
+    int32_t n_terms;       /* 1 .. GVT_MAX_TERMS */
+    int32_t homogeneous;   /* nonzero: needs the drug and target domains to coincide */
+    int32_t reserved;
+    gvt_term terms[GVT_MAX_TERMS];
+} gvt_desc;
+
+/* A dense kernel matrix in device memory. */
+typedef struct gvt_matrix {
+    const void* data;      /* device pointer, row-major */
+    int64_t rows, cols;    /* rows index output-pair ids, cols index input-pair ids */
+    int64_t ld;            /* leading dimension in elements, >= cols */
+    int32_t dtype;         /* gvt_dtype; must equal the call's dtype */
+    int32_t symmetric;     /* nonzero: caller asserts data[a*ld+b] == data[b*ld+a] (square).
+                              Lets stage 1 read columns as rows; otherwise the library
+                              transposes into its workspace. */
+} gvt_matrix;
+
+typedef struct gvt_handle gvt_handle;   /* workspace, library state */
+typedef struct gvt_plan gvt_plan;       /* sorted index sequences of one problem */
+
+/* Message describing the last failure on the calling thread ("" if none).
+ * The pointer stays valid until the next failing call on this thread. */
+const char* gvt_last_error(void);
+
+/* Library version, e.g. 1.0 -> 10000. */
+int32_t gvt_version(void);
+
+/* Create / destroy a handle.  The handle owns a growable device workspace
+ * and must not be used by two host threads at once.  Destroying NULL is OK.
+ * gvt_destroy synchronises the device before releasing memory. */
+gvt_status gvt_create(gvt_handle** out);
+gvt_status gvt_destroy(gvt_handle* h);
+
+/*
+ * Build a plan for a pair sample (Sec. 2: the sequences d, t; Sec. 3: the
+ * sampling operators R(d,t), R(dhat,that)).
+ *   m_rows, m_cols : shape of M (rows: output drug ids, cols: input drug ids)
+ *   q_rows, q_cols : shape of N (rows: output target ids, cols: input target ids)
+ *   d_in, t_in     : n_in input pairs (device int32); d_in < m_cols, t_in < q_cols
+ *   d_out, t_out   : n_out output pairs (device int32); d_out < m_rows, t_out < q_rows.
+ *                    Both NULL (and n_out ignored): output pairs = input pairs,
+ *                    the training operator of Eq. (1).
+ * The plan copies the sequences (the caller may free them afterwards),
+ * validates every index (GVT_ERR_INDEX_OOB names the first failing array)
+ * and sorts them by each component with a stable device radix sort.
+ * Synchronises `stream`.  n_in or n_out may be 0.  Counts must be < 2^31.
+ */
+gvt_status gvt_plan_create(gvt_handle* h,
+                           int64_t m_rows, int64_t m_cols, int64_t q_rows, int64_t q_cols,
+                           const int32_t* d_in, const int32_t* t_in, int64_t n_in,
+                           const int32_t* d_out, const int32_t* t_out, int64_t n_out,
+                           void* stream, gvt_plan** out);
+
+/* Release a plan (synchronises the device).  NULL is OK. */
+gvt_status gvt_plan_destroy(gvt_plan* plan);
+
+/* Number of input and output pairs of a plan. */
+gvt_status gvt_plan_sizes(const gvt_plan* plan, int64_t* n_in, int64_t* n_out);
+
+/*
+ * The Kronecker product kernel matrix times k_cols vectors (Theorem 1):
+ *     u = R(dhat,that) (M kron N) R(d,t)^T v
+ * v : n_in x k_cols, u : n_out x k_cols (column-major, device, `dtype`).
+ * M, N : kernel matrices in `dtype` (GVT_F64 or GVT_F32).  u is overwritten.
+ * The ordering of the two stages is chosen by the cost
+ * min(qbar*n + m*nhat, mbar*n + q*nhat) of Theorem 1.
+ */
+gvt_status gvt_matvec(gvt_plan* plan, const gvt_matrix* M, const gvt_matrix* N,
+                      const void* v, void* u, int64_t k_cols, int32_t dtype, void* stream);
+
+/* Fill `out` with the sum-of-Kronecker form of a Table 4b kernel
+ * (Corollary 1 and its proof; MLPK has 10 terms). */
+gvt_status gvt_desc_make(int32_t kind, gvt_desc* out);
+
+/*
+ * Pairwise kernel matrix times vectors:  u = R(dhat,that) K_desc R(d,t)^T v,
+ * K_desc = sum over desc->terms (Corollary 1).  Same layout rules as
+ * gvt_matvec; homogeneous descriptors need m_rows == q_rows and
+ * m_cols == q_cols and read M only (N may be NULL).  Terms that share
+ * factors and output components are merged so that each stage runs once
+ * per distinct (factor, index recipe).
+ */
+gvt_status gvt_pairwise_kernel_matvec(gvt_plan* plan, const gvt_desc* desc,
+                                      const gvt_matrix* M, const gvt_matrix* N,
+                                      const void* v, void* u, int64_t k_cols,
+                                      int32_t dtype, void* stream);
+
+/*
+ * Predictions for new pairs (Sec. 3, representer form; Eq. 1's prediction
+ * product):  p = R(dhat,that) K_desc R(d,t)^T a, with a the dual
+ * coefficients of the training pairs (the plan's input pairs) and the
+ * plan's output pairs the pairs to predict.  M and N are the cross kernels
+ * (rows: prediction-side ids, cols: training-side ids).
+ */
+gvt_status gvt_predict(gvt_plan* plan, const gvt_desc* desc,
+                       const gvt_matrix* M, const gvt_matrix* N,
+                       const void* a, void* p, int64_t k_cols, int32_t dtype, void* stream);
+
+/*
+ * Gaussian base kernel  K[a, b] = exp(-gamma * ||X_a - Y_b||^2)
+ * (Sec. 5.2, squared norm), computed in FP64 and stored in out_dtype
+ * (GVT_F64, GVT_F32 or GVT_BF16).  X: rows_x x dim, Y: rows_y x dim,
+ * row-major FP64 device arrays; Y may equal X.  K: rows_x x rows_y, ld ldk.
+ */
+gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x,
+                               const double* Y, int64_t rows_y, int64_t dim,
+                               double gamma, void* K, int64_t ldk, int32_t out_dtype,
+                               void* stream);
+
+/* Convert n elements between dtypes (device to device, round to nearest). */
+gvt_status gvt_convert(const void* src, int32_t src_dtype, void* dst, int32_t dst_dtype,
+                       int64_t n, void* stream);
+
+/* ------------------------------------------------------------------ solver */
+
+typedef enum gvt_solve_mode {
+    GVT_SOLVE_FP64_CG = 0,    /* plain CG, FP64 operator and vectors */
+    GVT_SOLVE_MIXED_IR = 1    /* FP64 residual + refinement around a low-precision inner CG */
+} gvt_solve_mode;
+
+typedef struct gvt_solve_opts {
+    double rel_tol;          /* target ||y - (K + lambda I) a||_2 / ||y||_2 (default 1e-6) */
+    int64_t max_iter;        /* total CG iterations, inner ones included (default 10000) */
+    int32_t mode;            /* gvt_solve_mode (default GVT_SOLVE_FP64_CG) */
+    int32_t inner_dtype;     /* MIXED_IR inner operator dtype: GVT_F32 (default) */
+    double inner_tol;        /* MIXED_IR inner relative tolerance (default 1e-3) */
+    int32_t max_refine;      /* MIXED_IR outer steps (default 30) */
+    int32_t check_every;     /* CG iterations between host convergence checks (default 1) */
+} gvt_solve_opts;
+
+typedef struct gvt_solve_info {
+    int64_t iterations;      /* CG iterations performed (inner ones for MIXED_IR) */
+    int32_t refinements;     /* outer refinement steps (MIXED_IR) */
+    int32_t status;          /* gvt_status of the solve */
+    double rel_residual;     /* final ||y - (K+lambda I)a|| / ||y||, recomputed in FP64 */
+    double time_ms;          /* wall-clock time of the solve on the host */
+} gvt_solve_info;
+
+/* Fill `o` with the defaults listed in gvt_solve_opts. */
+gvt_status gvt_solve_opts_default(gvt_solve_opts* o);
+
+/*
+ * Kernel ridge regression (Eq. linsystem / Eq. 1): solve
+ *     (R K_desc R^T + lambda I) a = y
+ * over the plan's input pairs (the plan must be a training plan: output
+ * pairs = input pairs).  M, N: FP64 kernel matrices.  y: n FP64.
+ * a: n FP64, in: warm start (set it to zero for a cold start), out: solution.
+ * MIXED_IR computes the residual y - (K + lambda I)a with the FP64 operator,
+ * solves for the correction with an FP32 operator (FP64 dot products and
+ * step lengths) and adds it to a in FP64; the inner matrices are converted
+ * into the handle's workspace.  Synchronises `stream`.  On
+ * GVT_ERR_NOT_CONVERGED / GVT_ERR_BREAKDOWN `a` holds the last iterate and
+ * `info` (may be NULL) is filled in.
+ */
+gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
+                            const gvt_matrix* M, const gvt_matrix* N,
+                            const double* y, double lambda, double* a,
+                            const gvt_solve_opts* opts, gvt_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------ instrumentation */
+
+/* Per-stage device time and algorithmic work of the products made with a
+ * handle while statistics are enabled.  Each stage launch is bracketed by
+ * CUDA events on its own stream. */
+typedef enum gvt_stat_kind {
+    GVT_STAT_STAGE1 = 0,     /* stage 1: S = B W (sparse scatter-accumulate) */
+    GVT_STAT_STAGE2 = 1,     /* stage 2: sampled gather-dot */
+    GVT_STAT_ONE_SIDED = 2,  /* one-sided terms: segment sums, GEMV, gather */
+    GVT_STAT_COUNT = 3
+} gvt_stat_kind;
+
+typedef struct gvt_kernel_stats {
+    int64_t launches;        /* launches recorded */
+    double ms;               /* summed device time of those launches */
+    double flops;            /* algorithmic flops (2 per multiply-add of the definition) */
+    double bytes;            /* algorithmic bytes: each operand read once, each result written once */
+} gvt_kernel_stats;
+
+/* Start (on != 0) or stop recording; starting clears the counters. */
+gvt_status gvt_stats_enable(gvt_handle* h, int32_t on);
+/* Fill out[0 .. GVT_STAT_COUNT-1].  Synchronises the recorded events. */
+gvt_status gvt_stats_read(gvt_handle* h, gvt_kernel_stats* out);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t gvt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GVT_H_ */

@@ -1,0 +1,219 @@
+// Internal declarations of the GVT library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gvt.h"
+
+namespace gvt {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+gvt_status cuda_fail(cudaError_t e, const char* what);
+
+#define GVT_CUDA(call)                                                     \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return ::gvt::cuda_fail(e_, #call);         \
+    } while (0)
+
+#define GVT_CHECK(call)                                                    \
+    do {                                                                   \
+        gvt_status s_ = (call);                                            \
+        if (s_ != GVT_OK) return s_;                                       \
+    } while (0)
+
+// Count `n` kernel launches made just before and check their launch status.
+void count_launches(int n);
+#define GVT_LAUNCHED(n, what)                                              \
+    do {                                                                   \
+        ::gvt::count_launches(n);                                          \
+        GVT_CUDA(cudaGetLastError());                                      \
+    } while (0)
+#define GVT_LAUNCH_CHECK(what) GVT_LAUNCHED(1, what)
+
+struct StatRec {
+    int kind;
+    cudaEvent_t e0, e1;
+    double flops, bytes;
+};
+
+// ---------------------------------------------------------------- device memory
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    gvt_status reserve(size_t nbytes, cudaStream_t s);   // grow-only
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Bump allocator over one growable device buffer: a call lays out its
+// temporaries with take(), then commit() grows the buffer if needed.
+struct Arena {
+    DevBuf buf;
+    size_t used = 0;
+    void reset() { used = 0; }
+    size_t take(size_t bytes) {  // returns offset, 256-byte aligned
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + bytes;
+        return off;
+    }
+    gvt_status commit(cudaStream_t s) { return buf.reserve(used, s); }
+    char* base() const { return static_cast<char*>(buf.ptr); }
+};
+
+}  // namespace gvt
+
+struct gvt_handle {
+    gvt::Arena ws;          // per-call workspace (S, transposes, partial sums)
+    gvt::Arena solve_ws;    // solver vectors
+    gvt::DevBuf status;     // device status words
+    double* host_scalars = nullptr;  // pinned
+    bool stats_on = false;
+    std::vector<gvt::StatRec> recs;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace gvt {
+// Bracket one stage launch with events when statistics are on.
+struct StatScope {
+    gvt_handle* h;
+    cudaStream_t s;
+    int kind;
+    double flops, bytes;
+    cudaEvent_t e0 = nullptr;
+    StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, double bytes_);
+    ~StatScope();
+};
+}  // namespace gvt
+
+namespace gvt {
+
+// Input or output pairs sorted (stably) by one component.
+struct Order {
+    int32_t* key = nullptr;    // sorted component values
+    int32_t* other = nullptr;  // the other component, same order
+    int32_t* perm = nullptr;   // original pair index
+    int32_t* seg = nullptr;    // seg[k] = first sorted position with key >= k, k in [0, K]
+    int64_t K = 0;             // id range of the key component
+};
+
+}  // namespace gvt
+
+struct gvt_plan {
+    gvt_handle* h = nullptr;
+    int64_t m_rows = 0, m_cols = 0, q_rows = 0, q_cols = 0;
+    int64_t n_in = 0, n_out = 0;
+    bool out_is_in = false;
+    int32_t* d_in = nullptr;
+    int32_t* t_in = nullptr;
+    int32_t* d_out = nullptr;
+    int32_t* t_out = nullptr;
+    gvt::Order in_by[2];    // [FIRST], [SECOND]
+    gvt::Order out_by[2];
+    std::vector<void*> allocs;
+};
+
+namespace gvt {
+
+// ---------------------------------------------------------------- sort / scan
+// Workspace bytes needed by radix_sort_by_key for n elements.
+size_t sort_workspace_bytes(int64_t n);
+// Stable sort of `keys` (values in [0, K)) carrying the original index.
+// out_key / out_perm: n each.  ws: sort_workspace_bytes(n) bytes.
+gvt_status radix_sort_by_key(const int32_t* keys, int64_t n, int64_t K, int32_t* out_key,
+                             int32_t* out_perm, void* ws, cudaStream_t s);
+// seg[k] = lower_bound(sorted_key, k), k in [0, K].
+gvt_status segment_offsets(const int32_t* sorted_key, int64_t n, int64_t K, int32_t* seg,
+                           cudaStream_t s);
+// out[i] = in[perm[i]]
+gvt_status gather_i32(const int32_t* in, const int32_t* perm, int64_t n, int32_t* out,
+                      cudaStream_t s);
+// min and max of an int32 array into dev_minmax[0..1] (int32); n > 0.
+gvt_status minmax_i32(const int32_t* x, int64_t n, int32_t* dev_minmax, cudaStream_t s);
+
+// ---------------------------------------------------------------- stage kernels
+enum FactorMode { FM_DENSE = 0, FM_SQUARE = 1 };
+
+// One source of stage-1 entries: the input pairs in one sorted order.
+// Entry j of column x (j in [seg[x], seg[x+1])) contributes coef*v[perm[j]] at
+// row bcol[j] of W.
+struct S1Source {
+    const int32_t* seg;
+    const int32_t* bcol;
+    const int32_t* perm;
+    double coef;
+};
+constexpr int kMaxSources = 4;
+struct S1Sources {
+    S1Source src[kMaxSources];
+    int count;
+};
+
+// S[y, x] = sum_src coef * sum_{j in seg_src[x]} Bt[bcol_j, y] * v[perm_j]   (y < Y, x < X)
+// Bt is B transposed: Bt[t*ldb + y] = B[y, t].  mode squares B's entries.
+template <class T>
+gvt_status stage1_dense(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
+                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s);
+// B = identity: S[y, x] = sum_src coef * sum_{j in seg_src[x], bcol_j == y} v[perm_j]
+// (S must be zeroed by the caller; entries with bcol >= Y are skipped).
+template <class T>
+gvt_status stage1_identity(const S1Sources& srcs, const T* v, T* S, int64_t lds, int64_t Y,
+                           int64_t X, cudaStream_t s);
+
+// Output pairs in one sorted order: row of A = arow[i], row of S = srow[i],
+// destination u[perm[i]].
+struct S2Outputs {
+    const int32_t* arow;
+    const int32_t* srow;
+    const int32_t* perm;
+    int64_t n;
+};
+// u[perm_i] += coef * sum_{x < X} A[arow_i, x] * S[srow_i, x]
+template <class T>
+gvt_status stage2_dense(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
+                        const S2Outputs& outs, double coef, T* u, cudaStream_t s);
+// A = identity: u[perm_i] += coef * S[srow_i, arow_i] (arow_i < X)
+template <class T>
+gvt_status stage2_identity(const T* S, int64_t lds, int64_t X, const S2Outputs& outs, double coef,
+                           T* u, cudaStream_t s);
+
+// One-sided terms (a factor is the all-ones operator).
+// s[x] += coef * sum_{j in seg[x]} v[perm_j]   for x < K
+template <class T>
+gvt_status segment_sums(const int32_t* seg, const int32_t* perm, int64_t K, const T* v, double coef,
+                        T* s_out, cudaStream_t s);
+// z[r] = sum_{x < X} F[r, x] * s[x]  for r < R  (mode squares F)
+template <class T>
+gvt_status gemv_rows(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svec, T* z,
+                     cudaStream_t s);
+// u[i] += z[idx[i]]  for i < n
+template <class T>
+gvt_status gather_add(const T* z, const int32_t* idx, int64_t n, T* u, cudaStream_t s);
+
+// Bt[c*ldt + r] = B[r*ldb + c]
+template <class T>
+gvt_status transpose(const T* B, int64_t ldb, int64_t rows, int64_t cols, T* Bt, int64_t ldt,
+                     cudaStream_t s);
+
+gvt_status convert(const void* src, int sdt, void* dst, int ddt, int64_t n, cudaStream_t s);
+gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t ry, int64_t dim,
+                           double gamma, void* K, int64_t ldk, int dtype, cudaStream_t s);
+
+size_t dtype_size(int dt);
+
+// ---------------------------------------------------------------- pairwise driver
+// u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).
+template <class T>
+gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                          const gvt_matrix* N, const T* v, T* u, cudaStream_t s);
+
+// ---------------------------------------------------------------- vector kernels (CG)
+template <class T>
+gvt_status vec_zero(T* x, int64_t n, cudaStream_t s);
+
+}  // namespace gvt

@@ -1,0 +1,408 @@
+// Kernel ridge regression (Eq. linsystem / Eq. 1) by conjugate gradients on
+// top of the GVT products: plain FP64 CG, and mixed-precision iterative
+// refinement (FP64 residual and correction, FP32 operator and vectors inside,
+// FP64 dot products and step lengths everywhere).
+//
+// Scalars live on the device; a CG iteration is
+//   w = K p (GVT), w += lambda p, pw = p.w        (fused shift + dot)
+//   alpha = rr / pw                               (one block)
+//   a += alpha p, r -= alpha w, rr' = r.r         (fused update + dot)
+//   beta = rr' / rr                               (one block)
+//   p = r + beta p
+// Dot products reduce in FP64 in a fixed order (per-block partials, then one
+// block), so a run is bitwise reproducible.
+#include <chrono>
+#include <cmath>
+
+#include "gvt_internal.h"
+
+namespace gvt {
+namespace {
+
+constexpr int kRedBlocks = 256;
+constexpr int kRedThreads = 256;
+
+enum Scal { SC_RR = 0, SC_PW, SC_ALPHA, SC_BETA, SC_FLAG, SC_RR0, SC_TMP, SC_COUNT };
+
+__device__ double block_sum(double x)
+{
+    __shared__ double sh[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = x;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kRedThreads / 32; ++i) r += sh[i];
+    __syncthreads();
+    return r;   // valid in thread 0
+}
+
+template <class X, class Y>
+__global__ void __launch_bounds__(kRedThreads)
+dot_kernel(const X* __restrict__ x, const Y* __restrict__ y, int64_t n, double* __restrict__ part)
+{
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)x[i] * (double)y[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// w += lambda p ; part = p.w
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+shift_dot_kernel(T* __restrict__ w, const T* __restrict__ p, double lam, int64_t n, double* __restrict__ part)
+{
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T wi = w[i] + (T)lam * p[i];
+        w[i] = wi;
+        acc += (double)p[i] * (double)wi;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// sc[dst] = sum(part); optionally alpha / beta / breakdown logic
+__global__ void __launch_bounds__(kRedThreads)
+finalize_kernel(const double* __restrict__ part, int nb, double* __restrict__ sc, int what)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
+    acc = block_sum(acc);
+    if (threadIdx.x != 0) return;
+    if (what == 0) {            // alpha = rr / pw
+        sc[SC_PW] = acc;
+        if (!(acc > 0.0) || !isfinite(acc)) {
+            sc[SC_FLAG] = 1.0;
+            sc[SC_ALPHA] = 0.0;
+        } else {
+            sc[SC_ALPHA] = sc[SC_RR] / acc;
+        }
+    } else if (what == 1) {     // beta = rr' / rr, rr = rr'
+        const double rr = sc[SC_RR];
+        sc[SC_BETA] = (rr > 0.0) ? acc / rr : 0.0;
+        sc[SC_RR] = acc;
+        if (!isfinite(acc)) sc[SC_FLAG] = 1.0;
+    } else if (what == 2) {     // rr = sum, start of a CG run
+        sc[SC_RR] = acc;
+        sc[SC_RR0] = acc;
+        sc[SC_FLAG] = 0.0;
+    } else {                    // plain dot into SC_TMP
+        sc[SC_TMP] = acc;
+    }
+}
+
+// a += alpha p ; r -= alpha w ; part = r.r
+template <class T, class TA>
+__global__ void __launch_bounds__(kRedThreads)
+update_kernel(TA* __restrict__ a, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ w,
+              int64_t n, const double* __restrict__ sc, double* __restrict__ part)
+{
+    const double alpha = sc[SC_ALPHA];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a[i] = (TA)((double)a[i] + alpha * (double)p[i]);
+        const T ri = (T)((double)r[i] - alpha * (double)w[i]);
+        r[i] = ri;
+        acc += (double)ri * (double)ri;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// p = r + beta p
+template <class T>
+__global__ void pupdate_kernel(T* __restrict__ p, const T* __restrict__ r, int64_t n, const double* __restrict__ sc)
+{
+    const double beta = sc[SC_BETA];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (T)((double)r[i] + beta * (double)p[i]);
+}
+
+// r = y - (Ka + lambda a), with Ka given
+__global__ void residual_kernel(const double* __restrict__ y, const double* __restrict__ Ka,
+                                const double* __restrict__ a, double lam, int64_t n, double* __restrict__ r)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = y[i] - (Ka[i] + lam * a[i]);
+}
+
+// dst = (float)(src * scale)
+__global__ void scale_to_f32_kernel(const double* __restrict__ src, double scale, int64_t n, float* __restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)(src[i] * scale);
+}
+
+// a += scale * c
+__global__ void axpy_f32_kernel(double* __restrict__ a, const float* __restrict__ c, double scale, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += scale * (double)c[i];
+}
+
+template <class T>
+__global__ void copy_kernel(T* __restrict__ dst, const T* __restrict__ src, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+unsigned vgrid(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > 152 * 8) g = 152 * 8;
+    return (unsigned)g;
+}
+
+// Plain CG on (K + lambda I) x = b with operator dtype T; x has type TA.
+// x starts at zero.  Returns iterations used through *iters and the final
+// recursive relative residual through *rel.
+template <class T, class TA>
+gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, const gvt_matrix* N,
+                  const T* b, double bnorm, double lam, TA* x, T* r, T* p, T* w, double* part, double* sc,
+                  double* hsc, double tol, int64_t max_iter, int check_every, int64_t* iters, double* rel,
+                  cudaStream_t s)
+{
+    const int64_t n = plan->n_in;
+    *iters = 0;
+    *rel = 1.0;
+    if (bnorm == 0.0) {
+        *rel = 0.0;
+        return GVT_OK;
+    }
+    copy_kernel<T><<<vgrid(n), 256, 0, s>>>(r, b, n);
+    copy_kernel<T><<<vgrid(n), 256, 0, s>>>(p, b, n);
+    dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
+    finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 2);
+    GVT_LAUNCHED(4, "cg init");
+    if (check_every < 1) check_every = 1;
+    int64_t it = 0;
+    while (it < max_iter) {
+        GVT_CHECK(pairwise_apply<T>(plan, desc, M, N, p, w, s));
+        shift_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lam, n, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
+        update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
+        pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
+        GVT_LAUNCHED(5, "cg iteration");
+        ++it;
+        if (it % check_every == 0 || it == max_iter) {
+            GVT_CUDA(cudaMemcpyAsync(hsc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+            GVT_CUDA(cudaStreamSynchronize(s));
+            *iters = it;
+            if (hsc[SC_FLAG] != 0.0) {
+                *rel = std::sqrt(std::fabs(hsc[SC_RR])) / bnorm;
+                set_error("CG breakdown: p^T (K + lambda I) p <= 0 or not finite");
+                return GVT_ERR_BREAKDOWN;
+            }
+            *rel = std::sqrt(hsc[SC_RR]) / bnorm;
+            if (*rel <= tol) return GVT_OK;
+        }
+    }
+    *iters = it;
+    return GVT_ERR_NOT_CONVERGED;
+}
+
+// ||y - (K64 a + lambda a)|| into r (FP64) and its norm on the host.
+gvt_status fp64_residual(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, const gvt_matrix* N,
+                         const double* y, const double* a, double lam, double* Ka, double* r, double* part,
+                         double* sc, double* hsc, double* rnorm, cudaStream_t s)
+{
+    const int64_t n = plan->n_in;
+    GVT_CHECK(pairwise_apply<double>(plan, desc, M, N, a, Ka, s));
+    residual_kernel<<<vgrid(n), 256, 0, s>>>(y, Ka, a, lam, n, r);
+    dot_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
+    finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 3);
+    GVT_LAUNCHED(3, "residual");
+    GVT_CUDA(cudaMemcpyAsync(hsc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GVT_CUDA(cudaStreamSynchronize(s));
+    *rnorm = std::sqrt(hsc[SC_TMP]);
+    return GVT_OK;
+}
+
+}  // namespace
+}  // namespace gvt
+
+using namespace gvt;
+
+extern "C" {
+
+gvt_status gvt_solve_opts_default(gvt_solve_opts* o)
+{
+    if (!o) {
+        set_error("gvt_solve_opts_default: NULL");
+        return GVT_ERR_INVALID_ARG;
+    }
+    o->rel_tol = 1e-6;
+    o->max_iter = 10000;
+    o->mode = GVT_SOLVE_FP64_CG;
+    o->inner_dtype = GVT_F32;
+    o->inner_tol = 1e-3;
+    o->max_refine = 30;
+    o->check_every = 1;
+    return GVT_OK;
+}
+
+gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                            const gvt_matrix* N, const double* y, double lambda, double* a,
+                            const gvt_solve_opts* opts_in, gvt_solve_info* info, void* stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    gvt_solve_opts opts;
+    if (opts_in) opts = *opts_in; else gvt_solve_opts_default(&opts);
+    gvt_solve_info loc{};
+    if (!info) info = &loc;
+    *info = gvt_solve_info{};
+    auto ret = [&](gvt_status st_) {
+        info->status = st_;
+        return st_;
+    };
+    if (!h || !plan || !desc || !M || (!N && !desc->homogeneous)) {
+        set_error("gvt_krr_cg_solve: NULL argument");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (!plan->out_is_in) {
+        set_error("gvt_krr_cg_solve: the plan must be a training plan (output pairs = input pairs)");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (!(lambda > 0.0) || !(opts.rel_tol > 0.0) || opts.max_iter < 0) {
+        set_error("gvt_krr_cg_solve: lambda and rel_tol must be > 0");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (opts.mode != GVT_SOLVE_FP64_CG && opts.mode != GVT_SOLVE_MIXED_IR) {
+        set_error("gvt_krr_cg_solve: unknown mode");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (opts.mode == GVT_SOLVE_MIXED_IR && opts.inner_dtype != GVT_F32) {
+        set_error("gvt_krr_cg_solve: MIXED_IR supports an FP32 inner operator");
+        return ret(GVT_ERR_UNSUPPORTED);
+    }
+    const int64_t n = plan->n_in;
+    if (n > 0 && (!y || !a)) {
+        set_error("gvt_krr_cg_solve: y or a is NULL");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (M->dtype != GVT_F64 || (N && !desc->homogeneous && N->dtype != GVT_F64)) {
+        set_error("gvt_krr_cg_solve: M and N must be FP64");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (n == 0) {
+        info->time_ms = 0.0;
+        return ret(GVT_OK);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool homo = desc->homogeneous != 0;
+    const gvt_matrix* Nn = homo ? M : N;
+
+    // ---- solver workspace
+    Arena& ws = h->solve_ws;
+    ws.reset();
+    const size_t o_r = ws.take(8 * n), o_p = ws.take(8 * n), o_w = ws.take(8 * n), o_y = ws.take(8 * n);
+    const size_t o_part = ws.take(8 * kRedBlocks), o_sc = ws.take(8 * SC_COUNT);
+    size_t o_m32 = 0, o_n32 = 0, o_r32 = 0, o_p32 = 0, o_w32 = 0, o_c32 = 0, o_q32 = 0;
+    const bool mixed = opts.mode == GVT_SOLVE_MIXED_IR;
+    if (mixed) {
+        o_m32 = ws.take(4 * (size_t)M->rows * M->ld);
+        if (!homo) o_n32 = ws.take(4 * (size_t)Nn->rows * Nn->ld);
+        o_r32 = ws.take(4 * n); o_p32 = ws.take(4 * n); o_w32 = ws.take(4 * n); o_c32 = ws.take(4 * n);
+        o_q32 = ws.take(4 * n);
+    }
+    gvt_status st = ws.commit(s);
+    if (st != GVT_OK) return ret(st);
+    char* base = ws.base();
+    double* r = (double*)(base + o_r);
+    double* p = (double*)(base + o_p);
+    double* w = (double*)(base + o_w);
+    double* ytmp = (double*)(base + o_y);
+    double* part = (double*)(base + o_part);
+    double* sc = (double*)(base + o_sc);
+    double* hsc = h->host_scalars;
+
+    // ||y||
+    dot_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(y, y, n, part);
+    finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 3);
+    count_launches(2);
+    if (cudaMemcpyAsync(hsc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ret(cuda_fail(cudaGetLastError(), "solve init"));
+    const double ynorm = std::sqrt(hsc[SC_TMP]);
+
+    auto finish = [&](gvt_status status) {
+        double rn = 0.0;
+        gvt_status s2 = fp64_residual(plan, desc, M, Nn, y, a, lambda, w, r, part, sc, hsc, &rn, s);
+        info->rel_residual = ynorm > 0 ? rn / ynorm : 0.0;
+        info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (s2 != GVT_OK) status = s2;
+        return ret(status);
+    };
+
+    if (!mixed) {
+        // b = y - (K a + lambda a) for a warm start; x accumulates the correction into a.
+        double rn;
+        st = fp64_residual(plan, desc, M, Nn, y, a, lambda, w, ytmp, part, sc, hsc, &rn, s);
+        if (st != GVT_OK) return ret(st);
+        if (ynorm == 0.0 || rn / ynorm <= opts.rel_tol) return finish(GVT_OK);
+        int64_t its = 0;
+        double rel = 1.0;
+        // CG on the correction: stop when ||r|| <= rel_tol * ||y||
+        st = cg_run<double, double>(plan, desc, M, Nn, ytmp, rn, lambda, a, r, p, w, part, sc, hsc,
+                                    opts.rel_tol * ynorm / rn, opts.max_iter, opts.check_every, &its, &rel, s);
+        info->iterations = its;
+        return finish(st);
+    }
+
+    // ---- mixed precision: FP32 copies of the kernel matrices
+    float* m32 = (float*)(base + o_m32);
+    float* n32 = homo ? m32 : (float*)(base + o_n32);
+    float* r32 = (float*)(base + o_r32);
+    float* p32 = (float*)(base + o_p32);
+    float* w32 = (float*)(base + o_w32);
+    float* c32 = (float*)(base + o_c32);
+    float* q32 = (float*)(base + o_q32);
+    // element count up to the end of the last row (a view's ld may run past its allocation)
+    auto span = [](const gvt_matrix* A) { return A->rows > 0 ? (A->rows - 1) * A->ld + A->cols : 0; };
+    st = convert(M->data, GVT_F64, m32, GVT_F32, span(M), s);
+    if (st == GVT_OK && !homo) st = convert(Nn->data, GVT_F64, n32, GVT_F32, span(Nn), s);
+    if (st != GVT_OK) return ret(st);
+    gvt_matrix M32 = *M, N32 = *Nn;
+    M32.data = m32; M32.dtype = GVT_F32;
+    N32.data = n32; N32.dtype = GVT_F32;
+
+    int64_t total = 0;
+    for (int k = 0; k <= opts.max_refine; ++k) {
+        double rn;
+        st = fp64_residual(plan, desc, M, Nn, y, a, lambda, w, r, part, sc, hsc, &rn, s);
+        if (st != GVT_OK) return ret(st);
+        info->refinements = k;
+        if (ynorm == 0.0 || rn / ynorm <= opts.rel_tol) {
+            info->iterations = total;
+            return finish(GVT_OK);
+        }
+        if (total >= opts.max_iter || k == opts.max_refine) break;
+        scale_to_f32_kernel<<<vgrid(n), 256, 0, s>>>(r, 1.0 / rn, n, r32);
+        count_launches(1);
+        vec_zero<float>(c32, n, s);
+        int64_t its = 0;
+        double rel = 1.0;
+        // the inner solve only needs to reach the outer target relative to ||r||
+        const double inner_tol = std::max(opts.inner_tol, 0.5 * opts.rel_tol * ynorm / rn);
+        st = cg_run<float, float>(plan, desc, &M32, &N32, r32, 1.0, lambda, c32, q32, p32, w32, part, sc,
+                                  hsc, inner_tol, opts.max_iter - total, opts.check_every, &its, &rel, s);
+        total += its;
+        if (st == GVT_ERR_BREAKDOWN) {
+            info->iterations = total;
+            return finish(st);
+        }
+        axpy_f32_kernel<<<vgrid(n), 256, 0, s>>>(a, c32, rn, n);
+        count_launches(1);
+    }
+    info->iterations = total;
+    return finish(GVT_ERR_NOT_CONVERGED);
+}
+
+}  // extern "C"

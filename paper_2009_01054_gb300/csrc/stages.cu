@@ -1,0 +1,509 @@
+// The two stages of the generalized vec trick (Theorem 1) and the small
+// kernels around them.
+//
+// Stage 1 (sparse, SIMT): S = B W, W holding v_j at (bcol_j, x_j), computed
+// column tile by column tile over input pairs sorted by x (segments).  A warp
+// reads 32 entries of a segment at a time and broadcasts each (row, weight)
+// with warp shuffles; every thread owns VEC consecutive output rows and TX
+// columns in registers and streams the needed row of B^T with one 16-byte
+// load per entry.
+//
+// Stage 2 (sampled gather-dot): u_i = <A[arow_i, :], S[srow_i, :]>, one warp
+// per output pair, outputs sorted by arow so that consecutive warps share the
+// A row in L1; 16-byte vector loads of both rows.
+#include <cuda_bf16.h>
+
+#include "gvt_internal.h"
+
+namespace gvt {
+namespace {
+
+template <class T> struct Vec;
+template <> struct Vec<float> {
+    using type = float4;
+    static constexpr int N = 4;
+    __device__ static void split(const float4& q, float* o) { o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w; }
+    __device__ static float4 make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <> struct Vec<double> {
+    using type = double2;
+    static constexpr int N = 2;
+    __device__ static void split(const double2& q, double* o) { o[0] = q.x; o[1] = q.y; }
+    __device__ static double2 make(const double* o) { return make_double2(o[0], o[1]); }
+};
+
+__host__ __device__ inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+unsigned grid1d(int64_t n, int threads, int64_t cap = 152 * 32)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ------------------------------------------------------------------ stage 1
+constexpr int kS1Threads = 128;
+constexpr int kS1Cols = 8;
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(kS1Threads)
+stage1_dense_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
+                    const T* __restrict__ v, T* __restrict__ S, int64_t lds, int64_t Y, int64_t X)
+{
+    constexpr int VEC = Vec<T>::N;
+    using VT = typename Vec<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int64_t y0 = (int64_t)blockIdx.x * (kS1Threads * VEC) + (int64_t)threadIdx.x * VEC;
+    const int64_t x0 = (int64_t)blockIdx.y * kS1Cols;
+    const bool vec_rows = (y0 + VEC <= Y) && (ldb % VEC == 0) && aligned16(Bt);
+
+    T acc[VEC][kS1Cols];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k)
+#pragma unroll
+        for (int c = 0; c < kS1Cols; ++c) acc[k][c] = T(0);
+
+#pragma unroll
+    for (int c = 0; c < kS1Cols; ++c) {
+        const int64_t x = x0 + c;
+        if (x >= X) break;
+        for (int si = 0; si < srcs.count; ++si) {
+            const S1Source& sr = srcs.src[si];
+            const int32_t beg = sr.seg[x], end = sr.seg[x + 1];
+            const T coef = (T)sr.coef;
+            for (int32_t j0 = beg; j0 < end; j0 += 32) {
+                const int32_t j = j0 + lane;
+                int32_t t = 0;
+                T w = T(0);
+                if (j < end) {
+                    t = sr.bcol[j];
+                    w = coef * v[sr.perm[j]];
+                }
+                const int cnt = min(32, end - j0);
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const int32_t tt = __shfl_sync(0xffffffffu, t, jj);
+                    const T ww = __shfl_sync(0xffffffffu, w, jj);
+                    const T* brow = Bt + (int64_t)tt * ldb + y0;
+                    T b[VEC];
+                    if (vec_rows) {
+                        Vec<T>::split(__ldg(reinterpret_cast<const VT*>(brow)), b);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < VEC; ++k) b[k] = (y0 + k < Y) ? __ldg(brow + k) : T(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        const T bk = MODE == FM_SQUARE ? b[k] * b[k] : b[k];
+                        acc[k][c] = fma(ww, bk, acc[k][c]);
+                    }
+                }
+            }
+        }
+    }
+
+    const bool vec_cols = (x0 + kS1Cols <= X) && (lds % VEC == 0) && aligned16(S) && (x0 % VEC == 0);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        const int64_t y = y0 + k;
+        if (y >= Y) break;
+        T* srow = S + y * lds + x0;
+        if (vec_cols) {
+#pragma unroll
+            for (int c = 0; c < kS1Cols; c += VEC)
+                *reinterpret_cast<VT*>(srow + c) = Vec<T>::make(&acc[k][c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < kS1Cols; ++c)
+                if (x0 + c < X) srow[c] = acc[k][c];
+        }
+    }
+}
+
+template <class T>
+__global__ void stage1_identity_kernel(S1Sources srcs, const T* __restrict__ v, T* __restrict__ S,
+                                       int64_t lds, int64_t Y, int64_t X)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < X;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        for (int si = 0; si < srcs.count; ++si) {
+            const S1Source& sr = srcs.src[si];
+            const T coef = (T)sr.coef;
+            for (int32_t j = sr.seg[x]; j < sr.seg[x + 1]; ++j) {
+                const int32_t y = sr.bcol[j];
+                if (y < Y) S[(int64_t)y * lds + x] += coef * v[sr.perm[j]];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ stage 2
+constexpr int kS2Threads = 256;
+constexpr int kS2PerWarp = 4;
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(kS2Threads)
+stage2_dense_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ S, int64_t lds,
+                    int64_t X, S2Outputs outs, T coef, T* __restrict__ u)
+{
+    constexpr int VEC = Vec<T>::N;
+    using VT = typename Vec<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (kS2Threads / 32) + (threadIdx.x >> 5);
+    const bool vec_ok = (lda % VEC == 0) && (lds % VEC == 0) && aligned16(A) && aligned16(S);
+    for (int o = 0; o < kS2PerWarp; ++o) {
+        const int64_t i = wid * kS2PerWarp + o;
+        if (i >= outs.n) return;
+        const T* arow = A + (int64_t)outs.arow[i] * lda;
+        const T* srow = S + (int64_t)outs.srow[i] * lds;
+        T acc = T(0);
+        if (vec_ok) {
+            const int64_t xv = (X / VEC) * VEC;
+            for (int64_t x = (int64_t)lane * VEC; x < xv; x += 32 * VEC) {
+                T a[VEC], s[VEC];
+                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(arow + x)), a);
+                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(srow + x)), s);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const T ak = MODE == FM_SQUARE ? a[k] * a[k] : a[k];
+                    acc = fma(ak, s[k], acc);
+                }
+            }
+            for (int64_t x = xv + lane; x < X; x += 32) {
+                const T ak = MODE == FM_SQUARE ? arow[x] * arow[x] : arow[x];
+                acc = fma(ak, srow[x], acc);
+            }
+        } else {
+            for (int64_t x = lane; x < X; x += 32) {
+                const T ak = MODE == FM_SQUARE ? arow[x] * arow[x] : arow[x];
+                acc = fma(ak, srow[x], acc);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) u[outs.perm[i]] += coef * acc;
+    }
+}
+
+template <class T>
+__global__ void stage2_identity_kernel(const T* __restrict__ S, int64_t lds, int64_t X,
+                                       S2Outputs outs, T coef, T* __restrict__ u)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < outs.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = outs.arow[i];
+        if (a < X) u[outs.perm[i]] += coef * S[(int64_t)outs.srow[i] * lds + a];
+    }
+}
+
+// ------------------------------------------------------------------ one-sided terms
+template <class T>
+__global__ void segment_sums_kernel(const int32_t* __restrict__ seg, const int32_t* __restrict__ perm,
+                                    int64_t K, const T* __restrict__ v, T coef, T* __restrict__ s)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < K;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        T acc = T(0);
+        for (int32_t j = seg[x]; j < seg[x + 1]; ++j) acc += v[perm[j]];
+        s[x] += coef * acc;
+    }
+}
+
+template <class T, int MODE>
+__global__ void gemv_rows_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
+                                 const T* __restrict__ s, T* __restrict__ z)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += nw) {
+        const T* row = F + r * ldf;
+        T acc = T(0);
+        for (int64_t x = lane; x < X; x += 32) {
+            const T f = MODE == FM_SQUARE ? row[x] * row[x] : row[x];
+            acc = fma(f, s[x], acc);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) z[r] = acc;
+    }
+}
+
+template <class T>
+__global__ void gather_add_kernel(const T* __restrict__ z, const int32_t* __restrict__ idx, int64_t n,
+                                  T* __restrict__ u)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += z[idx[i]];
+}
+
+template <class T>
+__global__ void transpose_kernel(const T* __restrict__ B, int64_t ldb, int64_t rows, int64_t cols,
+                                 T* __restrict__ Bt, int64_t ldt)
+{
+    __shared__ T tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = B[r * ldb + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) Bt[c * ldt + r] = tile[threadIdx.x][k];
+    }
+}
+
+template <class T>
+__global__ void zero_kernel(T* __restrict__ x, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = T(0);
+}
+
+template <class S, class D>
+__device__ inline D cvt(S x) { return (D)x; }
+template <> __device__ inline __nv_bfloat16 cvt<double, __nv_bfloat16>(double x) { return __double2bfloat16(x); }
+template <> __device__ inline __nv_bfloat16 cvt<float, __nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ inline double cvt<__nv_bfloat16, double>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+template <> __device__ inline float cvt<__nv_bfloat16, float>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <> __device__ inline __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 x) { return x; }
+
+template <class S, class D>
+__global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = cvt<S, D>(src[i]);
+}
+
+// Gaussian base kernel, FP64: a 32x32 output tile per block, features staged
+// through shared memory in chunks of 32 dimensions.
+template <class D>
+__global__ void gaussian_kernel_kernel(const double* __restrict__ X, int64_t rx,
+                                       const double* __restrict__ Y, int64_t ry, int64_t dim,
+                                       double gamma, D* __restrict__ K, int64_t ldk)
+{
+    __shared__ double xs[32][33];
+    __shared__ double ys[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int64_t a0 = (int64_t)blockIdx.y * 32, b0 = (int64_t)blockIdx.x * 32;
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t k0 = 0; k0 < dim; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t a = a0 + r, b = b0 + r, k = k0 + tx;
+            xs[r][tx] = (a < rx && k < dim) ? X[a * dim + k] : 0.0;
+            ys[r][tx] = (b < ry && k < dim) ? Y[b * dim + k] : 0.0;
+        }
+        __syncthreads();
+        const int kmax = (dim - k0 < 32) ? (int)(dim - k0) : 32;
+        for (int kk = 0; kk < kmax; ++kk) {
+            const double yv = ys[tx][kk];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const double d = xs[ty + 8 * i][kk] - yv;
+                acc[i] = fma(d, d, acc[i]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t a = a0 + ty + 8 * i, b = b0 + tx;
+        if (a < rx && b < ry) K[a * ldk + b] = cvt<double, D>(exp(-gamma * acc[i]));
+    }
+}
+
+}  // namespace
+
+size_t dtype_size(int dt)
+{
+    switch (dt) {
+    case GVT_F64: return 8;
+    case GVT_F32: return 4;
+    case GVT_BF16: return 2;
+    default: return 0;
+    }
+}
+
+template <class T>
+gvt_status stage1_dense(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
+                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s)
+{
+    if (Y <= 0 || X <= 0) return GVT_OK;
+    constexpr int VEC = Vec<T>::N;
+    const int64_t gy = (X + kS1Cols - 1) / kS1Cols;
+    if (gy > 65535) {
+        set_error("stage 1: too many columns");
+        return GVT_ERR_UNSUPPORTED;
+    }
+    dim3 grid((unsigned)((Y + kS1Threads * VEC - 1) / (kS1Threads * VEC)), (unsigned)gy);
+    if (mode == FM_SQUARE)
+        stage1_dense_kernel<T, FM_SQUARE><<<grid, kS1Threads, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+    else
+        stage1_dense_kernel<T, FM_DENSE><<<grid, kS1Threads, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+    GVT_LAUNCH_CHECK("stage1_dense");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status stage1_identity(const S1Sources& srcs, const T* v, T* S, int64_t lds, int64_t Y,
+                           int64_t X, cudaStream_t s)
+{
+    if (Y <= 0 || X <= 0) return GVT_OK;
+    stage1_identity_kernel<T><<<grid1d(X, 128), 128, 0, s>>>(srcs, v, S, lds, Y, X);
+    GVT_LAUNCH_CHECK("stage1_identity");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status stage2_dense(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
+                        const S2Outputs& outs, double coef, T* u, cudaStream_t s)
+{
+    if (outs.n <= 0) return GVT_OK;
+    const int64_t per_block = (kS2Threads / 32) * kS2PerWarp;
+    const int64_t g = (outs.n + per_block - 1) / per_block;
+    if (g > INT32_MAX) return GVT_ERR_UNSUPPORTED;
+    if (mode == FM_SQUARE)
+        stage2_dense_kernel<T, FM_SQUARE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
+    else
+        stage2_dense_kernel<T, FM_DENSE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
+    GVT_LAUNCH_CHECK("stage2_dense");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status stage2_identity(const T* S, int64_t lds, int64_t X, const S2Outputs& outs, double coef,
+                           T* u, cudaStream_t s)
+{
+    if (outs.n <= 0) return GVT_OK;
+    stage2_identity_kernel<T><<<grid1d(outs.n, 256), 256, 0, s>>>(S, lds, X, outs, (T)coef, u);
+    GVT_LAUNCH_CHECK("stage2_identity");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status segment_sums(const int32_t* seg, const int32_t* perm, int64_t K, const T* v, double coef,
+                        T* s_out, cudaStream_t s)
+{
+    if (K <= 0) return GVT_OK;
+    segment_sums_kernel<T><<<grid1d(K, 128), 128, 0, s>>>(seg, perm, K, v, (T)coef, s_out);
+    GVT_LAUNCH_CHECK("segment_sums");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status gemv_rows(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svec, T* z,
+                     cudaStream_t s)
+{
+    if (R <= 0) return GVT_OK;
+    const unsigned g = grid1d(R * 32, 256, 152 * 16);
+    if (mode == FM_SQUARE)
+        gemv_rows_kernel<T, FM_SQUARE><<<g, 256, 0, s>>>(F, ldf, R, X, svec, z);
+    else
+        gemv_rows_kernel<T, FM_DENSE><<<g, 256, 0, s>>>(F, ldf, R, X, svec, z);
+    GVT_LAUNCH_CHECK("gemv_rows");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status gather_add(const T* z, const int32_t* idx, int64_t n, T* u, cudaStream_t s)
+{
+    if (n <= 0) return GVT_OK;
+    gather_add_kernel<T><<<grid1d(n, 256), 256, 0, s>>>(z, idx, n, u);
+    GVT_LAUNCH_CHECK("gather_add");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status transpose(const T* B, int64_t ldb, int64_t rows, int64_t cols, T* Bt, int64_t ldt,
+                     cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) return GVT_OK;
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(B, ldb, rows, cols, Bt, ldt);
+    GVT_LAUNCH_CHECK("transpose");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status vec_zero(T* x, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return GVT_OK;
+    zero_kernel<T><<<grid1d(n, 256), 256, 0, s>>>(x, n);
+    GVT_LAUNCH_CHECK("zero");
+    return GVT_OK;
+}
+
+gvt_status convert(const void* src, int sdt, void* dst, int ddt, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return GVT_OK;
+    const unsigned g = grid1d(n, 256);
+#define GVT_CVT(ST, SD, DT, DD)                                                               \
+    if (sdt == SD && ddt == DD) {                                                             \
+        convert_kernel<ST, DT><<<g, 256, 0, s>>>(static_cast<const ST*>(src), static_cast<DT*>(dst), n); \
+        GVT_LAUNCH_CHECK("convert");                                                          \
+        return GVT_OK;                                                                        \
+    }
+    GVT_CVT(double, GVT_F64, double, GVT_F64)
+    GVT_CVT(double, GVT_F64, float, GVT_F32)
+    GVT_CVT(double, GVT_F64, __nv_bfloat16, GVT_BF16)
+    GVT_CVT(float, GVT_F32, double, GVT_F64)
+    GVT_CVT(float, GVT_F32, float, GVT_F32)
+    GVT_CVT(float, GVT_F32, __nv_bfloat16, GVT_BF16)
+    GVT_CVT(__nv_bfloat16, GVT_BF16, double, GVT_F64)
+    GVT_CVT(__nv_bfloat16, GVT_BF16, float, GVT_F32)
+    GVT_CVT(__nv_bfloat16, GVT_BF16, __nv_bfloat16, GVT_BF16)
+#undef GVT_CVT
+    set_error("convert: unsupported dtype pair");
+    return GVT_ERR_INVALID_ARG;
+}
+
+gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t ry, int64_t dim,
+                           double gamma, void* K, int64_t ldk, int dtype, cudaStream_t s)
+{
+    if (rx <= 0 || ry <= 0) return GVT_OK;
+    dim3 grid((unsigned)((ry + 31) / 32), (unsigned)((rx + 31) / 32));
+    dim3 block(32, 8);
+    switch (dtype) {
+    case GVT_F64:
+        gaussian_kernel_kernel<double><<<grid, block, 0, s>>>(X, rx, Y, ry, dim, gamma, (double*)K, ldk);
+        break;
+    case GVT_F32:
+        gaussian_kernel_kernel<float><<<grid, block, 0, s>>>(X, rx, Y, ry, dim, gamma, (float*)K, ldk);
+        break;
+    case GVT_BF16:
+        gaussian_kernel_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(X, rx, Y, ry, dim, gamma,
+                                                                    (__nv_bfloat16*)K, ldk);
+        break;
+    default:
+        set_error("gaussian_kernel: bad dtype");
+        return GVT_ERR_INVALID_ARG;
+    }
+    GVT_LAUNCH_CHECK("gaussian_kernel");
+    return GVT_OK;
+}
+
+#define GVT_INST(T)                                                                                 \
+    template gvt_status stage1_dense<T>(const T*, int64_t, int, const S1Sources&, const T*, T*,      \
+                                        int64_t, int64_t, int64_t, cudaStream_t);                   \
+    template gvt_status stage1_identity<T>(const S1Sources&, const T*, T*, int64_t, int64_t,        \
+                                           int64_t, cudaStream_t);                                  \
+    template gvt_status stage2_dense<T>(const T*, int64_t, int, const T*, int64_t, int64_t,          \
+                                        const S2Outputs&, double, T*, cudaStream_t);                \
+    template gvt_status stage2_identity<T>(const T*, int64_t, int64_t, const S2Outputs&, double, T*, \
+                                           cudaStream_t);                                           \
+    template gvt_status segment_sums<T>(const int32_t*, const int32_t*, int64_t, const T*, double,  \
+                                        T*, cudaStream_t);                                          \
+    template gvt_status gemv_rows<T>(const T*, int64_t, int, int64_t, int64_t, const T*, T*,         \
+                                     cudaStream_t);                                                 \
+    template gvt_status gather_add<T>(const T*, const int32_t*, int64_t, T*, cudaStream_t);         \
+    template gvt_status transpose<T>(const T*, int64_t, int64_t, int64_t, T*, int64_t,              \
+                                     cudaStream_t);                                                 \
+    template gvt_status vec_zero<T>(T*, int64_t, cudaStream_t);
+
+GVT_INST(float)
+GVT_INST(double)
+
+}  // namespace gvt

@@ -1,0 +1,352 @@
+"""Python binding of the C ABI in ``include/gvt.h`` (argument marshalling only).
+
+The raw functions carry the ABI names (``gvt_create``, ``gvt_plan_create``,
+``gvt_matvec``, ``gvt_pairwise_kernel_matvec``, ``gvt_krr_cg_solve``,
+``gvt_predict`` ...) and raise :class:`GvtError` on a non-zero status.  The
+small classes below (:class:`Handle`, :class:`Plan`) only turn torch tensors
+into device pointers and streams.  Every step of the computation runs in
+``libgvt.so``; there is no fallback: importing works without the library, the
+first call raises if it is missing.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+# ---------------------------------------------------------------- enums (gvt.h)
+GVT_OK = 0
+STATUS_NAMES = {0: "GVT_OK", 1: "GVT_ERR_INVALID_ARG", 2: "GVT_ERR_INDEX_OOB",
+                3: "GVT_ERR_UNSUPPORTED", 4: "GVT_ERR_ALLOC", 5: "GVT_ERR_CUDA",
+                6: "GVT_ERR_BREAKDOWN", 7: "GVT_ERR_NOT_CONVERGED", 8: "GVT_ERR_TIMEOUT"}
+GVT_F64, GVT_F32, GVT_BF16 = 0, 1, 2
+KERNELS = {"kronecker": 0, "gaussian": 1, "linear": 2, "poly2d": 3, "cartesian": 4,
+           "symmetric": 5, "antisymmetric": 6, "ranking": 7, "mlpk": 8}
+HOMOGENEOUS = {"symmetric", "antisymmetric", "ranking", "mlpk"}
+GVT_FACTOR_M, GVT_FACTOR_N, GVT_FACTOR_M_SQ, GVT_FACTOR_N_SQ, GVT_FACTOR_ONES, GVT_FACTOR_IDENTITY = range(6)
+GVT_FIRST, GVT_SECOND = 0, 1
+GVT_SOLVE_FP64_CG, GVT_SOLVE_MIXED_IR = 0, 1
+GVT_MAX_TERMS = 16
+
+
+class gvt_term(ctypes.Structure):
+    _fields_ = [("coef", c_dbl), ("factor_a", c_i32), ("factor_b", c_i32),
+                ("out_a", c_i32), ("out_b", c_i32), ("in_a", c_i32), ("in_b", c_i32)]
+
+
+class gvt_desc(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("n_terms", c_i32), ("homogeneous", c_i32),
+                ("reserved", c_i32), ("terms", gvt_term * GVT_MAX_TERMS)]
+
+
+class gvt_matrix(ctypes.Structure):
+    _fields_ = [("data", c_vp), ("rows", c_i64), ("cols", c_i64), ("ld", c_i64),
+                ("dtype", c_i32), ("symmetric", c_i32)]
+
+
+class gvt_solve_opts(ctypes.Structure):
+    _fields_ = [("rel_tol", c_dbl), ("max_iter", c_i64), ("mode", c_i32),
+                ("inner_dtype", c_i32), ("inner_tol", c_dbl), ("max_refine", c_i32),
+                ("check_every", c_i32)]
+
+
+class gvt_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", c_i64), ("refinements", c_i32), ("status", c_i32),
+                ("rel_residual", c_dbl), ("time_ms", c_dbl)]
+
+
+class gvt_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", c_i64), ("ms", c_dbl), ("flops", c_dbl), ("bytes", c_dbl)]
+
+
+GVT_STAT_STAGE1, GVT_STAT_STAGE2, GVT_STAT_ONE_SIDED, GVT_STAT_COUNT = 0, 1, 2, 3
+STAT_NAMES = ["stage1", "stage2", "one_sided"]
+
+
+class GvtError(RuntimeError):
+    def __init__(self, status, func, msg):
+        self.status = status
+        super().__init__("%s failed: %s (%s)" % (func, STATUS_NAMES.get(status, status), msg))
+
+
+# (name, restype, argtypes) of every entry point declared in include/gvt.h
+_P = ctypes.POINTER
+SIGNATURES = [
+    ("gvt_last_error", ctypes.c_char_p, []),
+    ("gvt_version", c_i32, []),
+    ("gvt_create", c_i32, [_P(c_vp)]),
+    ("gvt_destroy", c_i32, [c_vp]),
+    ("gvt_plan_create", c_i32, [c_vp, c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_i64,
+                                c_vp, c_vp, c_i64, c_vp, _P(c_vp)]),
+    ("gvt_plan_destroy", c_i32, [c_vp]),
+    ("gvt_plan_sizes", c_i32, [c_vp, _P(c_i64), _P(c_i64)]),
+    ("gvt_matvec", c_i32, [c_vp, _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp, c_i64, c_i32, c_vp]),
+    ("gvt_desc_make", c_i32, [c_i32, _P(gvt_desc)]),
+    ("gvt_pairwise_kernel_matvec", c_i32, [c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
+                                           c_vp, c_vp, c_i64, c_i32, c_vp]),
+    ("gvt_predict", c_i32, [c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
+                            c_i64, c_i32, c_vp]),
+    ("gvt_gaussian_kernel", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_dbl, c_vp, c_i64,
+                                    c_i32, c_vp]),
+    ("gvt_convert", c_i32, [c_vp, c_i32, c_vp, c_i32, c_i64, c_vp]),
+    ("gvt_solve_opts_default", c_i32, [_P(gvt_solve_opts)]),
+    ("gvt_stats_enable", c_i32, [c_vp, c_i32]),
+    ("gvt_stats_read", c_i32, [c_vp, c_vp]),
+    ("gvt_launch_count", c_i64, []),
+    ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
+                                 c_vp, c_dbl, c_vp, _P(gvt_solve_opts), _P(gvt_solve_info), c_vp]),
+]
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load():
+    """Load libgvt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libgvt.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_2009_01054_gb300.build)")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, res, args in SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def last_error():
+    return load().gvt_last_error().decode()
+
+
+def _call(name, *args):
+    st = getattr(load(), name)(*args)
+    if st != GVT_OK:
+        raise GvtError(st, name, last_error())
+    return st
+
+
+# ---------------------------------------------------------------- raw ABI calls
+def gvt_version():
+    return int(load().gvt_version())
+
+
+def gvt_create():
+    h = c_vp()
+    _call("gvt_create", ctypes.byref(h))
+    return h
+
+
+def gvt_destroy(h):
+    _call("gvt_destroy", h)
+
+
+def gvt_plan_create(h, m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t_out, n_out, stream):
+    p = c_vp()
+    _call("gvt_plan_create", h, m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in,
+          d_out, t_out, n_out, stream, ctypes.byref(p))
+    return p
+
+
+def gvt_plan_destroy(p):
+    _call("gvt_plan_destroy", p)
+
+
+def gvt_desc_make(kind):
+    d = gvt_desc()
+    _call("gvt_desc_make", KERNELS.get(kind, kind) if isinstance(kind, str) else kind, ctypes.byref(d))
+    return d
+
+
+def gvt_matvec(plan, M, N, v, u, k_cols, dtype, stream):
+    _call("gvt_matvec", plan, ctypes.byref(M), ctypes.byref(N), v, u, k_cols, dtype, stream)
+
+
+def gvt_pairwise_kernel_matvec(plan, desc, M, N, v, u, k_cols, dtype, stream):
+    _call("gvt_pairwise_kernel_matvec", plan, ctypes.byref(desc), ctypes.byref(M),
+          ctypes.byref(N) if N is not None else None, v, u, k_cols, dtype, stream)
+
+
+def gvt_predict(plan, desc, M, N, a, p, k_cols, dtype, stream):
+    _call("gvt_predict", plan, ctypes.byref(desc), ctypes.byref(M),
+          ctypes.byref(N) if N is not None else None, a, p, k_cols, dtype, stream)
+
+
+def gvt_gaussian_kernel(h, X, rows_x, Y, rows_y, dim, gamma, K, ldk, out_dtype, stream):
+    _call("gvt_gaussian_kernel", h, X, rows_x, Y, rows_y, dim, gamma, K, ldk, out_dtype, stream)
+
+
+def gvt_convert(src, src_dtype, dst, dst_dtype, n, stream):
+    _call("gvt_convert", src, src_dtype, dst, dst_dtype, n, stream)
+
+
+def gvt_stats_enable(h, on):
+    _call("gvt_stats_enable", h, 1 if on else 0)
+
+
+def gvt_stats_read(h):
+    """dict kind -> {launches, ms, flops, bytes}"""
+    arr = (gvt_kernel_stats * GVT_STAT_COUNT)()
+    _call("gvt_stats_read", h, ctypes.cast(arr, c_vp))
+    return {STAT_NAMES[k]: dict(launches=arr[k].launches, ms=arr[k].ms, flops=arr[k].flops,
+                                bytes=arr[k].bytes) for k in range(GVT_STAT_COUNT)}
+
+
+def gvt_launch_count():
+    return int(load().gvt_launch_count())
+
+
+def gvt_solve_opts_default():
+    o = gvt_solve_opts()
+    _call("gvt_solve_opts_default", ctypes.byref(o))
+    return o
+
+
+def gvt_krr_cg_solve(h, plan, desc, M, N, y, lam, a, opts, stream):
+    """Returns (status, gvt_solve_info); NOT_CONVERGED / BREAKDOWN are returned, not raised."""
+    info = gvt_solve_info()
+    st = load().gvt_krr_cg_solve(h, plan, ctypes.byref(desc), ctypes.byref(M),
+                                 ctypes.byref(N) if N is not None else None, y, lam, a,
+                                 ctypes.byref(opts), ctypes.byref(info), stream)
+    if st not in (GVT_OK, 6, 7):
+        raise GvtError(st, "gvt_krr_cg_solve", last_error())
+    return st, info
+
+
+# ---------------------------------------------------------------- torch marshalling
+def _torch():
+    import torch
+    return torch
+
+
+_DT = {"float64": GVT_F64, "float32": GVT_F32, "bfloat16": GVT_BF16}
+
+
+def dtype_code(t):
+    return _DT[str(t.dtype).replace("torch.", "")]
+
+
+def stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_vp(s.cuda_stream)
+
+
+def ptr(t):
+    return c_vp(t.data_ptr()) if t is not None and t.numel() > 0 else c_vp(t.data_ptr() if t is not None else 0)
+
+
+def matrix(t, symmetric=False):
+    """gvt_matrix view of a 2-D CUDA tensor with unit column stride."""
+    assert t.dim() == 2 and t.is_cuda and t.stride(1) == 1
+    return gvt_matrix(c_vp(t.data_ptr()), t.shape[0], t.shape[1], t.stride(0), dtype_code(t),
+                      1 if symmetric else 0)
+
+
+class Handle:
+    def __init__(self):
+        self.h = gvt_create()
+
+    def close(self):
+        if self.h is not None:
+            gvt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Sorted pair sample (gvt_plan_create).  d_out/t_out None = training plan."""
+
+    def __init__(self, handle, m_shape, q_shape, d_in, t_in, d_out=None, t_out=None, stream=None):
+        torch = _torch()
+        self.handle = handle
+        dev = torch.device("cuda")
+        self.d_in = torch.as_tensor(d_in, dtype=torch.int32, device=dev).contiguous()
+        self.t_in = torch.as_tensor(t_in, dtype=torch.int32, device=dev).contiguous()
+        self.n_in = self.d_in.numel()
+        if d_out is None:
+            do = to = c_vp(0)
+            self.n_out = self.n_in
+        else:
+            self.d_out = torch.as_tensor(d_out, dtype=torch.int32, device=dev).contiguous()
+            self.t_out = torch.as_tensor(t_out, dtype=torch.int32, device=dev).contiguous()
+            do, to = ptr(self.d_out), ptr(self.t_out)
+            self.n_out = self.d_out.numel()
+        self.p = gvt_plan_create(handle.h, m_shape[0], m_shape[1], q_shape[0], q_shape[1],
+                                 ptr(self.d_in), ptr(self.t_in), self.n_in, do, to, self.n_out,
+                                 stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "p", None) is not None:
+            gvt_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc(kind):
+    return kind if isinstance(kind, gvt_desc) else gvt_desc_make(kind)
+
+
+def pairwise_kernel_matvec(plan, kind, M, N, v, u=None, symmetric=True, stream=None, predict=False):
+    """u = R(dhat,that) K_kind R(d,t)^T v for CUDA tensors (v: n_in or n_in x k, column-major)."""
+    torch = _torch()
+    desc = _desc(kind)
+    vec = v.dim() == 1
+    k = 1 if vec else v.shape[1]
+    vv = v if vec else v.t().contiguous()          # column-major block
+    if u is None:
+        u = torch.empty((k, plan.n_out), dtype=v.dtype, device=v.device)
+    Mm = matrix(M, symmetric)
+    Nm = matrix(N, symmetric) if N is not None else None
+    fn = gvt_predict if predict else gvt_pairwise_kernel_matvec
+    fn(plan.p, desc, Mm, Nm, ptr(vv), ptr(u), k, dtype_code(v), stream_ptr(stream))
+    return u.reshape(-1) if vec else u.t()
+
+
+def predict(plan, kind, M, N, a, stream=None, symmetric=False):
+    return pairwise_kernel_matvec(plan, kind, M, N, a, symmetric=symmetric, stream=stream, predict=True)
+
+
+def gaussian_kernel(handle, X, Y=None, gamma=1.0, dtype=None, stream=None):
+    torch = _torch()
+    X = X.to(torch.float64).contiguous()
+    Y = X if Y is None else Y.to(torch.float64).contiguous()
+    out = torch.empty((X.shape[0], Y.shape[0]), dtype=dtype or torch.float64, device=X.device)
+    gvt_gaussian_kernel(handle.h, ptr(X), X.shape[0], ptr(Y), Y.shape[0], X.shape[1], float(gamma),
+                        ptr(out), out.stride(0), dtype_code(out), stream_ptr(stream))
+    return out
+
+
+def krr_cg_solve(handle, plan, kind, M, N, y, lam, a0=None, mode=GVT_SOLVE_FP64_CG, rel_tol=1e-6,
+                 max_iter=10000, inner_tol=1e-3, check_every=1, symmetric=True, stream=None):
+    """Solve (K + lam I) a = y; returns (a, status, info)."""
+    torch = _torch()
+    a = torch.zeros_like(y) if a0 is None else a0.clone()
+    o = gvt_solve_opts_default()
+    o.rel_tol, o.max_iter, o.mode, o.inner_tol, o.check_every = rel_tol, max_iter, mode, inner_tol, check_every
+    st, info = gvt_krr_cg_solve(handle.h, plan.p, _desc(kind), matrix(M, symmetric),
+                                matrix(N, symmetric) if N is not None else None,
+                                ptr(y), float(lam), ptr(a), o, stream_ptr(stream))
+    return a, st, info

@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (normwise, ||u - u*||_inf / ||u*||_inf): 1e-10 for FP64 results,
+1e-5 for FP32 results.  Inputs are the seeded synthetic workloads; both sides
+build their Gaussian base kernels from the same features.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2009_01054_gb300 import gvt, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-10, torch.float32: 1e-5}
+KINDS = list(gvt.KERNELS)
+DEV = "cuda"
+
+
+def normwise(u, ref):
+    u = np.asarray(u, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(u - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2009_01054_gb300 import build
+    build.build()
+    h = gvt.Handle()
+    yield h
+    h.close()
+
+
+def to_dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def gpu_gauss(H, X, gamma, dtype, Y=None):
+    return gvt.gaussian_kernel(H, to_dev(X), None if Y is None else to_dev(Y), gamma, dtype=dtype)
+
+
+def problem_kernels(H, p, dtype):
+    M = gpu_gauss(H, p.Xd, p.gamma, dtype)
+    N = M if p.homogeneous else gpu_gauss(H, p.Xt, p.gamma, dtype)
+    return M, N
+
+
+def oracle_kernels(p):
+    M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    N = M if p.homogeneous else orc.gaussian_kernel(p.Xt, gamma=p.gamma)
+    return M, N
+
+
+def run(H, kind, M, N, d_in, t_in, v, d_out=None, t_out=None, symmetric=True, m_shape=None, q_shape=None):
+    m_shape = m_shape or tuple(M.shape)
+    q_shape = q_shape or (tuple(M.shape) if N is None else tuple(N.shape))
+    plan = gvt.Plan(H, m_shape, q_shape, d_in, t_in, d_out, t_out)
+    u = gvt.pairwise_kernel_matvec(plan, kind, M, None if kind in gvt.HOMOGENEOUS else N,
+                                   to_dev(v, M.dtype), symmetric=symmetric)
+    torch.cuda.synchronize()
+    out = u.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+def test_gaussian_base_kernel(H):
+    p = synth.small(0)
+    Mg = gpu_gauss(H, p.Xd, p.gamma, torch.float64).cpu().numpy()
+    Mo = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    np.testing.assert_allclose(Mg, Mo, rtol=1e-13, atol=1e-15)
+    Xc = np.random.default_rng(1).standard_normal((33, 16))
+    Kc = gpu_gauss(H, p.Xd, p.gamma, torch.float64, Y=Xc).cpu().numpy()
+    np.testing.assert_allclose(Kc, orc.gaussian_kernel(p.Xd, Xc, gamma=p.gamma), rtol=1e-13, atol=1e-15)
+    K32 = gpu_gauss(H, p.Xd, p.gamma, torch.float32).cpu().numpy()
+    assert np.array_equal(K32, Mo.astype(np.float32)) or np.max(np.abs(K32 - Mo)) < 1e-7
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_kronecker_small_train_and_predict(H, dtype):
+    p = synth.small(0)
+    M, N = problem_kernels(H, p, dtype)
+    Mo, No = oracle_kernels(p)
+    u = run(H, "kronecker", M, N, p.d, p.t, p.v)
+    ref = orc.pairwise_matvec("kronecker", Mo, No, p.d, p.t, p.d, p.t, p.v)
+    assert normwise(u, ref) <= TOL[dtype]
+    up = run(H, "kronecker", M, N, p.d, p.t, p.v, p.d_pred, p.t_pred)
+    refp = orc.pairwise_matvec("kronecker", Mo, No, p.d_pred, p.t_pred, p.d, p.t, p.v)
+    assert normwise(up, refp) <= TOL[dtype]
+
+
+def _mixed_problem(kind, seed=5, m=150, q=70, n=3000, n_out=1700):
+    rng = np.random.default_rng(seed)
+    q = m if kind in gvt.HOMOGENEOUS else q
+    Xd = rng.standard_normal((m, 8))
+    Xt = Xd if kind in gvt.HOMOGENEOUS else rng.standard_normal((q, 8))
+    d, t = synth.random_pairs(rng, n, m, q)
+    do, to = synth.random_pairs(rng, n_out, m, q)
+    v = rng.standard_normal(n)
+    return Xd, Xt, d, t, do, to, v, 1.0 / 8
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("kind", KINDS)
+def test_every_kernel_small_ragged(H, kind, dtype):
+    """Ragged shapes (150 x 70 ids, 3000 pairs with repeats), prediction pairs != training pairs."""
+    Xd, Xt, d, t, do, to, v, g = _mixed_problem(kind)
+    M = gpu_gauss(H, Xd, g, dtype)
+    N = gpu_gauss(H, Xt, g, dtype)
+    Mo = orc.gaussian_kernel(Xd, gamma=g)
+    No = orc.gaussian_kernel(Xt, gamma=g)
+    u = run(H, kind, M, N, d, t, v, do, to)
+    ref = orc.pairwise_matvec(kind, Mo, No, do, to, d, t, v)
+    assert normwise(u, ref) <= TOL[dtype], kind
+    ut = run(H, kind, M, N, d, t, v)
+    reft = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, v)
+    assert normwise(ut, reft) <= TOL[dtype], kind
+
+
+def test_multiple_columns(H):
+    Xd, Xt, d, t, do, to, v, g = _mixed_problem("poly2d", n=1000, n_out=600)
+    V = np.random.default_rng(3).standard_normal((1000, 3))
+    M = gpu_gauss(H, Xd, g, torch.float64)
+    N = gpu_gauss(H, Xt, g, torch.float64)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t, do, to)
+    U = gvt.pairwise_kernel_matvec(plan, "poly2d", M, N, to_dev(V)).cpu().numpy()
+    ref = orc.pairwise_matvec("poly2d", orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g),
+                              do, to, d, t, V)
+    assert normwise(U, ref) <= 1e-10
+
+
+def test_cross_kernel_prediction_nonsymmetric(H):
+    """Rectangular cross kernels (new drugs and targets, Setting 4) exercise the transpose path."""
+    rng = np.random.default_rng(8)
+    Xd, Xt = rng.standard_normal((90, 6)), rng.standard_normal((40, 6))
+    Xd2, Xt2 = rng.standard_normal((25, 6)), rng.standard_normal((17, 6))
+    g = 1.0 / 6
+    d, t = synth.random_pairs(rng, 700, 90, 40)
+    do, to = synth.random_pairs(rng, 300, 25, 17)
+    v = rng.standard_normal(700)
+    for kind in ["kronecker", "linear", "poly2d"]:
+        Mx = gpu_gauss(H, Xd2, g, torch.float64, Y=Xd)
+        Nx = gpu_gauss(H, Xt2, g, torch.float64, Y=Xt)
+        plan = gvt.Plan(H, (25, 90), (17, 40), d, t, do, to)
+        u = gvt.predict(plan, kind, Mx, Nx, to_dev(v)).cpu().numpy()
+        ref = orc.pairwise_matvec(kind, orc.gaussian_kernel(Xd2, Xd, gamma=g),
+                                  orc.gaussian_kernel(Xt2, Xt, gamma=g), do, to, d, t, v)
+        assert normwise(u, ref) <= 1e-10, kind
+
+
+def test_edge_cases(H):
+    rng = np.random.default_rng(9)
+    m, q = 37, 29
+    Xd, Xt = rng.standard_normal((m, 4)), rng.standard_normal((q, 4))
+    M = gpu_gauss(H, Xd, 0.25, torch.float64)
+    N = gpu_gauss(H, Xt, 0.25, torch.float64)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=0.25), orc.gaussian_kernel(Xt, gamma=0.25)
+    # no input pairs: u = 0
+    do, to = synth.random_pairs(rng, 10, m, q)
+    u = run(H, "kronecker", M, N, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0), do, to)
+    assert np.all(u == 0) and u.shape == (10,)
+    # one pair
+    u = run(H, "mlpk", M, None, np.array([3], np.int32), np.array([5], np.int32), np.array([2.0]),
+            np.array([1, 5], np.int32), np.array([2, 3], np.int32), m_shape=(m, m), q_shape=(m, m))
+    ref = orc.pairwise_matvec("mlpk", Mo, None, [1, 5], [2, 3], [3], [5], [2.0])
+    assert normwise(u, ref) <= 1e-10
+    # every pair in one drug column (one long segment), 33 outputs (ragged warp tail)
+    d = np.zeros(5000, np.int32)
+    t = rng.integers(0, q, 5000).astype(np.int32)
+    v = rng.standard_normal(5000)
+    do, to = synth.random_pairs(rng, 33, m, q)
+    for kind in ["kronecker", "cartesian", "linear"]:
+        u = run(H, kind, M, N, d, t, v, do, to)
+        ref = orc.pairwise_matvec(kind, Mo, No, do, to, d, t, v)
+        assert normwise(u, ref) <= 1e-10, kind
+
+
+def test_index_out_of_bounds_is_rejected(H):
+    d = torch.tensor([0, 4, 2], dtype=torch.int32, device=DEV)
+    t = torch.tensor([1, 1, 3], dtype=torch.int32, device=DEV)
+    with pytest.raises(gvt.GvtError) as e:
+        gvt.Plan(H, (4, 4), (5, 5), d, t)
+    assert e.value.status == 2 and "d_in" in str(e.value)
+    with pytest.raises(gvt.GvtError) as e:
+        gvt.Plan(H, (4, 4), (5, 5), t, t, torch.tensor([0], dtype=torch.int32, device=DEV),
+                 torch.tensor([-1], dtype=torch.int32, device=DEV))
+    assert e.value.status == 2
+
+
+def test_results_are_bitwise_reproducible(H):
+    Xd, Xt, d, t, do, to, v, g = _mixed_problem("mlpk", n=4000)
+    M = gpu_gauss(H, Xd, g, torch.float32)
+    u1 = run(H, "mlpk", M, None, d, t, v, do, to)
+    u2 = run(H, "mlpk", M, None, d, t, v, do, to)
+    assert np.array_equal(u1, u2)
+
+
+@pytest.mark.slow
+def test_full_size_homogeneous_all_kernels_sampled(H):
+    """m = q = 2000, n = 200k (the benchmark workload), FP32 on the GPU, 256 sampled outputs
+    checked against the FP64 oracle (each against all 200k inputs)."""
+    p = synth.homogeneous(0)
+    M = gpu_gauss(H, p.Xd, p.gamma, torch.float32)
+    Mo = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
+    v = to_dev(p.v, torch.float32)
+    idx = np.random.default_rng(0).choice(p.n, 256, replace=False)
+    for kind in KINDS:
+        u = gvt.pairwise_kernel_matvec(plan, kind, M, M, v).double().cpu().numpy()
+        ref = orc.pairwise_matvec(kind, Mo, Mo, p.d[idx], p.t[idx], p.d, p.t, p.v.astype(np.float32))
+        assert normwise(u[idx], ref) <= 1e-5, kind
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", ["kronecker", "symmetric", "poly2d"])
+@pytest.mark.parametrize("mode", [gvt.GVT_SOLVE_FP64_CG, gvt.GVT_SOLVE_MIXED_IR])
+def test_krr_solve_small_matches_cholesky(H, kind, mode):
+    p = synth.small(0) if kind not in gvt.HOMOGENEOUS else synth.homogeneous(0, m=64, n=1000)
+    M, N = problem_kernels(H, p, torch.float64)
+    Mo, No = oracle_kernels(p)
+    lam = 1e-2
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    a, st, info = gvt.krr_cg_solve(H, plan, kind, M, N, to_dev(p.y), lam, mode=mode, rel_tol=1e-8)
+    assert st == 0, (st, info.iterations)
+    a = a.cpu().numpy()
+    K = orc.kernel_matrix(kind, Mo, No, p.d, p.t, p.d, p.t)
+    a_ref = orc.krr_solve_dense(K, p.y, lam)
+    mv = lambda x: orc.pairwise_matvec(kind, Mo, No, p.d, p.t, p.d, p.t, x)
+    assert orc.relative_residual(mv, a, p.y, lam) <= 1e-8 * 1.01 + 1e-12
+    assert info.rel_residual <= 1e-8
+    assert normwise(a, a_ref) <= 1e-5   # (K + lam I)^-1 amplifies the 1e-8 residual
+    plan.close()
+
+
+def test_solve_then_predict(H):
+    p = synth.small(0)
+    M, N = problem_kernels(H, p, torch.float64)
+    Mo, No = oracle_kernels(p)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, to_dev(p.y), 1e-2)
+    assert st == 0 and info.rel_residual <= 1e-6
+    pp = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t, p.d_pred, p.t_pred)
+    pred = gvt.predict(pp, "kronecker", M, N, a, symmetric=True).cpu().numpy()
+    ref = orc.pairwise_matvec("kronecker", Mo, No, p.d_pred, p.t_pred, p.d, p.t, a.cpu().numpy())
+    assert normwise(pred, ref) <= 1e-10
+
+
+def test_solve_reports_not_converged_and_warm_start_resumes(H):
+    p = synth.small(0)
+    M, N = problem_kernels(H, p, torch.float64)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    y = to_dev(p.y)
+    a5, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, 1e-3, max_iter=5)
+    assert st == 7 and info.iterations == 5
+    a, st, info2 = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, 1e-3, a0=a5)
+    assert st == 0 and info2.rel_residual <= 1e-6
