@@ -299,6 +299,49 @@ gvt_status gvt_stats_read(gvt_handle* h, gvt_kernel_stats* out);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t gvt_launch_count(void);
 
+/* ------------------------------------------------------- allocation-free product */
+
+/* Bytes of the fixed device scratch array behind gvt_matvec_static. */
+#define GVT_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/*
+ * u = R(dhat,that) (M kron N) R(d,t)^T v, like gvt_matvec, for callers that
+ * cannot allocate device memory: programs whose framework owns all device
+ * memory through its own pool, or latency-bound loops that may not call
+ * cudaMalloc / cudaFree (they can synchronise the device).  The paper has no
+ * counterpart; this is a deployment variant of the Theorem 1 product.
+ *
+ * It needs no handle and no plan and calls no allocating routine.  Its only
+ * scratch (one error word and the q_rows x m_cols intermediate S of the
+ * two-stage product) lives in a static __device__ array of
+ * GVT_STATIC_SCRATCH_BYTES bytes, which every device that loads the library
+ * holds until the process exits.  Requests with
+ * q_rows * m_cols * element size > GVT_STATIC_SCRATCH_BYTES - 256 return
+ * GVT_ERR_INVALID_ARG without launching anything.
+ *
+ *  - Arguments as for gvt_plan_create + gvt_matvec (device index arrays,
+ *    d_out = t_out = NULL for the training operator), one column, dtype
+ *    GVT_F64 or GVT_F32.  A symmetric N lets stage 1 read rows instead of
+ *    columns.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call clears the parts of the array it uses; the array keeps the
+ *    last call's contents otherwise.  All calls share the one array, so calls
+ *    whose work overlaps on the GPU (different streams, other host threads)
+ *    race and give wrong results: serialise them.
+ *  - Stage 1 accumulates with atomic adds, so the summation order (and the
+ *    last bits of u) can differ from gvt_matvec and between calls.
+ *  - Indices are checked inside the kernels; pairs outside the kernel
+ *    matrices are skipped and reported as GVT_ERR_INDEX_OOB.  The call
+ *    synchronises `stream` to read that check.
+ */
+gvt_status gvt_matvec_static(int64_t m_rows, int64_t m_cols, int64_t q_rows, int64_t q_cols,
+                             const int32_t* d_in, const int32_t* t_in, int64_t n_in,
+                             const int32_t* d_out, const int32_t* t_out, int64_t n_out,
+                             const gvt_matrix* M, const gvt_matrix* N, const void* v, void* u,
+                             int32_t dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,8 @@ SIGNATURES = [
     ("gvt_launch_count", c_i64, []),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
                                  c_vp, c_dbl, c_vp, _P(gvt_solve_opts), _P(gvt_solve_info), c_vp]),
+    ("gvt_matvec_static", c_i32, [c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
+                                  _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp, c_i32, c_vp]),
 ]
 
 _lib = None
@@ -200,6 +202,13 @@ def gvt_stats_read(h):
 
 def gvt_launch_count():
     return int(load().gvt_launch_count())
+
+
+def gvt_matvec_static(m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t_out, n_out,
+                      M, N, v, u, dtype, stream):
+    """Allocation-free Kronecker product (see include/gvt.h); raises on a non-zero status."""
+    _call("gvt_matvec_static", m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t_out,
+          n_out, ctypes.byref(M), ctypes.byref(N), v, u, dtype, stream)
 
 
 def gvt_solve_opts_default():
