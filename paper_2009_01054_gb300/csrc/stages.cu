@@ -13,6 +13,8 @@
 // A row in L1; 16-byte vector loads of both rows.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "gvt_internal.h"
 
 namespace gvt {
@@ -43,59 +45,114 @@ unsigned grid1d(int64_t n, int threads, int64_t cap = 152 * 32)
 }
 
 // ------------------------------------------------------------------ stage 1
-constexpr int kS1Threads = 128;
-constexpr int kS1Cols = 8;
+// Tile: blockDim = NT threads, each owning RPT consecutive rows y (RPT/VEC
+// 16-byte loads per entry), and kS1Cols consecutive columns x of S.  The
+// entries of the tile's columns are contiguous in every sorted source; they
+// are staged in shared memory as (row offset of B^T, weight) records, which
+// every warp reads with one broadcast load per entry.
+constexpr int kS1Cols = 4;
+constexpr int kS1Chunk = 512;     // staged entries per round
 
-template <class T, int MODE>
-__global__ void __launch_bounds__(kS1Threads)
+template <class T>
+struct S1Entry {
+    int64_t off;   // bcol * ldb
+    T w;           // coef * v[perm]
+};
+
+template <class T, int MODE, int NT, int RPT>
+__global__ void __launch_bounds__(NT)
 stage1_dense_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
                     const T* __restrict__ v, T* __restrict__ S, int64_t lds, int64_t Y, int64_t X)
 {
     constexpr int VEC = Vec<T>::N;
+    constexpr int NV = RPT / VEC;
+    constexpr int U = 4;   // entries in flight per thread
     using VT = typename Vec<T>::type;
-    const int lane = threadIdx.x & 31;
-    const int64_t y0 = (int64_t)blockIdx.x * (kS1Threads * VEC) + (int64_t)threadIdx.x * VEC;
-    const int64_t x0 = (int64_t)blockIdx.y * kS1Cols;
-    const bool vec_rows = (y0 + VEC <= Y) && (ldb % VEC == 0) && aligned16(Bt);
+    __shared__ S1Entry<T> ent[kS1Chunk];
+    __shared__ int32_t sseg[kMaxSources][kS1Cols + 1];
 
-    T acc[VEC][kS1Cols];
+    const int64_t y0 = (int64_t)blockIdx.x * (NT * RPT) + (int64_t)threadIdx.x * RPT;
+    const int64_t x0 = (int64_t)blockIdx.y * kS1Cols;
+    const bool vec_rows = (y0 + RPT <= Y) && (ldb % VEC == 0) && aligned16(Bt);
+    const T* __restrict__ by = Bt + y0;
+
+    if (threadIdx.x < kMaxSources * (kS1Cols + 1)) {
+        const int si = threadIdx.x / (kS1Cols + 1), c = threadIdx.x % (kS1Cols + 1);
+        if (si < srcs.count) {
+            const int64_t x = min(x0 + c, X);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k)
+            for (int k = 0; k < kMaxSources; ++k)
+                if (k == si) sseg[si][c] = srcs.src[k].seg[x];
+        }
+    }
+
+    T acc[RPT][kS1Cols];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
 #pragma unroll
         for (int c = 0; c < kS1Cols; ++c) acc[k][c] = T(0);
 
 #pragma unroll
-    for (int c = 0; c < kS1Cols; ++c) {
-        const int64_t x = x0 + c;
-        if (x >= X) break;
-        for (int si = 0; si < srcs.count; ++si) {
-            const S1Source& sr = srcs.src[si];
-            const int32_t beg = sr.seg[x], end = sr.seg[x + 1];
-            const T coef = (T)sr.coef;
-            for (int32_t j0 = beg; j0 < end; j0 += 32) {
-                const int32_t j = j0 + lane;
-                int32_t t = 0;
-                T w = T(0);
-                if (j < end) {
-                    t = sr.bcol[j];
-                    w = coef * v[sr.perm[j]];
-                }
-                const int cnt = min(32, end - j0);
-                for (int jj = 0; jj < cnt; ++jj) {
-                    const int32_t tt = __shfl_sync(0xffffffffu, t, jj);
-                    const T ww = __shfl_sync(0xffffffffu, w, jj);
-                    const T* brow = Bt + (int64_t)tt * ldb + y0;
-                    T b[VEC];
-                    if (vec_rows) {
-                        Vec<T>::split(__ldg(reinterpret_cast<const VT*>(brow)), b);
-                    } else {
+    for (int si = 0; si < kMaxSources; ++si) {
+        if (si >= srcs.count) break;
+        const S1Source& sr = srcs.src[si];
+        const T coef = (T)sr.coef;
+        __syncthreads();
+        const int32_t jb = sseg[si][0], je = sseg[si][kS1Cols];
+        for (int32_t j0 = jb; j0 < je; j0 += kS1Chunk) {
+            __syncthreads();   // the previous round's records are consumed
+            for (int k = threadIdx.x; k < kS1Chunk && j0 + k < je; k += NT) {
+                const int32_t j = j0 + k;
+                ent[k].off = (int64_t)sr.bcol[j] * ldb;
+                ent[k].w = coef * v[sr.perm[j]];
+            }
+            __syncthreads();
 #pragma unroll
-                        for (int k = 0; k < VEC; ++k) b[k] = (y0 + k < Y) ? __ldg(brow + k) : T(0);
+            for (int c = 0; c < kS1Cols; ++c) {
+                const int lo = max(sseg[si][c], j0) - j0;
+                const int hi = min(sseg[si][c + 1], j0 + kS1Chunk) - j0;
+                int k = lo;
+                for (; k + U <= hi; k += U) {
+                    T b[U][RPT];
+                    T w[U];
+#pragma unroll
+                    for (int e = 0; e < U; ++e) {
+                        const S1Entry<T> r = ent[k + e];
+                        w[e] = r.w;
+                        const T* row = by + r.off;
+                        if (vec_rows) {
+#pragma unroll
+                            for (int q = 0; q < NV; ++q)
+                                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(row) + q), &b[e][q * VEC]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < RPT; ++q) b[e][q] = (y0 + q < Y) ? __ldg(row + q) : T(0);
+                        }
                     }
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) {
-                        const T bk = MODE == FM_SQUARE ? b[k] * b[k] : b[k];
-                        acc[k][c] = fma(ww, bk, acc[k][c]);
+                    for (int e = 0; e < U; ++e)
+#pragma unroll
+                        for (int q = 0; q < RPT; ++q) {
+                            const T bq = MODE == FM_SQUARE ? b[e][q] * b[e][q] : b[e][q];
+                            acc[q][c] = fma(w[e], bq, acc[q][c]);
+                        }
+                }
+                for (; k < hi; ++k) {
+                    const S1Entry<T> r = ent[k];
+                    const T* row = by + r.off;
+                    T b[RPT];
+                    if (vec_rows) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q)
+                            Vec<T>::split(__ldg(reinterpret_cast<const VT*>(row) + q), &b[q * VEC]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < RPT; ++q) b[q] = (y0 + q < Y) ? __ldg(row + q) : T(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) {
+                        const T bq = MODE == FM_SQUARE ? b[q] * b[q] : b[q];
+                        acc[q][c] = fma(r.w, bq, acc[q][c]);
                     }
                 }
             }
@@ -104,18 +161,18 @@ stage1_dense_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
 
     const bool vec_cols = (x0 + kS1Cols <= X) && (lds % VEC == 0) && aligned16(S) && (x0 % VEC == 0);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        const int64_t y = y0 + k;
+    for (int q = 0; q < RPT; ++q) {
+        const int64_t y = y0 + q;
         if (y >= Y) break;
         T* srow = S + y * lds + x0;
         if (vec_cols) {
 #pragma unroll
             for (int c = 0; c < kS1Cols; c += VEC)
-                *reinterpret_cast<VT*>(srow + c) = Vec<T>::make(&acc[k][c]);
+                *reinterpret_cast<VT*>(srow + c) = Vec<T>::make(&acc[q][c]);
         } else {
 #pragma unroll
             for (int c = 0; c < kS1Cols; ++c)
-                if (x0 + c < X) srow[c] = acc[k][c];
+                if (x0 + c < X) srow[c] = acc[q][c];
         }
     }
 }
@@ -139,49 +196,96 @@ __global__ void stage1_identity_kernel(S1Sources srcs, const T* __restrict__ v, 
 
 // ------------------------------------------------------------------ stage 2
 constexpr int kS2Threads = 256;
-constexpr int kS2PerWarp = 4;
+constexpr int kS2Group = 4;      // outputs per warp, processed together
 
+// A warp takes kS2Group consecutive outputs (sorted by A row).  When they
+// share their A row -- the common case, every A row serves ~n/m outputs --
+// each chunk of the A row is loaded once for the whole group, so a group
+// costs 1 + kS2Group row loads per chunk instead of 2 * kS2Group.
 template <class T, int MODE>
 __global__ void __launch_bounds__(kS2Threads)
 stage2_dense_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ S, int64_t lds,
                     int64_t X, S2Outputs outs, T coef, T* __restrict__ u)
 {
     constexpr int VEC = Vec<T>::N;
+    constexpr int G = kS2Group;
     using VT = typename Vec<T>::type;
     const int lane = threadIdx.x & 31;
-    const int64_t wid = (int64_t)blockIdx.x * (kS2Threads / 32) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (kS2Threads / 32);
     const bool vec_ok = (lda % VEC == 0) && (lds % VEC == 0) && aligned16(A) && aligned16(S);
-    for (int o = 0; o < kS2PerWarp; ++o) {
-        const int64_t i = wid * kS2PerWarp + o;
-        if (i >= outs.n) return;
-        const T* arow = A + (int64_t)outs.arow[i] * lda;
-        const T* srow = S + (int64_t)outs.srow[i] * lds;
-        T acc = T(0);
-        if (vec_ok) {
-            const int64_t xv = (X / VEC) * VEC;
+    const int64_t xv = vec_ok ? (X / VEC) * VEC : 0;
+    for (int64_t grp = (int64_t)blockIdx.x * (kS2Threads / 32) + (threadIdx.x >> 5);
+         grp * G < outs.n; grp += nwarps) {
+        const int64_t i0 = grp * G;
+        const int ng = (outs.n - i0 < G) ? (int)(outs.n - i0) : G;
+        int32_t ar = 0, sr = 0, pm = 0;
+        if (lane < ng) {
+            ar = outs.arow[i0 + lane];
+            sr = outs.srow[i0 + lane];
+            pm = outs.perm[i0 + lane];
+        }
+        const int32_t ar0 = __shfl_sync(0xffffffffu, ar, 0);
+        const bool same = __all_sync(0xffffffffu, lane >= ng || ar == ar0);
+        const T* arow[G];
+        const T* srow[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            // groups shorter than G repeat their last output; only real ones are written
+            const int gg = g < ng ? g : ng - 1;
+            arow[g] = A + (int64_t)__shfl_sync(0xffffffffu, ar, gg) * lda;
+            srow[g] = S + (int64_t)__shfl_sync(0xffffffffu, sr, gg) * lds;
+        }
+        T acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = T(0);
+        if (same) {
             for (int64_t x = (int64_t)lane * VEC; x < xv; x += 32 * VEC) {
-                T a[VEC], s[VEC];
-                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(arow + x)), a);
-                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(srow + x)), s);
+                T a[VEC], sv[G][VEC];
+                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(arow[0] + x)), a);
+#pragma unroll
+                for (int g = 0; g < G; ++g) Vec<T>::split(__ldg(reinterpret_cast<const VT*>(srow[g] + x)), sv[g]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     const T ak = MODE == FM_SQUARE ? a[k] * a[k] : a[k];
-                    acc = fma(ak, s[k], acc);
+#pragma unroll
+                    for (int g = 0; g < G; ++g) acc[g] = fma(ak, sv[g][k], acc[g]);
                 }
             }
-            for (int64_t x = xv + lane; x < X; x += 32) {
-                const T ak = MODE == FM_SQUARE ? arow[x] * arow[x] : arow[x];
-                acc = fma(ak, srow[x], acc);
-            }
         } else {
-            for (int64_t x = lane; x < X; x += 32) {
-                const T ak = MODE == FM_SQUARE ? arow[x] * arow[x] : arow[x];
-                acc = fma(ak, srow[x], acc);
+            for (int64_t x = (int64_t)lane * VEC; x < xv; x += 32 * VEC) {
+                T a[G][VEC], sv[G][VEC];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    Vec<T>::split(__ldg(reinterpret_cast<const VT*>(arow[g] + x)), a[g]);
+                    Vec<T>::split(__ldg(reinterpret_cast<const VT*>(srow[g] + x)), sv[g]);
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        const T ak = MODE == FM_SQUARE ? a[g][k] * a[g][k] : a[g][k];
+                        acc[g] = fma(ak, sv[g][k], acc[g]);
+                    }
+            }
+        }
+        for (int64_t x = xv + lane; x < X; x += 32) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const T ak = MODE == FM_SQUARE ? arow[g][x] * arow[g][x] : arow[g][x];
+                acc[g] = fma(ak, srow[g][x], acc[g]);
             }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) u[outs.perm[i]] += coef * acc;
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
+        if (lane < ng) {
+            T mine = acc[0];
+#pragma unroll
+            for (int g = 1; g < G; ++g)
+                if (lane == g) mine = acc[g];
+            u[pm] += coef * mine;
+        }
     }
 }
 
@@ -197,15 +301,19 @@ __global__ void stage2_identity_kernel(const T* __restrict__ S, int64_t lds, int
 }
 
 // ------------------------------------------------------------------ one-sided terms
+// one warp per segment
 template <class T>
 __global__ void segment_sums_kernel(const int32_t* __restrict__ seg, const int32_t* __restrict__ perm,
                                     int64_t K, const T* __restrict__ v, T coef, T* __restrict__ s)
 {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < K;
-         x += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); x < K; x += nw) {
         T acc = T(0);
-        for (int32_t j = seg[x]; j < seg[x + 1]; ++j) acc += v[perm[j]];
-        s[x] += coef * acc;
+        for (int32_t j = seg[x] + lane; j < seg[x + 1]; j += 32) acc += v[perm[j]];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) s[x] += coef * acc;
     }
 }
 
@@ -327,22 +435,36 @@ size_t dtype_size(int dt)
     }
 }
 
+template <class T, int NT, int RPT>
+static void launch_stage1(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v, T* S,
+                          int64_t lds, int64_t Y, int64_t X, int64_t gy, cudaStream_t s)
+{
+    dim3 grid((unsigned)((Y + NT * RPT - 1) / (NT * RPT)), (unsigned)gy);
+    if (mode == FM_SQUARE)
+        stage1_dense_kernel<T, FM_SQUARE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+    else
+        stage1_dense_kernel<T, FM_DENSE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+}
+
 template <class T>
 gvt_status stage1_dense(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
                         T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s)
 {
     if (Y <= 0 || X <= 0) return GVT_OK;
-    constexpr int VEC = Vec<T>::N;
     const int64_t gy = (X + kS1Cols - 1) / kS1Cols;
     if (gy > 65535) {
         set_error("stage 1: too many columns");
         return GVT_ERR_UNSUPPORTED;
     }
-    dim3 grid((unsigned)((Y + kS1Threads * VEC - 1) / (kS1Threads * VEC)), (unsigned)gy);
-    if (mode == FM_SQUARE)
-        stage1_dense_kernel<T, FM_SQUARE><<<grid, kS1Threads, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
-    else
-        stage1_dense_kernel<T, FM_DENSE><<<grid, kS1Threads, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+    // rows per block: 1024 (128 x 8) for tall S, 256 (64 x 4) for short S (FP64: 512 / 128)
+    constexpr bool f32 = sizeof(T) == 4;
+    if (Y >= 768) {
+        if (f32) launch_stage1<T, 128, 8>(Bt, ldb, mode, srcs, v, S, lds, Y, X, gy, s);
+        else launch_stage1<T, 128, 4>(Bt, ldb, mode, srcs, v, S, lds, Y, X, gy, s);
+    } else {
+        if (f32) launch_stage1<T, 64, 4>(Bt, ldb, mode, srcs, v, S, lds, Y, X, gy, s);
+        else launch_stage1<T, 64, 2>(Bt, ldb, mode, srcs, v, S, lds, Y, X, gy, s);
+    }
     GVT_LAUNCH_CHECK("stage1_dense");
     return GVT_OK;
 }
@@ -362,9 +484,8 @@ gvt_status stage2_dense(const T* A, int64_t lda, int mode, const T* S, int64_t l
                         const S2Outputs& outs, double coef, T* u, cudaStream_t s)
 {
     if (outs.n <= 0) return GVT_OK;
-    const int64_t per_block = (kS2Threads / 32) * kS2PerWarp;
-    const int64_t g = (outs.n + per_block - 1) / per_block;
-    if (g > INT32_MAX) return GVT_ERR_UNSUPPORTED;
+    const int64_t groups = (outs.n + kS2Group - 1) / kS2Group;
+    const int64_t g = std::min<int64_t>((groups + (kS2Threads / 32) - 1) / (kS2Threads / 32), 152 * 64);
     if (mode == FM_SQUARE)
         stage2_dense_kernel<T, FM_SQUARE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
     else
@@ -388,7 +509,7 @@ gvt_status segment_sums(const int32_t* seg, const int32_t* perm, int64_t K, cons
                         T* s_out, cudaStream_t s)
 {
     if (K <= 0) return GVT_OK;
-    segment_sums_kernel<T><<<grid1d(K, 128), 128, 0, s>>>(seg, perm, K, v, (T)coef, s_out);
+    segment_sums_kernel<T><<<grid1d(K * 32, 256), 256, 0, s>>>(seg, perm, K, v, (T)coef, s_out);
     GVT_LAUNCH_CHECK("segment_sums");
     return GVT_OK;
 }

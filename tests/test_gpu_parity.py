@@ -255,3 +255,19 @@ def test_solve_reports_not_converged_and_warm_start_resumes(H):
     assert st == 7 and info.iterations == 5
     a, st, info2 = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, 1e-3, a0=a5)
     assert st == 0 and info2.rel_residual <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("kind", ["kronecker", "poly2d", "symmetric", "mlpk", "cartesian"])
+def test_tall_tiles_medium(H, kind, dtype):
+    """m = q = 900 ids (stage-1 tiles of 1024 rows, partly empty), 20k pairs, every output checked."""
+    rng = np.random.default_rng(17)
+    m = 900
+    X = rng.standard_normal((m, 10))
+    d, t = synth.random_pairs(rng, 20000, m, m)
+    v = rng.standard_normal(20000)
+    M = gpu_gauss(H, X, 0.1, dtype)
+    Mo = orc.gaussian_kernel(X, gamma=0.1)
+    u = run(H, kind, M, M, d, t, v)
+    ref = orc.pairwise_matvec(kind, Mo, Mo, d, t, d, t, v)
+    assert normwise(u, ref) <= TOL[dtype], kind
