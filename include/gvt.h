@@ -222,6 +222,39 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x,
                                double gamma, void* K, int64_t ldk, int32_t out_dtype,
                                void* stream);
 
+/*
+ * Engine of stage 1 for FP32 products of dense x dense terms.
+ *  GVT_STAGE1_SIMT      : sparse scatter-accumulate over the sorted pairs (default).
+ *  GVT_STAGE1_TC_BF16X3 : W is densified and S = B W runs as a tcgen05 BF16 GEMM
+ *                         on hi/lo splits of both operands (hi*hi + hi*lo + lo*hi,
+ *                         each product accurate to ~1e-5 relative, FP32
+ *                         accumulation); the stage ordering then minimises the
+ *                         stage-2 length.  Worth it when W is dense (n / (q m)
+ *                         above a few percent).  Stage 2 stays FP32.
+ * Affects later products made with plans of this handle; FP64 products ignore it.
+ */
+typedef enum gvt_stage1_engine {
+    GVT_STAGE1_SIMT = 0,
+    GVT_STAGE1_TC_BF16X3 = 1
+} gvt_stage1_engine;
+
+gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine);
+
+/* Synchronise the device and report (then clear) errors recorded by device
+ * code of this handle: GVT_ERR_TIMEOUT when a bounded wait in a tensor-core
+ * kernel expired. */
+gvt_status gvt_check_device_errors(gvt_handle* h, void* stream);
+
+/*
+ * The tensor-core GEMM behind GVT_STAGE1_TC_BF16X3, exposed for testing:
+ * C[M x N] = A[M x K] B[N x K]^T with A, B BF16 row-major (K innermost,
+ * K a multiple of 64, lda and ldb multiples of 8, 16-byte aligned), C FP32
+ * row-major with leading dimension ldc >= N.  Asynchronous; device-side
+ * timeouts are reported by gvt_check_device_errors.
+ */
+gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                            int64_t ldc, int64_t M, int64_t N, int64_t K, void* stream);
+
 /* Convert n elements between dtypes (device to device, round to nearest). */
 gvt_status gvt_convert(const void* src, int32_t src_dtype, void* dst, int32_t dst_dtype,
                        int64_t n, void* stream);
@@ -237,7 +270,8 @@ typedef struct gvt_solve_opts {
     double rel_tol;          /* target ||y - (K + lambda I) a||_2 / ||y||_2 (default 1e-6) */
     int64_t max_iter;        /* total CG iterations, inner ones included (default 10000) */
     int32_t mode;            /* gvt_solve_mode (default GVT_SOLVE_FP64_CG) */
-    int32_t inner_dtype;     /* MIXED_IR inner operator dtype: GVT_F32 (default) */
+    int32_t inner_dtype;     /* MIXED_IR inner operator: GVT_F32 (default, SIMT stages) or
+                                GVT_BF16 (FP32 CG with the GVT_STAGE1_TC_BF16X3 stage 1) */
     double inner_tol;        /* MIXED_IR inner relative tolerance (default 1e-3) */
     int32_t max_refine;      /* MIXED_IR outer steps (default 30) */
     int32_t check_every;     /* CG iterations between host convergence checks (default 1) */

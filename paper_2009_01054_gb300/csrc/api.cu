@@ -205,8 +205,11 @@ gvt_status gvt_create(gvt_handle** out)
         set_error("gvt_create: host allocation failed");
         return GVT_ERR_ALLOC;
     }
-    if (h->status.reserve(256, nullptr) != GVT_OK) {
+    if (h->status.reserve(256, nullptr) != GVT_OK || cudaMemset(h->status.ptr, 0, h->status.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h->status.release();
         delete h;
+        set_error("gvt_create: device status buffer allocation failed");
         return GVT_ERR_ALLOC;
     }
     if (cudaMallocHost(&h->host_scalars, 64 * sizeof(double)) != cudaSuccess) {
@@ -477,6 +480,45 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x, c
         return GVT_ERR_UNSUPPORTED;
     }
     return gaussian_kernel(X, rows_x, Y, rows_y, dim, gamma, K, ldk, out_dtype, as_stream(stream));
+}
+
+gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine)
+{
+    if (!h || (engine != GVT_STAGE1_SIMT && engine != GVT_STAGE1_TC_BF16X3)) {
+        set_error("gvt_set_stage1_engine: bad handle or engine");
+        return GVT_ERR_INVALID_ARG;
+    }
+    h->stage1_engine = engine;
+    return GVT_OK;
+}
+
+gvt_status gvt_check_device_errors(gvt_handle* h, void* stream)
+{
+    if (!h) {
+        set_error("gvt_check_device_errors: handle is NULL");
+        return GVT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = as_stream(stream);
+    int word = 0;
+    GVT_CUDA(cudaMemcpyAsync(&word, handle_err_word(h), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GVT_CUDA(cudaStreamSynchronize(s));
+    if (word != 0) {
+        GVT_CUDA(cudaMemsetAsync(handle_err_word(h), 0, sizeof(int), s));
+        GVT_CUDA(cudaStreamSynchronize(s));
+        set_error("a bounded wait in a tensor-core kernel expired; its results are invalid");
+        return (gvt_status)word;
+    }
+    return GVT_OK;
+}
+
+gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                            int64_t ldc, int64_t M, int64_t N, int64_t K, void* stream)
+{
+    if (!h || (M > 0 && N > 0 && (!A || !B || !C))) {
+        set_error("gvt_tc_gemm_bf16: NULL argument");
+        return GVT_ERR_INVALID_ARG;
+    }
+    return tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, handle_err_word(h), as_stream(stream));
 }
 
 gvt_status gvt_convert(const void* src, int32_t src_dtype, void* dst, int32_t dst_dtype, int64_t n,

@@ -74,6 +74,7 @@ struct gvt_handle {
     gvt::DevBuf status;     // device status words
     double* host_scalars = nullptr;  // pinned
     bool stats_on = false;
+    int stage1_engine = 0;          // gvt_stage1_engine for FP32 products
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;
 };
@@ -205,6 +206,18 @@ gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t
                            double gamma, void* K, int64_t ldk, int dtype, cudaStream_t s);
 
 size_t dtype_size(int dt);
+
+// ---------------------------------------------------------------- tensor-core stage 1
+// Device error word of a handle (bounded waits in tensor-core kernels report here).
+inline int* handle_err_word(gvt_handle* h) { return static_cast<int*>(h->status.ptr) + 16; }
+// C[M x N] (FP32, ld ldc) = A[M x K] B[N x K]^T, A and B BF16 K-major (K % 64 == 0).
+gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                        int64_t N, int64_t K, int* err, cudaStream_t s);
+size_t dense_stage1_workspace(int64_t Y, int64_t K, int64_t X);
+// S[Y x X] = B[Y x K] W with W densified from the sources (keys[si][j] = column x of entry j)
+gvt_status dense_stage1(const float* B, int64_t ldb, int64_t Y, int64_t K, int square, const S1Sources& srcs,
+                        const int32_t* const keys[kMaxSources], int64_t n, const float* v, int64_t X, float* S,
+                        int64_t lds, void* ws, int* err, cudaStream_t s);
 
 // ---------------------------------------------------------------- pairwise driver
 // u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).

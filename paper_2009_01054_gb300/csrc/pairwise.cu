@@ -46,7 +46,7 @@ struct Compiled {
 int64_t out_range(const gvt_plan* p, int c) { return c == GVT_FIRST ? p->m_rows : p->q_rows; }
 int64_t in_range(const gvt_plan* p, int c) { return c == GVT_FIRST ? p->m_cols : p->q_cols; }
 
-gvt_status compile(const gvt_plan* p, const gvt_desc* d, const gvt_matrix* mats[2], Compiled& out)
+gvt_status compile(const gvt_plan* p, const gvt_desc* d, const gvt_matrix* mats[2], bool tc, Compiled& out)
 {
     if (d->n_terms < 1 || d->n_terms > GVT_MAX_TERMS) {
         set_error("descriptor: n_terms out of range");
@@ -102,8 +102,12 @@ gvt_status compile(const gvt_plan* p, const gvt_desc* d, const gvt_matrix* mats[
         if (is_dense(t.factor_a) && is_dense(t.factor_b)) {
             const gvt_matrix* A = mats[base_matrix(t.factor_a, homo)];
             const gvt_matrix* B = mats[base_matrix(t.factor_b, homo)];
-            const double c1 = (double)out_range(p, t.out_b) * p->n_in + (double)in_range(p, t.in_a) * p->n_out;
-            const double c2 = (double)out_range(p, t.out_a) * p->n_in + (double)in_range(p, t.in_b) * p->n_out;
+            double c1 = (double)out_range(p, t.out_b) * p->n_in + (double)in_range(p, t.in_a) * p->n_out;
+            double c2 = (double)out_range(p, t.out_a) * p->n_in + (double)in_range(p, t.in_b) * p->n_out;
+            if (tc) {   // stage 1 on tensor cores is cheap: minimise the stage-2 length instead
+                c1 = (double)in_range(p, t.in_a) * p->n_out;
+                c2 = (double)in_range(p, t.in_b) * p->n_out;
+            }
             (void)A; (void)B;
             if (c2 < c1) {
                 std::swap(t.factor_a, t.factor_b);
@@ -170,10 +174,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
 {
     const bool homo = desc->homogeneous != 0;
     const gvt_matrix* mats[2] = {M, homo ? M : N};
-    Compiled C;
-    GVT_CHECK(compile(plan, desc, mats, C));
-
     gvt_handle* h = plan->h;
+    const bool tc = sizeof(T) == 4 && h->stage1_engine == GVT_STAGE1_TC_BF16X3;
+    Compiled C;
+    GVT_CHECK(compile(plan, desc, mats, tc, C));
+
     const int64_t n_out = plan->n_out;
 
     // ---- workspace layout
@@ -204,6 +209,15 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         one_elems = std::max(one_elems, F->cols + F->rows);
     }
     const size_t off_one = one_elems > 0 ? ws.take(sizeof(T) * (size_t)one_elems) : 0;
+    size_t tc_bytes = 0;
+    if (tc)
+        for (auto& g : C.two)
+            if (is_dense(g.fa) && is_dense(g.fb)) {
+                const int ib = g.recipe.begin()->first.second;
+                const int64_t X = in_range(plan, g.recipe.begin()->first.first);
+                tc_bytes = std::max(tc_bytes, dense_stage1_workspace(out_range(plan, g.ob), in_range(plan, ib), X));
+            }
+    const size_t off_tc = tc_bytes > 0 ? ws.take(tc_bytes) : 0;
     GVT_CHECK(ws.commit(s));
     char* base = ws.base();
 
@@ -249,7 +263,22 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         }
         const double E = (double)srcs.count * (double)plan->n_in;
         const double sz = (double)sizeof(T);
-        if (g.fb == GVT_FACTOR_IDENTITY) {
+        bool same_ib = true;   // every source's W row ids share one id range (the K of the GEMM)
+        for (auto& r : g.recipe)
+            same_ib = same_ib && in_range(plan, r.first.second) == in_range(plan, g.recipe.begin()->first.second);
+        if (tc && is_dense(g.fa) && is_dense(g.fb) && same_ib) {
+            const int ib = g.recipe.begin()->first.second;
+            const gvt_matrix* Bm = mats[base_matrix(g.fb, homo)];
+            const int32_t* keys[kMaxSources] = {nullptr, nullptr, nullptr, nullptr};
+            int k = 0;
+            for (auto& r : g.recipe) keys[k++] = plan->in_by[r.first.first].key;
+            const int64_t K = in_range(plan, ib);
+            StatScope st(h, s, GVT_STAT_STAGE1, 2.0 * 3.0 * Y * (double)((K + 63) / 64 * 64) * X,
+                         2.0 * (3.0 * (Y + X) * ((K + 63) / 64 * 64)) + sz * Y * X + E * (8 + sz));
+            GVT_CHECK(dense_stage1(reinterpret_cast<const float*>(Bm->data), Bm->ld, Y, K, sq_mode(g.fb), srcs, keys,
+                                   plan->n_in, reinterpret_cast<const float*>(v), X, reinterpret_cast<float*>(S), lds,
+                                   base + off_tc, handle_err_word(h), s));
+        } else if (g.fb == GVT_FACTOR_IDENTITY) {
             GVT_CHECK(vec_zero<T>(S, Y * lds, s));
             StatScope st(h, s, GVT_STAT_STAGE1, E, sz * Y * X + E * (8 + sz));
             GVT_CHECK(stage1_identity<T>(srcs, v, S, lds, Y, X, s));

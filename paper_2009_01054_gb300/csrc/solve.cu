@@ -278,8 +278,8 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         set_error("gvt_krr_cg_solve: unknown mode");
         return ret(GVT_ERR_INVALID_ARG);
     }
-    if (opts.mode == GVT_SOLVE_MIXED_IR && opts.inner_dtype != GVT_F32) {
-        set_error("gvt_krr_cg_solve: MIXED_IR supports an FP32 inner operator");
+    if (opts.mode == GVT_SOLVE_MIXED_IR && opts.inner_dtype != GVT_F32 && opts.inner_dtype != GVT_BF16) {
+        set_error("gvt_krr_cg_solve: MIXED_IR inner operator must be GVT_F32 or GVT_BF16");
         return ret(GVT_ERR_UNSUPPORTED);
     }
     const int64_t n = plan->n_in;
@@ -391,8 +391,23 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         double rel = 1.0;
         // the inner solve only needs to reach the outer target relative to ||r||
         const double inner_tol = std::max(opts.inner_tol, 0.5 * opts.rel_tol * ynorm / rn);
+        const int saved_engine = plan->h->stage1_engine;
+        if (opts.inner_dtype == GVT_BF16) plan->h->stage1_engine = GVT_STAGE1_TC_BF16X3;
         st = cg_run<float, float>(plan, desc, &M32, &N32, r32, 1.0, lambda, c32, q32, p32, w32, part, sc,
                                   hsc, inner_tol, opts.max_iter - total, opts.check_every, &its, &rel, s);
+        plan->h->stage1_engine = saved_engine;
+        if (opts.inner_dtype == GVT_BF16) {
+            int word = 0;
+            if (cudaMemcpyAsync(&word, handle_err_word(plan->h), sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return ret(cuda_fail(cudaGetLastError(), "device error word"));
+            if (word) {
+                cudaMemsetAsync(handle_err_word(plan->h), 0, sizeof(int), s);
+                set_error("a bounded wait in the tensor-core stage 1 expired");
+                info->iterations = total + its;
+                return ret(GVT_ERR_TIMEOUT);
+            }
+        }
         total += its;
         if (st == GVT_ERR_BREAKDOWN) {
             info->iterations = total;

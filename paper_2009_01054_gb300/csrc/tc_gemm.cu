@@ -1,0 +1,390 @@
+// Dense stage 1 on the 5th-generation tensor cores.
+//
+// A BF16 GEMM  C[M x N] (FP32) = A[M x K] * B[N x K]^T  with both operands
+// K-major (row-major with K innermost).  One CTA computes a 128 x BN tile of
+// C (optionally one K slice of it, reduced with atomic adds):
+//   warp 0, one thread : TMA producer -- cp.async.bulk.tensor 2-D loads of
+//                        128 x 64 (A) and BN x 64 (B) tiles, 128-byte swizzle,
+//                        into a TC_STAGES-deep ring, completion on mbarriers;
+//   warp 1, one thread : MMA issuer -- tcgen05.mma kind::f16 (BF16 in, FP32
+//                        accumulate in TMEM), K = 16 per instruction, then
+//                        tcgen05.commit to free the ring slot;
+//   all 4 warps        : epilogue -- tcgen05.ld 32x32b from TMEM (warp w owns
+//                        accumulator rows 32w..32w+31) and stores to C.
+// Every wait on an mbarrier is bounded by a clock budget; on expiry the
+// thread records GVT_ERR_TIMEOUT in a device error word, the kernel waits
+// (bounded) for the copies it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "gvt_internal.h"
+
+namespace gvt {
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;            // BF16 elements in one 128-byte swizzle row
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 128;
+constexpr long long TC_TIMEOUT_CYCLES = 4000000000ll;   // about 2 s at 2 GHz
+
+struct TcShared {
+    uint64_t full[TC_STAGES];
+    uint64_t empty[TC_STAGES];
+    uint64_t done;
+    uint32_t tmem_base;
+    int timeout;
+    int issued;      // TMA stage loads issued
+    int consumed;    // stage loads the MMA thread has waited for
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > TC_TIMEOUT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 x BF16 -> FP32
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once every tcgen05 operation issued so far by this thread completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
+// layout written by TMA: rows of 128 bytes, 8-row (1024-byte) swizzle atoms
+// stacked along M/N.  Fields: start address >> 4 (bits 0-13), leading byte
+// offset >> 4 (bits 16-29, unused for this layout), stride byte offset >> 4
+// (bits 32-45) = 1024 B between 8-row groups, descriptor version 1 (bits
+// 46-47), base offset 0 (tiles are 1024-byte aligned), layout type
+// SWIZZLE_128B = 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
+// A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_bf16_f32()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+template <int BN>
+constexpr size_t tc_smem_bytes()
+{
+    return (size_t)TC_STAGES * (TC_BM + BN) * TC_BK * 2 + sizeof(TcShared) + 1024;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               float* __restrict__ C, int64_t ldc, int M, int N, int kb_total, int kb_per_split,
+               int atomic_out, int* __restrict__ err)
+{
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+    constexpr int A_BYTES = TC_BM * TC_BK * 2;
+    constexpr int B_BYTES = BN * TC_BK * 2;
+    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment of the shared-space offset (swizzle atoms, descriptor base offset 0)
+    unsigned char* tiles = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    TcShared* sh = reinterpret_cast<TcShared*>(tiles + TC_STAGES * STAGE_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    const int kb0 = blockIdx.z * kb_per_split;
+    const int kb1 = min(kb_total, kb0 + kb_per_split);
+    const int nkb = kb1 - kb0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        mbar_init(&sh->done, 1);
+        sh->timeout = 0;
+        sh->issued = 0;
+        sh->consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc(&sh->tmem_base, BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int i = 0;
+        for (; i < nkb; ++i) {
+            const int s = i % TC_STAGES;
+            if (i >= TC_STAGES && !mbar_wait(&sh->empty[s], ((i / TC_STAGES) - 1) & 1)) {
+                atomicExch(&sh->timeout, 1);
+                break;
+            }
+            if (*(volatile int*)&sh->timeout) break;
+            unsigned char* sa = tiles + s * STAGE_BYTES;
+            mbar_expect_tx(&sh->full[s], STAGE_BYTES);
+            const int kx = (kb0 + i) * TC_BK;
+            tma_load_2d(sa, &mapA, &sh->full[s], kx, m0);
+            tma_load_2d(sa + A_BYTES, &mapB, &sh->full[s], kx, n0);
+        }
+        sh->issued = i;
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16_f32<BN>();
+        int i = 0;
+        for (; i < nkb; ++i) {
+            const int s = i % TC_STAGES;
+            if (!mbar_wait(&sh->full[s], (i / TC_STAGES) & 1)) {
+                atomicExch(&sh->timeout, 1);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(tiles + s * STAGE_BYTES);
+            const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sa + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)   // +32 bytes along K per instruction
+                umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(&sh->empty[s]);
+        }
+        sh->consumed = i;
+        umma_commit(&sh->done);
+    }
+    __syncwarp();
+
+    // ---- epilogue: TMEM -> registers -> C
+    const bool ok = mbar_wait(&sh->done, 0);
+    tc_fence_after();
+    __syncthreads();
+    const bool good = ok && sh->timeout == 0 && nkb > 0;
+    const int gm = m0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(trow + (uint32_t)c, r);
+        tmem_ld_wait();
+        if (good && gm < M) {
+            float* crow = C + (int64_t)gm * ldc + n0 + c;
+            const int lim = min(16, N - (n0 + c));
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                if (e < lim) {
+                    const float f = __uint_as_float(r[e]);
+                    if (atomic_out) atomicAdd(crow + e, f);
+                    else crow[e] = f;
+                }
+            }
+        }
+    }
+
+    if (threadIdx.x == 0 && (!ok || sh->timeout)) {
+        atomicExch(err, (int)GVT_ERR_TIMEOUT);
+        // wait (bounded) for the tile copies that were issued but never consumed
+        for (int i = sh->consumed; i < sh->issued; ++i)
+            if (!mbar_wait(&sh->full[i % TC_STAGES], (i / TC_STAGES) & 1)) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+__global__ void zero_rows_kernel(float* __restrict__ C, int64_t ldc, int64_t M, int64_t N)
+{
+    const int64_t total = M * N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        C[(i / N) * ldc + (i % N)] = 0.f;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+cudaError_t g_encode_err = cudaSuccess;
+
+gvt_status get_encode()
+{
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        g_encode_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (g_encode_err == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return GVT_ERR_CUDA;
+    }
+    return GVT_OK;
+}
+
+gvt_status make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int64_t ld, int box_rows)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+        return GVT_ERR_CUDA;
+    }
+    return GVT_OK;
+}
+
+template <int BN>
+gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M, int64_t N,
+                     int64_t K, int* err, cudaStream_t s)
+{
+    const int gx = (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
+    const int kb_total = (int)(K / TC_BK);
+    const int tiles = gx * gy;
+    int splits = (148 + tiles - 1) / tiles;
+    splits = std::max(1, std::min(splits, kb_total / 4));
+    const int kb_per = (kb_total + splits - 1) / splits;
+    splits = (kb_total + kb_per - 1) / kb_per;
+    const int atomic_out = splits > 1 ? 1 : 0;
+    if (atomic_out) {
+        zero_rows_kernel<<<152 * 4, 256, 0, s>>>(C, ldc, M, N);
+        GVT_LAUNCH_CHECK("tc zero");
+    }
+    const size_t smem = tc_smem_bytes<BN>();
+    GVT_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(gx, gy, splits);
+    tc_gemm_kernel<BN><<<grid, TC_THREADS, smem, s>>>(ma, mb, C, ldc, (int)M, (int)N, kb_total, kb_per,
+                                                       atomic_out, err);
+    GVT_LAUNCH_CHECK("tc_gemm");
+    return GVT_OK;
+}
+
+}  // namespace
+
+gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                        int64_t N, int64_t K, int* err, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return GVT_OK;
+    if (K <= 0 || K % TC_BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N ||
+        ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M > INT32_MAX || N > INT32_MAX || K / TC_BK > INT32_MAX) {
+        set_error("tc_gemm_bf16: K must be a positive multiple of 64, lda/ldb multiples of 8, "
+                  "A and B 16-byte aligned");
+        return GVT_ERR_INVALID_ARG;
+    }
+    if ((M + TC_BM - 1) / TC_BM > 2147483647ll || (N + 63) / 64 > 65535) {
+        set_error("tc_gemm_bf16: matrix too large");
+        return GVT_ERR_UNSUPPORTED;
+    }
+    GVT_CHECK(get_encode());
+    const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+    CUtensorMap ma, mb;
+    GVT_CHECK(make_map(&ma, A, M, K, lda, TC_BM));
+    GVT_CHECK(make_map(&mb, B, N, K, ldb, BN));
+    if (BN == 64) return launch_tc<64>(ma, mb, C, ldc, M, N, K, err, s);
+    if (BN == 128) return launch_tc<128>(ma, mb, C, ldc, M, N, K, err, s);
+    return launch_tc<256>(ma, mb, C, ldc, M, N, K, err, s);
+}
+
+}  // namespace gvt

@@ -27,6 +27,7 @@ HOMOGENEOUS = {"symmetric", "antisymmetric", "ranking", "mlpk"}
 GVT_FACTOR_M, GVT_FACTOR_N, GVT_FACTOR_M_SQ, GVT_FACTOR_N_SQ, GVT_FACTOR_ONES, GVT_FACTOR_IDENTITY = range(6)
 GVT_FIRST, GVT_SECOND = 0, 1
 GVT_SOLVE_FP64_CG, GVT_SOLVE_MIXED_IR = 0, 1
+GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3 = 0, 1
 GVT_MAX_TERMS = 16
 
 
@@ -96,6 +97,9 @@ SIGNATURES = [
     ("gvt_launch_count", c_i64, []),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
                                  c_vp, c_dbl, c_vp, _P(gvt_solve_opts), _P(gvt_solve_info), c_vp]),
+    ("gvt_set_stage1_engine", c_i32, [c_vp, c_i32]),
+    ("gvt_check_device_errors", c_i32, [c_vp, c_vp]),
+    ("gvt_tc_gemm_bf16", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]),
     ("gvt_matvec_static", c_i32, [c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
                                   _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp, c_i32, c_vp]),
 ]
@@ -209,6 +213,18 @@ def gvt_matvec_static(m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t
     """Allocation-free Kronecker product (see include/gvt.h); raises on a non-zero status."""
     _call("gvt_matvec_static", m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t_out,
           n_out, ctypes.byref(M), ctypes.byref(N), v, u, dtype, stream)
+
+
+def gvt_set_stage1_engine(h, engine):
+    _call("gvt_set_stage1_engine", h, engine)
+
+
+def gvt_check_device_errors(h, stream):
+    _call("gvt_check_device_errors", h, stream)
+
+
+def gvt_tc_gemm_bf16(h, A, lda, B, ldb, C, ldc, M, N, K, stream):
+    _call("gvt_tc_gemm_bf16", h, A, lda, B, ldb, C, ldc, M, N, K, stream)
 
 
 def gvt_solve_opts_default():
@@ -349,12 +365,14 @@ def gaussian_kernel(handle, X, Y=None, gamma=1.0, dtype=None, stream=None):
 
 
 def krr_cg_solve(handle, plan, kind, M, N, y, lam, a0=None, mode=GVT_SOLVE_FP64_CG, rel_tol=1e-6,
-                 max_iter=10000, inner_tol=1e-3, check_every=1, symmetric=True, stream=None):
+                 max_iter=10000, inner_tol=1e-3, check_every=1, symmetric=True, stream=None,
+                 inner_dtype=GVT_F32):
     """Solve (K + lam I) a = y; returns (a, status, info)."""
     torch = _torch()
     a = torch.zeros_like(y) if a0 is None else a0.clone()
     o = gvt_solve_opts_default()
     o.rel_tol, o.max_iter, o.mode, o.inner_tol, o.check_every = rel_tol, max_iter, mode, inner_tol, check_every
+    o.inner_dtype = inner_dtype
     st, info = gvt_krr_cg_solve(handle.h, plan.p, _desc(kind), matrix(M, symmetric),
                                 matrix(N, symmetric) if N is not None else None,
                                 ptr(y), float(lam), ptr(a), o, stream_ptr(stream))

@@ -1,0 +1,104 @@
+"""Tensor-core dense stage 1 (tcgen05 BF16 GEMM on hi/lo splits) against references.
+
+* the raw GEMM C = A B^T on BF16 inputs against an FP64 product of the same
+  BF16 values (tolerance 1e-5 of max |C|: FP32 accumulation);
+* the Kronecker / poly2d products with GVT_STAGE1_TC_BF16X3 against the FP64
+  oracle: each product of hi/lo splits is accurate to 3 * 2^-18 relative, so
+  the normwise error is bounded by 1.2e-5 * sum|terms| / |u|; the test
+  asserts 1e-4 and prints the measured error;
+* a mixed-precision solve whose inner operator uses the tensor cores reaches
+  the FP64 relative residual 1e-6 checked by the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2009_01054_gb300 import gvt, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2009_01054_gb300 import build
+    build.build()
+    h = gvt.Handle()
+    yield h
+    h.close()
+
+
+def normwise(u, ref):
+    return float(np.max(np.abs(u - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (129, 17, 64), (300, 250, 192), (2000, 250, 6144),
+                                   (1000, 1000, 1024), (37, 300, 128)])
+def test_tc_gemm_bf16(H, M, N, K):
+    g = torch.Generator(device=DEV).manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g, device=DEV).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g, device=DEV).to(torch.bfloat16)
+    C = torch.full((M, N + 3), 7.0, device=DEV)           # ldc > N: padding must stay untouched
+    gvt.gvt_tc_gemm_bf16(H.h, gvt.ptr(A), K, gvt.ptr(B), K, gvt.ptr(C), N + 3, M, N, K, gvt.stream_ptr())
+    gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+    ref = (A.double() @ B.double().T).cpu().numpy()
+    c = C.cpu().numpy()
+    assert np.all(c[:, N:] == 7.0)
+    err = np.max(np.abs(c[:, :N] - ref)) / np.max(np.abs(ref))
+    assert err <= 1e-5, err
+
+
+def _problem(seed=3, m=300, q=80, dim=12, rho=0.25):
+    rng = np.random.default_rng(seed)
+    Xd, Xt = rng.standard_normal((m, dim)), rng.standard_normal((q, dim))
+    n = int(rho * m * q)
+    cells = rng.choice(m * q, n, replace=False)
+    d, t = (cells // q).astype(np.int32), (cells % q).astype(np.int32)
+    return Xd, Xt, d, t, rng.standard_normal(n), 1.0 / dim
+
+
+@pytest.mark.parametrize("kind", ["kronecker", "poly2d", "symmetric", "mlpk"])
+def test_tc_engine_pairwise_parity(H, kind):
+    Xd, Xt, d, t, v, g = _problem()
+    if kind in gvt.HOMOGENEOUS:
+        Xt = Xd
+        rng = np.random.default_rng(5)
+        d, t = synth.random_pairs(rng, 12000, Xd.shape[0], Xd.shape[0])
+        v = rng.standard_normal(len(d))
+    M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=g, dtype=torch.float32)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=g, dtype=torch.float32)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t)
+    vv = torch.as_tensor(v, dtype=torch.float32, device=DEV)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_TC_BF16X3)
+    try:
+        u = gvt.pairwise_kernel_matvec(plan, kind, M, N, vv).double().cpu().numpy()
+        gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    u32 = gvt.pairwise_kernel_matvec(plan, kind, M, N, vv).double().cpu().numpy()
+    ref = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, v.astype(np.float32))
+    err = normwise(u, ref)
+    print("%s: tensor-core stage 1 error vs FP64 %.2e (FP32 SIMT %.2e)" % (kind, err, normwise(u32, ref)))
+    assert err <= 1e-4
+    plan.close()
+
+
+def test_mixed_ir_with_tensor_core_inner_operator(H):
+    Xd, Xt, d, t, v, g = _problem(seed=4)
+    y = np.random.default_rng(6).standard_normal(len(d))
+    M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=g)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=g)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t)
+    lam = 1e-1
+    a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, torch.as_tensor(y, device=DEV), lam,
+                                   mode=gvt.GVT_SOLVE_MIXED_IR, inner_dtype=gvt.GVT_BF16)
+    assert st == 0, (st, info.iterations, info.refinements, info.rel_residual)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g)
+    mv = lambda x: orc.pairwise_matvec("kronecker", Mo, No, d, t, d, t, x)
+    rr = orc.relative_residual(mv, a.cpu().numpy(), y, lam)
+    print("bf16x3 inner: %d inner iterations, %d refinements, oracle residual %.2e"
+          % (info.iterations, info.refinements, rr))
+    assert rr <= 1.05e-6
+    plan.close()
