@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--engine", default="simt", choices=["simt", "tc"],
+                    help="stage-1 engine of the FP32 products: sparse SIMT, or tcgen05 BF16x3 on densified W")
+    ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     return ap.parse_args()
 
 
@@ -235,6 +238,8 @@ def run_gvt(args, ws, rank, local):
     descs = [gvt.gvt_desc_make(k) for k in KINDS]
     Mm = gvt.matrix(M, symmetric=True)
     sp = gvt.stream_ptr()
+    if args.engine == "tc":
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_TC_BF16X3)
     stream = torch.cuda.current_stream()
     vp = gvt.ptr(v)
     up = [gvt.ptr(U[i]) for i in range(len(KINDS))]
@@ -290,7 +295,14 @@ def run_gvt(args, ws, rank, local):
     ai = flops_l / max(bytes_l, 1.0)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     ridge = FP32_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
-    if ai > ridge:
+    if args.engine == "tc" and dom == "stage1":
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        achieved = flops_l / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
+                "frac": achieved / bf16, "peak_source": peak_src + " bf16 burst",
+                "note": "dense BF16x3 GEMM flops (3 split products over the densified W), split/densify "
+                        "kernels inside the timed scope"}
+    elif ai > ridge:
         achieved = flops_l / (per_launch_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
@@ -299,8 +311,8 @@ def run_gvt(args, ws, rank, local):
         achieved = bytes_l / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_src}
-    kname = {"stage1": "stage1_dense_kernel", "stage2": "stage2_dense_kernel",
-             "one_sided": "gemv_rows_kernel"}[dom]
+    kname = {"stage1": "tc_gemm_kernel" if args.engine == "tc" else "stage1_dense_kernel",
+             "stage2": "stage2_dense_kernel", "one_sided": "gemv_rows_kernel"}[dom]
     roof.update({"kernel": kname, "traffic": traffic_for(kname), "ms_per_launch": per_launch_ms,
                  "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
                  "hbm_frac": (bytes_l / (per_launch_ms / 1e3) / 1e9) / hbm})
@@ -334,9 +346,14 @@ def run_gvt(args, ws, rank, local):
            "ms_per_step": float(t.item())}
 
     # ---- KRR solve: plain FP64 CG vs mixed-precision refinement
+    accuracy = None
+    if rank == 0:
+        accuracy = sampled_error(p, M, plan, gvt, torch, dev)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    tc_gemm = bench_tc_gemm(H, gvt, torch, dev, peaks) if rank == 0 else None
     solve = None
     if not args.no_solve and rank == 0:
-        solve = bench_solve(H, gvt, torch, dev)
+        solve = bench_solve(H, gvt, torch, dev, [float(x) for x in args.solve_lambdas.split(",")])
 
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -355,7 +372,8 @@ def run_gvt(args, ws, rank, local):
                           "l2": "flushed (512 MB write) before every timed step, outside the events",
                           "parallelism": "replicas: independent problems per rank (seed = rank)"},
                "roofline": roof, "stages": stage_summary, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clk, "gpu_launches": launches, "solve": solve}
+               "clocks": clk, "gpu_launches": launches, "engine": args.engine,
+               "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve}
         print(json.dumps(out), flush=True)
     plan.close()
     H.close()
@@ -363,28 +381,79 @@ def run_gvt(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def bench_solve(H, gvt, torch, dev, lam=1e-2):
-    """Merget-shaped KRR (m=2000, q=250, n=120k, Kronecker kernel): wall time to FP64
-    rel. residual 1e-6 for plain FP64 CG and for FP32-inner iterative refinement."""
+def sampled_error(p, M, plan, gvt, torch, dev, rows=64):
+    """Normwise error of the timed FP32 products vs the FP64 oracle on sampled output rows."""
+    import numpy as np
+    import oracle as orc
+    Mo = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    idx = np.random.default_rng(1).choice(p.n, rows, replace=False)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=dev)
+    out = {}
+    for kind in KINDS:
+        u = gvt.pairwise_kernel_matvec(plan, kind, M, M, v).double().cpu().numpy()
+        ref = orc.pairwise_matvec(kind, Mo, Mo, p.d[idx], p.t[idx], p.d, p.t, p.v.astype(np.float32))
+        out[kind] = float(np.max(np.abs(u[idx] - ref)) / np.max(np.abs(ref)))
+    out["max"] = max(out.values())
+    out["sample"] = "%d output rows, normwise max|u - u*| / max|u*|" % rows
+    return out
+
+
+def bench_tc_gemm(H, gvt, torch, dev, peaks, reps=50):
+    """The tcgen05 BF16 GEMM of the dense stage 1 on the Merget-shaped problem in ordering B:
+    S' (2000 x 250) = [hi|hi|lo](M) [hi|lo|hi](W^T)^T, K' = 3 * 2048."""
+    Y, X, K = 2000, 250, 3 * 2048
+    g = torch.Generator(device=dev).manual_seed(0)
+    A = torch.randn(Y, K, generator=g, device=dev).to(torch.bfloat16)
+    B = torch.randn(X, K, generator=g, device=dev).to(torch.bfloat16)
+    C = torch.empty(Y, X, device=dev)
+    sp = gvt.stream_ptr()
+    for _ in range(5):
+        gvt.gvt_tc_gemm_bf16(H.h, gvt.ptr(A), K, gvt.ptr(B), K, gvt.ptr(C), X, Y, X, K, sp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        gvt.gvt_tc_gemm_bf16(H.h, gvt.ptr(A), K, gvt.ptr(B), K, gvt.ptr(C), X, Y, X, K, sp)
+    e1.record()
+    torch.cuda.synchronize()
+    gvt.gvt_check_device_errors(H.h, sp)
+    ms = e0.elapsed_time(e1) / reps
+    tf = 2.0 * Y * X * K / (ms / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    return {"shape": "M=%d N=%d K=%d (bf16 in, fp32 out)" % (Y, X, K), "ms": ms, "bound": "tensor",
+            "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "note": "includes launch and the split-K zeroing; small GEMM (16 x 1 output tiles x 10 K splits)"}
+
+
+def bench_solve(H, gvt, torch, dev, lambdas):
+    """Merget-shaped KRR (m=2000, q=250, n=120k, Kronecker kernel): wall time to FP64 rel.
+    residual 1e-6 for plain FP64 CG, FP32-inner refinement and tensor-core-inner refinement."""
     from paper_2009_01054_gb300 import synth
     p = synth.merget(0)
     M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma)
     N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=dev), gamma=p.gamma)
     plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
     y = torch.as_tensor(p.y, device=dev)
-    res = {"workload": "merget-shaped: m=2000, q=250, 128-d, n=120k (24%%), Kronecker of Gaussians, "
-                       "lambda=%g, target FP64 rel. residual 1e-6" % lam}
-    for name, mode in (("fp64_cg", gvt.GVT_SOLVE_FP64_CG), ("mixed_ir", gvt.GVT_SOLVE_MIXED_IR)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=10,
-                                       max_iter=20000)
-        torch.cuda.synchronize()
-        wall = (time.perf_counter() - t0) * 1e3
-        res[name] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
-                     "refinements": int(info.refinements), "rel_residual": info.rel_residual}
-    if res["mixed_ir"]["ms"] > 0:
-        res["speedup_vs_fp64_cg"] = res["fp64_cg"]["ms"] / res["mixed_ir"]["ms"]
+    res = {"workload": "merget-shaped: m=2000, q=250, 128-d, n=120k (24%), Kronecker of Gaussians, "
+                       "target FP64 rel. residual 1e-6", "runs": {}}
+    variants = (("fp64_cg", gvt.GVT_SOLVE_FP64_CG, gvt.GVT_F32),
+                ("mixed_ir_f32", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32),
+                ("mixed_ir_tc_bf16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_BF16))
+    for lam in lambdas:
+        r = {}
+        for name, mode, inner in variants:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=10,
+                                           max_iter=20000, inner_dtype=inner)
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) * 1e3
+            r[name] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
+                       "refinements": int(info.refinements), "rel_residual": info.rel_residual}
+        for name in ("mixed_ir_f32", "mixed_ir_tc_bf16x3"):
+            if r[name]["status"] == "GVT_OK" and r["fp64_cg"]["status"] == "GVT_OK":
+                r[name]["speedup_vs_fp64_cg"] = r["fp64_cg"]["ms"] / r[name]["ms"]
+        res["runs"]["lambda=%g" % lam] = r
     plan.close()
     return res
 

@@ -343,8 +343,9 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     const int gx = (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
     const int kb_total = (int)(K / TC_BK);
     const int tiles = gx * gy;
-    int splits = (148 + tiles - 1) / tiles;
-    splits = std::max(1, std::min(splits, kb_total / 4));
+    // split K only when the output tiles alone leave most SMs idle
+    int splits = tiles >= 100 ? 1 : (148 + tiles - 1) / tiles;
+    splits = std::max(1, std::min(splits, kb_total / 8));
     const int kb_per = (kb_total + splits - 1) / splits;
     splits = (kb_total + kb_per - 1) / kb_per;
     const int atomic_out = splits > 1 ? 1 : 0;
@@ -378,7 +379,12 @@ gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, 
         return GVT_ERR_UNSUPPORTED;
     }
     GVT_CHECK(get_encode());
-    const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+    // widest N tile that still gives >= 64 output tiles (fewer split-K partial sums to reduce)
+    const int64_t gx = (M + TC_BM - 1) / TC_BM;
+    int BN = 256;
+    while (BN > 64 && gx * ((N + BN - 1) / BN) < 64) BN /= 2;
+    if (N <= 64) BN = 64;
+    else if (N <= 128 && BN > 128) BN = 128;
     CUtensorMap ma, mb;
     GVT_CHECK(make_map(&ma, A, M, K, lda, TC_BM));
     GVT_CHECK(make_map(&mb, B, N, K, ldb, BN));
