@@ -306,6 +306,37 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
                             const double* y, double lambda, double* a,
                             const gvt_solve_opts* opts, gvt_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------ batched solves */
+
+/* One problem of a batched solve.  All pointers are device memory. */
+typedef struct gvt_problem {
+    int64_t m, q, n;          /* drugs, targets, training pairs (m, q <= 65535) */
+    const double* M;          /* m x m FP64 drug kernel, row-major (ld = m), symmetric */
+    const double* N;          /* q x q FP64 target kernel, row-major (ld = q), symmetric */
+    const int32_t* d;         /* n drug ids in [0, m) */
+    const int32_t* t;         /* n target ids in [0, q) */
+    const double* y;          /* n labels */
+    double* a;                /* out: n x n_lambda dual coefficients, column c at a + c * n */
+} gvt_problem;
+
+/*
+ * Kernel ridge regression (Eq. linsystem) for many independent problems and
+ * several regularisation values at once: for every problem b and every
+ * lambda_c, (R_b (M_b kron N_b) R_b^T + lambda_c I) a_bc = y_b.
+ * One persistent launch per stage covers the whole batch; each loaded kernel
+ * entry serves all lambda columns.  Inner CG in FP32 with FP64 dot products
+ * and step lengths, one iteration captured as a CUDA graph; the outer loop
+ * refines with FP64 residuals until every system reaches
+ * ||y_b - (K_b + lambda_c I) a_bc|| / ||y_b|| <= opts->rel_tol.  The tile shape
+ * of stage 1 is autotuned on the first call for a batch shape and cached in
+ * the handle.  n_lambda in [1, 16].  rel_residuals (host, may be NULL)
+ * receives the final FP64 relative residual of system (b, c) at
+ * [b * n_lambda + c].  Synchronises `stream`.
+ */
+gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem* probs, int64_t n_probs,
+                                    const double* lambdas, int64_t n_lambda, const gvt_solve_opts* opts,
+                                    double* rel_residuals, gvt_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------ instrumentation */
 
 /* Per-stage device time and algorithmic work of the products made with a

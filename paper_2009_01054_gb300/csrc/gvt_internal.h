@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gvt.h"
@@ -75,6 +77,7 @@ struct gvt_handle {
     double* host_scalars = nullptr;  // pinned
     bool stats_on = false;
     int stage1_engine = 0;          // gvt_stage1_engine for FP32 products
+    std::map<std::tuple<int, int64_t, int>, int> batch_tune;   // batched stage-1 tile choice
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;
 };

@@ -65,6 +65,11 @@ GVT_STAT_STAGE1, GVT_STAT_STAGE2, GVT_STAT_ONE_SIDED, GVT_STAT_COUNT = 0, 1, 2, 
 STAT_NAMES = ["stage1", "stage2", "one_sided"]
 
 
+class gvt_problem(ctypes.Structure):
+    _fields_ = [("m", c_i64), ("q", c_i64), ("n", c_i64), ("M", c_vp), ("N", c_vp), ("d", c_vp),
+                ("t", c_vp), ("y", c_vp), ("a", c_vp)]
+
+
 class GvtError(RuntimeError):
     def __init__(self, status, func, msg):
         self.status = status
@@ -97,6 +102,8 @@ SIGNATURES = [
     ("gvt_launch_count", c_i64, []),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
                                  c_vp, c_dbl, c_vp, _P(gvt_solve_opts), _P(gvt_solve_info), c_vp]),
+    ("gvt_krr_cg_solve_batched", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, _P(gvt_solve_opts), c_vp,
+                                         _P(gvt_solve_info), c_vp]),
     ("gvt_set_stage1_engine", c_i32, [c_vp, c_i32]),
     ("gvt_check_device_errors", c_i32, [c_vp, c_vp]),
     ("gvt_tc_gemm_bf16", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]),
@@ -213,6 +220,46 @@ def gvt_matvec_static(m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t
     """Allocation-free Kronecker product (see include/gvt.h); raises on a non-zero status."""
     _call("gvt_matvec_static", m_rows, m_cols, q_rows, q_cols, d_in, t_in, n_in, d_out, t_out,
           n_out, ctypes.byref(M), ctypes.byref(N), v, u, dtype, stream)
+
+
+def gvt_krr_cg_solve_batched(h, probs, lambdas, opts, stream):
+    """probs: list of gvt_problem; returns (status, info, rel_residuals[n_probs][n_lambda])."""
+    arr = (gvt_problem * len(probs))(*probs)
+    lam = (c_dbl * len(lambdas))(*lambdas)
+    rr = (c_dbl * (len(probs) * len(lambdas)))()
+    info = gvt_solve_info()
+    st = load().gvt_krr_cg_solve_batched(h, ctypes.cast(arr, c_vp), len(probs), ctypes.cast(lam, c_vp),
+                                         len(lambdas), ctypes.byref(opts), ctypes.cast(rr, c_vp),
+                                         ctypes.byref(info), stream)
+    if st not in (GVT_OK, 6, 7):
+        raise GvtError(st, "gvt_krr_cg_solve_batched", last_error())
+    res = [[rr[b * len(lambdas) + c] for c in range(len(lambdas))] for b in range(len(probs))]
+    return st, info, res
+
+
+def krr_solve_batched(handle, problems, lambdas, rel_tol=1e-6, inner_tol=1e-3, max_iter=20000,
+                      max_refine=30, check_every=5, stream=None):
+    """problems: list of dicts with CUDA tensors M, N (FP64), d, t (int32), y (FP64).
+    Returns (list of a tensors (n x n_lambda), status, info, rel_residuals)."""
+    torch = _torch()
+    keep, probs, outs = [], [], []
+    for p in problems:
+        d = p["d"].to(torch.int32).contiguous()
+        t = p["t"].to(torch.int32).contiguous()
+        y = p["y"].to(torch.float64).contiguous()
+        M = p["M"].to(torch.float64).contiguous()
+        N = p["N"].to(torch.float64).contiguous()
+        n = d.numel()
+        a = torch.zeros((len(lambdas), n), dtype=torch.float64, device=y.device)
+        keep += [d, t, y, M, N, a]
+        outs.append(a)
+        probs.append(gvt_problem(M.shape[0], N.shape[0], n, c_vp(M.data_ptr()), c_vp(N.data_ptr()),
+                                 c_vp(d.data_ptr()), c_vp(t.data_ptr()), c_vp(y.data_ptr()),
+                                 c_vp(a.data_ptr())))
+    o = gvt_solve_opts_default()
+    o.rel_tol, o.inner_tol, o.max_iter, o.max_refine, o.check_every = rel_tol, inner_tol, max_iter, max_refine, check_every
+    st, info, rr = gvt_krr_cg_solve_batched(handle.h, probs, list(lambdas), o, stream_ptr(stream))
+    return [a.t() for a in outs], st, info, rr
 
 
 def gvt_set_stage1_engine(h, engine):
