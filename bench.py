@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--engine", default="simt", choices=["simt", "tc"],
                     help="stage-1 engine of the FP32 products: sparse SIMT, or tcgen05 BF16x3 on densified W")
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-problems", type=int, default=256)
     return ap.parse_args()
 
 
@@ -354,6 +356,9 @@ def run_gvt(args, ws, rank, local):
     solve = None
     if not args.no_solve and rank == 0:
         solve = bench_solve(H, gvt, torch, dev, [float(x) for x in args.solve_lambdas.split(",")])
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = bench_batched(H, gvt, torch, dev, args.batched_problems)
 
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -373,7 +378,8 @@ def run_gvt(args, ws, rank, local):
                           "parallelism": "replicas: independent problems per rank (seed = rank)"},
                "roofline": roof, "stages": stage_summary, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clk, "gpu_launches": launches, "engine": args.engine,
-               "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve}
+               "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve,
+               "batched": batched}
         print(json.dumps(out), flush=True)
     plan.close()
     H.close()
@@ -456,6 +462,58 @@ def bench_solve(H, gvt, torch, dev, lambdas):
         res["runs"]["lambda=%g" % lam] = r
     plan.close()
     return res
+
+
+def bench_batched(H, gvt, torch, dev, n_probs, sample=8):
+    """Batched uneven problems: n_probs KRR problems (m, q ~ U{32..512}, density ~ U[5%, 60%],
+    32-d features, Kronecker of Gaussians) x 16 lambdas (logspace 1e-4..1) in one batched solve to
+    FP64 rel. residual 1e-6, against plain FP64 CG run system by system on a sample of problems."""
+    from paper_2009_01054_gb300 import synth
+    t0 = time.perf_counter()
+    ps = synth.batched(n_probs)
+    gen_s = time.perf_counter() - t0
+    lambdas = list(ps[0].lambdas)
+    probs = []
+    for p in ps:
+        M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma)
+        N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=dev), gamma=p.gamma)
+        probs.append(dict(M=M, N=N, d=torch.as_tensor(p.d, device=dev), t=torch.as_tensor(p.t, device=dev),
+                          y=torch.as_tensor(p.y, device=dev)))
+    total_pairs = sum(p.n for p in ps)
+    # first call includes the autotuner; time the second (tuned, cached) call
+    gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A, st, info, rr = gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6)
+    torch.cuda.synchronize()
+    batched_ms = (time.perf_counter() - t0) * 1e3
+    worst = max(max(r) for r in rr)
+    # plain FP64 CG, one system at a time, on the first `sample` problems
+    t0 = time.perf_counter()
+    fp_iters, fp_worst, sample_pairs = 0, 0.0, 0
+    for b in range(min(sample, len(ps))):
+        p = probs[b]
+        plan = gvt.Plan(H, tuple(p["M"].shape), tuple(p["N"].shape), p["d"], p["t"])
+        for lam in lambdas:
+            a, st2, inf2 = gvt.krr_cg_solve(H, plan, "kronecker", p["M"], p["N"], p["y"], lam, max_iter=50000,
+                                            check_every=10)
+            fp_iters += inf2.iterations
+            fp_worst = max(fp_worst, inf2.rel_residual)
+        sample_pairs += ps[b].n
+        plan.close()
+    torch.cuda.synchronize()
+    fp_ms = (time.perf_counter() - t0) * 1e3
+    est_full = fp_ms * total_pairs / max(sample_pairs, 1)
+    return {"workload": "%d problems, m,q ~ U{32..512}, density ~ U[5%%,60%%], 32-d, %d lambdas logspace(-4,0), "
+                        "%d pairs total, %d systems" % (len(ps), len(lambdas), total_pairs, len(ps) * len(lambdas)),
+            "batched_ms": batched_ms, "status": gvt.STATUS_NAMES[st], "inner_iterations": int(info.iterations),
+            "refinements": int(info.refinements), "max_rel_residual": worst,
+            "plain_fp64_cg_sample": {"problems": min(sample, len(ps)), "systems": min(sample, len(ps)) * len(lambdas),
+                                     "ms": fp_ms, "iterations": fp_iters, "max_rel_residual": fp_worst,
+                                     "pairs": sample_pairs},
+            "plain_fp64_cg_estimate_ms": est_full,
+            "estimate_note": "plain FP64 CG time for all systems scaled from the sample by pair count",
+            "speedup_vs_plain_fp64_cg_estimate": est_full / batched_ms, "data_generation_s": gen_s}
 
 
 def main():

@@ -310,7 +310,8 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
 
 /* One problem of a batched solve.  All pointers are device memory. */
 typedef struct gvt_problem {
-    int64_t m, q, n;          /* drugs, targets, training pairs (m, q <= 65535) */
+    int64_t m, q, n;          /* drugs, targets, training pairs; m * kc <= 25600 where kc is
+                                 n_lambda rounded up to 4 (8, 16), q <= 65535 */
     const double* M;          /* m x m FP64 drug kernel, row-major (ld = m), symmetric */
     const double* N;          /* q x q FP64 target kernel, row-major (ld = q), symmetric */
     const int32_t* d;         /* n drug ids in [0, m) */

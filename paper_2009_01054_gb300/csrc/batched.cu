@@ -32,58 +32,127 @@ struct BProb {
     int64_t q_off;   // packed N_b (q x q)
     int64_t seg_off; // packed seg_b (m + 1)
     int64_t s_off;   // packed S_b (q x m x kc)
+    int64_t seg2_off;// packed target-order segments (q + 1)
 };
 
 constexpr int KC_MAX = 16;
 
+// Packed kernel matrices use a row pitch rounded up to 4 elements (zero
+// padding), so 4 consecutive rows of a column tile load as one 16-byte vector.
+__host__ __device__ inline int pitch4(int x) { return (x + 3) & ~3; }
+
+template <class T> struct V4;
+template <> struct V4<float> {
+    __device__ static void ld(const float* p, float (&o)[4])
+    {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    }
+    __device__ static void ld_shared(const float* p, float (&o)[4])
+    {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    }
+};
+template <> struct V4<double> {
+    __device__ static void ld(const double* p, double (&o)[4])
+    {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    __device__ static void ld_shared(const double* p, double (&o)[4])
+    {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+};
+
 // ------------------------------------------------------------------ stage 1
-// item = (problem, first column x0, first row y0); a CTA of NT threads owns
-// 4*NT/ (kc/4) rows ... concretely: thread = (row quad, column quad).
+// item = (problem, first column x0, first row y0).  Thread = (row quad rq,
+// column quad cq); the item's entries are staged in shared memory as
+// (target id, pair) records and consumed 4 at a time (8 vector loads in flight).
+constexpr int kB1Chunk = 256;
+constexpr int kB1MaxTx = 2;      // columns per stage-1 item (register tile)
+
 template <class T, int NT>
 __global__ void __launch_bounds__(NT)
 b_stage1_kernel(const int4* __restrict__ items, int n_items, const BProb* __restrict__ probs,
                 const T* __restrict__ Npk, const int32_t* __restrict__ seg, const int32_t* __restrict__ tcol,
                 const int32_t* __restrict__ perm, const T* __restrict__ V, T* __restrict__ S, int kc, int tx)
 {
+    __shared__ int2 ent[kB1Chunk];
     const int cq_n = kc / 4;                 // column quads; NT / cq_n row quads per item
     const int cq = threadIdx.x % cq_n, rq = threadIdx.x / cq_n;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 w = items[it];
         const BProb P = probs[w.x];
+        const int qp = pitch4(P.q);
         const int y = w.z + rq * 4;
         const bool row_ok = y < P.q;
-        const T* Nb = Npk + P.q_off;
+        const T* Nb = Npk + P.q_off + (row_ok ? y : 0);
+        const T* Vb = V + P.n_off * kc + cq * 4;
         const int32_t* sg = seg + P.seg_off;
         const int xe = min(w.y + tx, P.m);
-        for (int x = w.y; x < xe; ++x) {
-            T acc[4][4];
+        const int jb = sg[w.y], je = sg[xe];
+        T acc[kB1MaxTx][4][4];   // [column in tile][row][lambda]
+#pragma unroll
+        for (int u = 0; u < kB1MaxTx; ++u)
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
-            const int j1 = sg[x + 1];
-            for (int j = sg[x]; j < j1; ++j) {
-                const int64_t g = P.n_off + j;
-                const int32_t t = tcol[g];
-                const T* vr = V + (P.n_off + perm[g]) * kc + cq * 4;
-                T vv[4], nb[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) vv[c] = vr[c];
-                const T* nr = Nb + (int64_t)t * P.q + y;   // row t of the symmetric N_b
-#pragma unroll
-                for (int a = 0; a < 4; ++a) nb[a] = (row_ok && y + a < P.q) ? nr[a] : T(0);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][c] = fma(nb[a], vv[c], acc[a][c]);
+                for (int c = 0; c < 4; ++c) acc[u][a][c] = T(0);
+        for (int j0 = jb; j0 < je; j0 += kB1Chunk) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < kB1Chunk && j0 + e < je; e += NT) {
+                const int64_t g = P.n_off + j0 + e;
+                ent[e] = make_int2(tcol[g], perm[g]);
             }
-            if (row_ok) {
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kB1MaxTx; ++u) {
+                if (w.y + u >= xe) break;
+                const int lo = max(sg[w.y + u], j0) - j0;
+                const int hi = min(sg[w.y + u + 1], j0 + kB1Chunk) - j0;
+                int e = lo;
+                for (; e + 4 <= hi; e += 4) {
+                    T nb[4][4], vv[4][4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int2 en = ent[e + r];
+                        V4<T>::ld(Nb + (int64_t)en.x * qp, nb[r]);
+                        V4<T>::ld(Vb + (int64_t)en.y * kc, vv[r]);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) acc[u][a][c] = fma(nb[r][a], vv[r][c], acc[u][a][c]);
+                }
+                for (; e < hi; ++e) {
+                    T nb[4], vv[4];
+                    const int2 en = ent[e];
+                    V4<T>::ld(Nb + (int64_t)en.x * qp, nb);
+                    V4<T>::ld(Vb + (int64_t)en.y * kc, vv);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[u][a][c] = fma(nb[a], vv[c], acc[u][a][c]);
+                }
+            }
+        }
+        if (row_ok) {
+#pragma unroll
+            for (int u = 0; u < kB1MaxTx; ++u) {
+                if (w.y + u >= xe) break;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     if (y + a >= P.q) break;
-                    T* sr = S + P.s_off + ((int64_t)(y + a) * P.m + x) * kc + cq * 4;
+                    T* sr = S + P.s_off + ((int64_t)(y + a) * P.m + w.y + u) * kc + cq * 4;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) sr[c] = acc[a][c];
+                    for (int c = 0; c < 4; ++c) sr[c] = acc[u][a][c];
                 }
             }
         }
@@ -91,15 +160,23 @@ b_stage1_kernel(const int4* __restrict__ items, int n_items, const BProb* __rest
 }
 
 // ------------------------------------------------------------------ stage 2
-// item = (problem, first output, end output) in drug-sorted order; one warp
-// per output: 8 lanes along x times 4 lanes along column quads (kc = 16).
+// item = (problem, target t): the outputs with target t (pairs sorted by
+// target) all read row t of S_b, which is staged once in shared memory
+// (padded to pitch4(m) rows of kc with zeros).  A warp takes 4 outputs of the
+// group at a time; lane = (x quad xl, lambda quad cq): per x quad it loads
+// the 4 x 4 block of S from shared memory and one 4-vector of each output's
+// M row, then does 64 multiply-adds.
+constexpr int kB2G = 4;
+
 template <class T>
 __global__ void __launch_bounds__(256)
 b_stage2_kernel(const int4* __restrict__ items, int n_items, const BProb* __restrict__ probs,
-                const T* __restrict__ Mpk, const int32_t* __restrict__ key, const int32_t* __restrict__ tcol,
-                const int32_t* __restrict__ perm, const T* __restrict__ S, const T* __restrict__ V,
+                const T* __restrict__ Mpk, const int32_t* __restrict__ seg2, const int32_t* __restrict__ dcol2,
+                const int32_t* __restrict__ perm2, const T* __restrict__ S, const T* __restrict__ V,
                 const double* __restrict__ lam, T* __restrict__ Wout, int kc)
 {
+    extern __shared__ __align__(16) unsigned char s2_raw[];
+    T* srow = reinterpret_cast<T*>(s2_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cq_n = kc / 4;
     const int xl_n = 32 / cq_n;
@@ -107,27 +184,53 @@ b_stage2_kernel(const int4* __restrict__ items, int n_items, const BProb* __rest
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 w = items[it];
         const BProb P = probs[w.x];
+        const int t = w.y;
+        const int32_t* sg = seg2 + P.seg2_off;
+        const int i0 = sg[t], i1 = sg[t + 1];
+        const int mp = pitch4(P.m);
+        const T* src = S + P.s_off + (int64_t)t * P.m * kc;
+        __syncthreads();
+        for (int e = threadIdx.x; e < mp * kc; e += blockDim.x) srow[e] = e < P.m * kc ? src[e] : T(0);
+        __syncthreads();
         const T* Mb = Mpk + P.m_off;
-        for (int i = w.y + warp; i < w.z; i += 8) {
-            const int64_t g = P.n_off + i;
-            const int32_t r = key[g], s = tcol[g];
-            const T* mr = Mb + (int64_t)r * P.m;
-            const T* sr = S + P.s_off + (int64_t)s * P.m * kc + cq * 4;
-            T acc[4] = {T(0), T(0), T(0), T(0)};
-            for (int x = xl; x < P.m; x += xl_n) {
-                const T mv = mr[x];
+        for (int ib = i0 + warp * kB2G; ib < i1; ib += 8 * kB2G) {
+            const int ng = min(kB2G, i1 - ib);
+            const T* mr[kB2G];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[c] = fma(mv, sr[(int64_t)x * kc + c], acc[c]);
+            for (int g = 0; g < kB2G; ++g) {
+                const int gi = ib + (g < ng ? g : ng - 1);
+                mr[g] = Mb + (int64_t)dcol2[P.n_off + gi] * mp;
+            }
+            T acc[kB2G][4];
+#pragma unroll
+            for (int g = 0; g < kB2G; ++g)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[g][c] = T(0);
+            for (int x = xl * 4; x < mp; x += xl_n * 4) {
+                T sv[4][4], mv[kB2G][4];
+#pragma unroll
+                for (int xx = 0; xx < 4; ++xx) V4<T>::ld_shared(srow + (x + xx) * kc + cq * 4, sv[xx]);
+#pragma unroll
+                for (int g = 0; g < kB2G; ++g) V4<T>::ld(mr[g] + x, mv[g]);
+#pragma unroll
+                for (int g = 0; g < kB2G; ++g)
+#pragma unroll
+                    for (int xx = 0; xx < 4; ++xx)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[g][c] = fma(mv[g][xx], sv[xx][c], acc[g][c]);
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                for (int o = cq_n; o < 32; o <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-            if (xl == 0) {
-                const int64_t row = (P.n_off + perm[g]) * kc + cq * 4;
+            for (int g = 0; g < kB2G; ++g)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int cc = cq * 4 + c;
-                    Wout[row + c] = acc[c] + (T)lam[cc] * V[row + c];
+                for (int c = 0; c < 4; ++c)
+                    for (int o = cq_n; o < 32; o <<= 1) acc[g][c] += __shfl_xor_sync(0xffffffffu, acc[g][c], o);
+            if (xl == 0) {
+#pragma unroll
+                for (int g = 0; g < kB2G; ++g) {
+                    if (g >= ng) break;
+                    const int64_t row = (P.n_off + perm2[P.n_off + ib + g]) * kc + cq * 4;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) Wout[row + c] = acc[g][c] + (T)lam[cq * 4 + c] * V[row + c];
                 }
             }
         }
@@ -135,12 +238,14 @@ b_stage2_kernel(const int4* __restrict__ items, int n_items, const BProb* __rest
 }
 
 // ------------------------------------------------------------------ batched CG vector kernels
-// One block per problem; thread (jl, c) with c = tid % kc.  Systems: b * kc + c.
+// Work unit: a chunk of kRows consecutive rows of one problem (chunk = (b, r0, r1));
+// thread (jl, c) with c = tid % kc.  Dot products produce one partial sum per
+// (chunk, column); b_sys_sum adds a problem's chunks in a fixed order.
 constexpr int kBT = 256;
+constexpr int kRows = 128;
 
 __device__ double bsum_col(double x, double* sh, int kc)
 {
-    // reduce over the (kBT / kc) row lanes that share column c = tid % kc
     sh[threadIdx.x] = x;
     __syncthreads();
     double r = 0.0;
@@ -152,19 +257,32 @@ __device__ double bsum_col(double x, double* sh, int kc)
 
 template <class T>
 __global__ void __launch_bounds__(kBT)
-b_dot_kernel(const BProb* __restrict__ probs, const T* __restrict__ X, const T* __restrict__ Y, int kc,
-             double* __restrict__ out)
+b_dot_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs, const T* __restrict__ X,
+             const T* __restrict__ Y, int kc, double* __restrict__ part)
 {
     __shared__ double sh[kBT];
-    const BProb P = probs[blockIdx.x];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
     double acc = 0.0;
-    for (int64_t j = jl; j < P.n; j += nl) {
-        const int64_t e = (P.n_off + j) * kc + c;
+    for (int j = ch.y + jl; j < ch.z; j += nl) {
+        const int64_t e = (base + j) * kc + c;
         acc += (double)X[e] * (double)Y[e];
     }
     const double r = bsum_col(acc, sh, kc);
-    if (threadIdx.x < kc) out[(int64_t)blockIdx.x * kc + threadIdx.x] = r;
+    if (threadIdx.x < kc) part[(int64_t)blockIdx.x * kc + threadIdx.x] = r;
+}
+
+// out[b * kc + c] = sum of part over problem b's chunks [cfirst[b], cfirst[b+1])
+__global__ void b_sys_sum_kernel(const double* __restrict__ part, const int32_t* __restrict__ cfirst, int P, int kc,
+                                 double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= P * kc) return;
+    const int b = s / kc, c = s % kc;
+    double acc = 0.0;
+    for (int q = cfirst[b]; q < cfirst[b + 1]; ++q) acc += part[(int64_t)q * kc + c];
+    out[s] = acc;
 }
 
 // per-system scalars
@@ -212,39 +330,42 @@ __global__ void b_beta_kernel(const double* __restrict__ rr_new, double* __restr
     }
 }
 
-// x += alpha p; r -= alpha w; part rr (per problem block)
+// x += alpha p; r -= alpha w; partial r.r per chunk
 template <class T>
 __global__ void __launch_bounds__(kBT)
-b_update_kernel(const BProb* __restrict__ probs, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                const T* __restrict__ w, const double* __restrict__ sc, int kc, double* __restrict__ rr_out)
+b_update_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs, T* __restrict__ x,
+                T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ w, const double* __restrict__ sc,
+                int kc, double* __restrict__ part)
 {
     __shared__ double sh[kBT];
-    const BProb P = probs[blockIdx.x];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    const double alpha = sc[((int64_t)blockIdx.x * kc + c) * B_N + B_ALPHA];
+    const double alpha = sc[((int64_t)ch.x * kc + c) * B_N + B_ALPHA];
     double acc = 0.0;
-    for (int64_t j = jl; j < P.n; j += nl) {
-        const int64_t e = (P.n_off + j) * kc + c;
+    for (int j = ch.y + jl; j < ch.z; j += nl) {
+        const int64_t e = (base + j) * kc + c;
         x[e] = (T)((double)x[e] + alpha * (double)p[e]);
         const T ri = (T)((double)r[e] - alpha * (double)w[e]);
         r[e] = ri;
         acc += (double)ri * (double)ri;
     }
-    const double s = bsum_col(acc, sh, kc);
-    if (threadIdx.x < kc) rr_out[(int64_t)blockIdx.x * kc + threadIdx.x] = s;
+    const double sres = bsum_col(acc, sh, kc);
+    if (threadIdx.x < kc) part[(int64_t)blockIdx.x * kc + threadIdx.x] = sres;
 }
 
 // p = r + beta p
 template <class T>
 __global__ void __launch_bounds__(kBT)
-b_pupdate_kernel(const BProb* __restrict__ probs, T* __restrict__ p, const T* __restrict__ r,
-                 const double* __restrict__ sc, int kc)
+b_pupdate_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs, T* __restrict__ p,
+                 const T* __restrict__ r, const double* __restrict__ sc, int kc)
 {
-    const BProb P = probs[blockIdx.x];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    const double beta = sc[((int64_t)blockIdx.x * kc + c) * B_N + B_BETA];
-    for (int64_t j = jl; j < P.n; j += nl) {
-        const int64_t e = (P.n_off + j) * kc + c;
+    const double beta = sc[((int64_t)ch.x * kc + c) * B_N + B_BETA];
+    for (int j = ch.y + jl; j < ch.z; j += nl) {
+        const int64_t e = (base + j) * kc + c;
         p[e] = (T)((double)r[e] + beta * (double)p[e]);
     }
 }
@@ -264,28 +385,31 @@ __global__ void b_init_scal_kernel(const double* __restrict__ rr0, double* __res
 }
 
 // r64 = Y (broadcast over columns < k) - W64 ; W64 already holds K a + lambda a
-__global__ void b_residual_kernel(const BProb* __restrict__ probs, const double* __restrict__ y,
-                                  const double* __restrict__ W, double* __restrict__ r, int k, int kc)
+__global__ void b_residual_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs,
+                                  const double* __restrict__ y, const double* __restrict__ W, double* __restrict__ r,
+                                  int k, int kc)
 {
-    const BProb P = probs[blockIdx.x];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    for (int64_t j = jl; j < P.n; j += nl) {
-        const int64_t e = (P.n_off + j) * kc + c;
-        r[e] = (c < k) ? y[P.n_off + j] - W[e] : 0.0;
+    for (int j = ch.y + jl; j < ch.z; j += nl) {
+        const int64_t e = (base + j) * kc + c;
+        r[e] = (c < k) ? y[base + j] - W[e] : 0.0;
     }
 }
 
-// r32 = r64 / ||r||_sys ; c32 = 0
-__global__ void b_scale_kernel(const BProb* __restrict__ probs, const double* __restrict__ r64,
-                               const double* __restrict__ rn, float* __restrict__ b32, float* __restrict__ rr32,
-                               float* __restrict__ p32, float* __restrict__ c32, int kc)
+// b32 = r32 = p32 = r64 / ||r||_sys ; c32 = 0
+__global__ void b_scale_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs,
+                               const double* __restrict__ r64, const double* __restrict__ rn, float* __restrict__ b32,
+                               float* __restrict__ rr32, float* __restrict__ p32, float* __restrict__ c32, int kc)
 {
-    const BProb P = probs[blockIdx.x];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    const double n = rn[(int64_t)blockIdx.x * kc + c];
+    const double n = rn[(int64_t)ch.x * kc + c];
     const double inv = n > 0.0 ? 1.0 / n : 0.0;
-    for (int64_t j = jl; j < P.n; j += nl) {
-        const int64_t e = (P.n_off + j) * kc + c;
+    for (int j = ch.y + jl; j < ch.z; j += nl) {
+        const int64_t e = (base + j) * kc + c;
         const float v = (float)(r64[e] * inv);
         b32[e] = v;
         rr32[e] = v;
@@ -295,14 +419,16 @@ __global__ void b_scale_kernel(const BProb* __restrict__ probs, const double* __
 }
 
 // a64 += ||r|| * c32
-__global__ void b_correct_kernel(const BProb* __restrict__ probs, double* __restrict__ a, const float* __restrict__ c32,
-                                 const double* __restrict__ rn, int kc)
+__global__ void b_correct_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs,
+                                 double* __restrict__ a, const float* __restrict__ c32, const double* __restrict__ rn,
+                                 int kc)
 {
-    const BProb P = probs[blockIdx.x];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    const double n = rn[(int64_t)blockIdx.x * kc + c];
-    for (int64_t j = jl; j < P.n; j += nl) {
-        const int64_t e = (P.n_off + j) * kc + c;
+    const double n = rn[(int64_t)ch.x * kc + c];
+    for (int j = ch.y + jl; j < ch.z; j += nl) {
+        const int64_t e = (base + j) * kc + c;
         a[e] += n * (double)c32[e];
     }
 }
@@ -318,11 +444,16 @@ __global__ void b_unpack_kernel(const BProb* __restrict__ probs, const double* _
     for (int64_t j = jl; j < P.n; j += nl) o[(int64_t)c * P.n + j] = a[(P.n_off + j) * kc + c];
 }
 
-__global__ void b_pack_kernel(const double* __restrict__ src, int64_t n, double* __restrict__ d64, float* __restrict__ d32)
+// dst[r * pitch4(n) + c] = src[r * n + c] (zero padding), FP64 and FP32 copies
+__global__ void b_pack_kernel(const double* __restrict__ src, int n, double* __restrict__ d64, float* __restrict__ d32)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        d64[i] = src[i];
-        d32[i] = (float)src[i];
+    const int np = pitch4(n);
+    const int64_t total = (int64_t)n * np;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / np, c = i % np;
+        const double v = c < n ? src[r * n + c] : 0.0;
+        d64[i] = v;
+        d32[i] = (float)v;
     }
 }
 
@@ -340,15 +471,17 @@ unsigned gs(int64_t n)
 
 // ------------------------------------------------------------------ operator object
 struct Batch {
-    int P = 0, k = 0, kc = 0;
-    int64_t n_total = 0, mm = 0, qq = 0, segs = 0, s_elems = 0;
+    int P = 0, k = 0, kc = 0, m_max = 0;
+    int64_t n_total = 0, mm = 0, qq = 0, segs = 0, segs2 = 0, s_elems = 0;
     std::vector<BProb> hp;
     BProb* probs = nullptr;
     double* M64 = nullptr; float* M32 = nullptr;
     double* N64 = nullptr; float* N32 = nullptr;
-    int32_t *key = nullptr, *tcol = nullptr, *perm = nullptr, *seg = nullptr;
-    int4 *it1 = nullptr, *it2 = nullptr;
-    int n1 = 0, n2 = 0;
+    int32_t *key = nullptr, *tcol = nullptr, *perm = nullptr, *seg = nullptr;        // drug order
+    int32_t *key2 = nullptr, *dcol2 = nullptr, *perm2 = nullptr, *seg2 = nullptr;    // target order
+    int4 *it1 = nullptr, *it2 = nullptr, *chunks = nullptr;
+    int32_t* cfirst = nullptr;
+    int n1 = 0, n2 = 0, nch = 0;
     int tx = 2, nt1 = 128;        // autotuned stage-1 shape
     std::vector<void*> allocs;
     ~Batch() { for (void* p : allocs) cudaFree(p); }
@@ -367,7 +500,7 @@ struct Batch {
     }
 };
 
-gvt_status build_items(Batch& B, int tx, int nt1, std::vector<int4>& i1)
+void build_items(const Batch& B, int tx, int nt1, std::vector<int4>& i1)
 {
     const int rows_per = 4 * (nt1 / (B.kc / 4));
     std::vector<std::pair<double, int4>> w;
@@ -381,7 +514,6 @@ gvt_status build_items(Batch& B, int tx, int nt1, std::vector<int4>& i1)
     std::stable_sort(w.begin(), w.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
     i1.clear();
     for (auto& e : w) i1.push_back(e.second);
-    return GVT_OK;
 }
 
 template <class T>
@@ -392,9 +524,20 @@ gvt_status apply(const Batch& B, const T* Mpk, const T* Npk, const T* V, T* S, T
         b_stage1_kernel<T, 128><<<grid1, 128, 0, s>>>(B.it1, B.n1, B.probs, Npk, B.seg, B.tcol, B.perm, V, S, B.kc, B.tx);
     else
         b_stage1_kernel<T, 64><<<grid1, 64, 0, s>>>(B.it1, B.n1, B.probs, Npk, B.seg, B.tcol, B.perm, V, S, B.kc, B.tx);
-    b_stage2_kernel<T><<<152 * 8, 256, 0, s>>>(B.it2, B.n2, B.probs, Mpk, B.key, B.tcol, B.perm, S, V, lam, W, B.kc);
+    const size_t smem = sizeof(T) * (size_t)pitch4(B.m_max) * B.kc;
+    b_stage2_kernel<T><<<152 * 4, 256, smem, s>>>(B.it2, B.n2, B.probs, Mpk, B.seg2, B.dcol2, B.perm2, S, V, lam, W,
+                                                  B.kc);
     GVT_LAUNCHED(2, "batched operator");
     return GVT_OK;
+}
+
+// out[sys] = X . Y per system (chunk partials, then a fixed-order sum per problem)
+template <class T>
+void sys_dot(const Batch& B, const T* X, const T* Y, double* part, double* out, cudaStream_t s)
+{
+    b_dot_kernel<T><<<B.nch, kBT, 0, s>>>(B.chunks, B.probs, X, Y, B.kc, part);
+    b_sys_sum_kernel<<<(B.P * B.kc + 255) / 256, 256, 0, s>>>(part, B.cfirst, B.P, B.kc, out);
+    count_launches(2);
 }
 
 }  // namespace
@@ -433,21 +576,25 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
     B.P = (int)n_probs;
     B.k = (int)n_lambda;
     B.kc = (B.k + 3) / 4 * 4;
-    if (B.kc == 12) B.kc = 16;   // column quads must divide the 32 lanes of a warp
+    if (B.kc == 12) B.kc = 16;   // lambda quads must divide the 32 lanes of a warp
     B.hp.resize(B.P);
     int64_t maxn = 0;
     for (int b = 0; b < B.P; ++b) {
         const gvt_problem& p = probs[b];
-        if (p.m <= 0 || p.q <= 0 || p.m > 65535 || p.q > 65535 || p.n < 0 || p.n > INT32_MAX ||
+        // stage 2 keeps one FP64 row of S_b (m x kc) in shared memory: m * kc * 8 <= 200 KiB
+        if (p.m <= 0 || p.q <= 0 || pitch4((int)std::min<int64_t>(p.m, 1 << 20)) * B.kc * 8 > 200 * 1024 || p.q > 65535 || p.n < 0 || p.n > INT32_MAX ||
             (p.n > 0 && (!p.d || !p.t || !p.y || !p.a)) || !p.M || !p.N) {
-            set_error("gvt_krr_cg_solve_batched: bad problem " + std::to_string(b));
+            set_error("gvt_krr_cg_solve_batched: bad problem " + std::to_string(b) +
+                      " (m * padded lambda count <= 25600, q <= 65535)");
             return ret(GVT_ERR_INVALID_ARG);
         }
         BProb& q = B.hp[b];
         q.n_off = B.n_total; q.n = (int32_t)p.n; q.m = (int32_t)p.m; q.q = (int32_t)p.q; q.pad = 0;
-        q.m_off = B.mm; q.q_off = B.qq; q.seg_off = B.segs; q.s_off = B.s_elems;
-        B.n_total += p.n; B.mm += p.m * p.m; B.qq += p.q * p.q; B.segs += p.m + 1;
+        q.m_off = B.mm; q.q_off = B.qq; q.seg_off = B.segs; q.s_off = B.s_elems; q.seg2_off = B.segs2;
+        B.n_total += p.n; B.mm += p.m * pitch4((int)p.m); B.qq += p.q * pitch4((int)p.q);
+        B.segs += p.m + 1; B.segs2 += p.q + 1;
         B.s_elems += p.q * p.m * B.kc;
+        B.m_max = std::max<int>(B.m_max, (int)p.m);
         maxn = std::max<int64_t>(maxn, p.n);
     }
     const int kc = B.kc, k = B.k;
@@ -459,25 +606,27 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
     BCHK(B.alloc(&B.N64, B.qq)); BCHK(B.alloc(&B.N32, B.qq));
     BCHK(B.alloc(&B.key, B.n_total)); BCHK(B.alloc(&B.tcol, B.n_total)); BCHK(B.alloc(&B.perm, B.n_total));
     BCHK(B.alloc(&B.seg, B.segs));
-    void* sort_ws = nullptr;
-    BCHK(B.alloc(reinterpret_cast<char**>(&sort_ws), sort_workspace_bytes(maxn)));
+    BCHK(B.alloc(&B.key2, B.n_total)); BCHK(B.alloc(&B.dcol2, B.n_total)); BCHK(B.alloc(&B.perm2, B.n_total));
+    BCHK(B.alloc(&B.seg2, B.segs2));
+    char* sort_ws = nullptr;
+    BCHK(B.alloc(&sort_ws, sort_workspace_bytes(maxn)));
     int32_t* mm = h->status.as<int32_t>();
     for (int b = 0; b < B.P; ++b) {
         const gvt_problem& p = probs[b];
         const BProb& q = B.hp[b];
-        b_pack_kernel<<<gs(q.m * (int64_t)q.m), 256, 0, s>>>(p.M, (int64_t)q.m * q.m, B.M64 + q.m_off, B.M32 + q.m_off);
-        b_pack_kernel<<<gs(q.q * (int64_t)q.q), 256, 0, s>>>(p.N, (int64_t)q.q * q.q, B.N64 + q.q_off, B.N32 + q.q_off);
+        b_pack_kernel<<<gs(q.m * (int64_t)pitch4(q.m)), 256, 0, s>>>(p.M, q.m, B.M64 + q.m_off, B.M32 + q.m_off);
+        b_pack_kernel<<<gs(q.q * (int64_t)pitch4(q.q)), 256, 0, s>>>(p.N, q.q, B.N64 + q.q_off, B.N32 + q.q_off);
         count_launches(2);
         if (q.n == 0) {
             BCHK(segment_offsets(B.key + q.n_off, 0, q.m, B.seg + q.seg_off, s));
+            BCHK(segment_offsets(B.key2 + q.n_off, 0, q.q, B.seg2 + q.seg2_off, s));
             continue;
         }
-        // validate ids, then sort this problem's pairs by drug id
+        // validate ids, then sort this problem's pairs by drug id (stage 1) and by target id (stage 2)
         int32_t hm[4];
         BCHK(minmax_i32(p.d, q.n, mm, s));
-        if (cudaMemcpyAsync(hm, mm, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ret(cuda_fail(cudaGetLastError(), "batched validation"));
         BCHK(minmax_i32(p.t, q.n, mm + 2, s));
-        if (cudaMemcpyAsync(hm + 2, mm + 2, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(hm, mm, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return ret(cuda_fail(cudaGetLastError(), "batched validation"));
         if (hm[0] < 0 || hm[1] >= q.m || hm[2] < 0 || hm[3] >= q.q) {
@@ -487,55 +636,96 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
         BCHK(radix_sort_by_key(p.d, q.n, q.m, B.key + q.n_off, B.perm + q.n_off, sort_ws, s));
         BCHK(gather_i32(p.t, B.perm + q.n_off, q.n, B.tcol + q.n_off, s));
         BCHK(segment_offsets(B.key + q.n_off, q.n, q.m, B.seg + q.seg_off, s));
+        BCHK(radix_sort_by_key(p.t, q.n, q.q, B.key2 + q.n_off, B.perm2 + q.n_off, sort_ws, s));
+        BCHK(gather_i32(p.d, B.perm2 + q.n_off, q.n, B.dcol2 + q.n_off, s));
+        BCHK(segment_offsets(B.key2 + q.n_off, q.n, q.q, B.seg2 + q.seg2_off, s));
     }
     if (cudaMemcpyAsync(B.probs, B.hp.data(), sizeof(BProb) * B.P, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return ret(cuda_fail(cudaGetLastError(), "batched upload"));
 
-    // stage-2 items: chunks of 64 outputs
-    std::vector<int4> i2;
+    // stage-2 items: one per (problem, target with outputs), largest first
+    std::vector<int32_t> hseg2(B.segs2);
+    if (cudaMemcpyAsync(hseg2.data(), B.seg2, 4 * (size_t)B.segs2, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ret(cuda_fail(cudaGetLastError(), "batched segments"));
     {
         std::vector<std::pair<double, int4>> w;
-        for (int b = 0; b < B.P; ++b)
-            for (int i0 = 0; i0 < B.hp[b].n; i0 += 64)
-                w.push_back({(double)B.hp[b].m * std::min(64, B.hp[b].n - i0),
-                             make_int4(b, i0, std::min(i0 + 64, B.hp[b].n), 0)});
+        for (int b = 0; b < B.P; ++b) {
+            const BProb& q = B.hp[b];
+            for (int t = 0; t < q.q; ++t) {
+                const int ns = hseg2[q.seg2_off + t + 1] - hseg2[q.seg2_off + t];
+                if (ns > 0) w.push_back({(double)ns * q.m + q.m, make_int4(b, t, 0, 0)});
+            }
+        }
         std::stable_sort(w.begin(), w.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+        std::vector<int4> i2;
         for (auto& e : w) i2.push_back(e.second);
+        B.n2 = (int)i2.size();
+        BCHK(B.alloc(&B.it2, i2.size()));
+        if (!i2.empty() &&
+            cudaMemcpyAsync(B.it2, i2.data(), sizeof(int4) * i2.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return ret(cuda_fail(cudaGetLastError(), "batched items"));
     }
-    B.n2 = (int)i2.size();
-    BCHK(B.alloc(&B.it2, i2.size()));
+    // row chunks of every problem for the vector kernels
+    {
+        std::vector<int4> ch;
+        std::vector<int32_t> cf(B.P + 1, 0);
+        for (int b = 0; b < B.P; ++b) {
+            cf[b] = (int32_t)ch.size();
+            for (int r0 = 0; r0 < B.hp[b].n; r0 += kRows) ch.push_back(make_int4(b, r0, std::min(r0 + kRows, B.hp[b].n), 0));
+        }
+        cf[B.P] = (int32_t)ch.size();
+        if (ch.empty()) ch.push_back(make_int4(0, 0, 0, 0));
+        B.nch = (int)ch.size();
+        BCHK(B.alloc(&B.chunks, ch.size()));
+        BCHK(B.alloc(&B.cfirst, cf.size()));
+        if (cudaMemcpyAsync(B.chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(B.cfirst, cf.data(), 4 * cf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return ret(cuda_fail(cudaGetLastError(), "batched chunks"));
+    }
+    // stage 2 stages one S row (m x kc) in shared memory
+    {
+        const size_t sm64 = sizeof(double) * (size_t)pitch4(B.m_max) * kc;
+        const size_t sm32 = sizeof(float) * (size_t)pitch4(B.m_max) * kc;
+        if (sm64 > 48 * 1024 &&
+            cudaFuncSetAttribute(b_stage2_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64) != cudaSuccess)
+            return ret(cuda_fail(cudaGetLastError(), "stage 2 shared memory"));
+        if (sm32 > 48 * 1024 &&
+            cudaFuncSetAttribute(b_stage2_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32) != cudaSuccess)
+            return ret(cuda_fail(cudaGetLastError(), "stage 2 shared memory"));
+    }
 
     // ---- vectors
     const int64_t NE = B.n_total * kc;
     double *lam = nullptr, *a64 = nullptr, *r64 = nullptr, *w64 = nullptr, *S64 = nullptr, *ynorm = nullptr;
-    double *rn = nullptr, *part = nullptr, *sc = nullptr, *skip = nullptr;
+    double *rn = nullptr, *part = nullptr, *sysv = nullptr, *sc = nullptr, *skip = nullptr, *ypk = nullptr;
     float *S32 = nullptr, *b32 = nullptr, *r32 = nullptr, *p32 = nullptr, *w32 = nullptr, *c32 = nullptr;
     int* flags = nullptr;
     BCHK(B.alloc(&lam, kc)); BCHK(B.alloc(&a64, NE)); BCHK(B.alloc(&r64, NE)); BCHK(B.alloc(&w64, NE));
     BCHK(B.alloc(&S64, B.s_elems)); BCHK(B.alloc(&S32, B.s_elems));
     BCHK(B.alloc(&b32, NE)); BCHK(B.alloc(&r32, NE)); BCHK(B.alloc(&p32, NE)); BCHK(B.alloc(&w32, NE));
-    BCHK(B.alloc(&c32, NE)); BCHK(B.alloc(&ynorm, nsys)); BCHK(B.alloc(&rn, nsys)); BCHK(B.alloc(&part, nsys));
+    BCHK(B.alloc(&c32, NE)); BCHK(B.alloc(&ynorm, nsys)); BCHK(B.alloc(&rn, nsys));
+    BCHK(B.alloc(&part, (size_t)B.nch * kc)); BCHK(B.alloc(&sysv, nsys));
     BCHK(B.alloc(&sc, (size_t)nsys * B_N)); BCHK(B.alloc(&skip, nsys)); BCHK(B.alloc(&flags, 4));
+    BCHK(B.alloc(&ypk, B.n_total));
     std::vector<double> hl(kc, 1.0);
     for (int c = 0; c < k; ++c) hl[c] = lambdas_host[c];
     if (cudaMemcpyAsync(lam, hl.data(), sizeof(double) * kc, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(B.it2, i2.data(), sizeof(int4) * i2.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(a64, 0, sizeof(double) * NE, s) != cudaSuccess ||
         cudaMemsetAsync(flags, 0, 16, s) != cudaSuccess)
         return ret(cuda_fail(cudaGetLastError(), "batched init"));
-
-    // ||y|| per system: pack y, broadcast it over the columns with W = 0
-    std::vector<double> hyn(nsys, 0.0);
-    double* ypk = nullptr;
-    BCHK(B.alloc(&ypk, B.n_total));
     for (int b = 0; b < B.P; ++b)
         if (B.hp[b].n > 0 &&
             cudaMemcpyAsync(ypk + B.hp[b].n_off, probs[b].y, 8 * (size_t)B.hp[b].n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return ret(cuda_fail(cudaGetLastError(), "batched y"));
+
+    // ||y|| per system: broadcast y over the columns (W = 0)
+    std::vector<double> hyn(nsys, 0.0);
     b_fill_kernel<double><<<gs(NE), 256, 0, s>>>(w64, NE, 0.0);
-    b_residual_kernel<<<B.P, kBT, 0, s>>>(B.probs, ypk, w64, r64, k, kc);
-    b_dot_kernel<double><<<B.P, kBT, 0, s>>>(B.probs, r64, r64, kc, ynorm);
-    count_launches(3);
+    b_residual_kernel<<<B.nch, kBT, 0, s>>>(B.chunks, B.probs, ypk, w64, r64, k, kc);
+    count_launches(2);
+    sys_dot<double>(B, r64, r64, part, ynorm, s);
     if (cudaMemcpyAsync(hyn.data(), ynorm, 8 * (size_t)nsys, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return ret(cuda_fail(cudaGetLastError(), "batched norms"));
@@ -545,8 +735,8 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
     const int grid1 = 152 * 8;
     {
         struct Cand { int tx, nt; };
-        const Cand cands[] = {{1, 128}, {2, 128}, {4, 128}, {2, 64}, {4, 64}};
-        const int ncand = 5;
+        const Cand cands[] = {{1, 128}, {2, 128}, {1, 64}, {2, 64}};
+        const int ncand = 4;
         std::vector<int4> i1;
         auto key = std::make_tuple(B.P, B.n_total, kc);
         auto itc = h->batch_tune.find(key);
@@ -591,7 +781,6 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
         B.n1 = (int)i1.size();
         if (cudaMemcpyAsync(B.it1, i1.data(), sizeof(int4) * i1.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return ret(cuda_fail(cudaGetLastError(), "batched items"));
-        info->refinements = 0;
     }
 
     // ---- one inner CG iteration (FP32 operator, FP64 scalars), captured as a CUDA graph
@@ -600,11 +789,12 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
     const unsigned sg = (unsigned)((nsys + 255) / 256);
     auto record_iter = [&](cudaStream_t cs) -> gvt_status {
         GVT_CHECK(apply<float>(B, B.M32, B.N32, p32, S32, w32, lam, grid1, cs));
-        b_dot_kernel<float><<<B.P, kBT, 0, cs>>>(B.probs, p32, w32, kc, part);
-        b_alpha_kernel<<<sg, 256, 0, cs>>>(part, sc, nsys, flags);
-        b_update_kernel<float><<<B.P, kBT, 0, cs>>>(B.probs, c32, r32, p32, w32, sc, kc, part);
-        b_beta_kernel<<<sg, 256, 0, cs>>>(part, sc, nsys, flags + 1);
-        b_pupdate_kernel<float><<<B.P, kBT, 0, cs>>>(B.probs, p32, r32, sc, kc);
+        sys_dot<float>(B, p32, w32, part, sysv, cs);
+        b_alpha_kernel<<<sg, 256, 0, cs>>>(sysv, sc, nsys, flags);
+        b_update_kernel<float><<<B.nch, kBT, 0, cs>>>(B.chunks, B.probs, c32, r32, p32, w32, sc, kc, part);
+        b_sys_sum_kernel<<<sg, 256, 0, cs>>>(part, B.cfirst, B.P, kc, sysv);
+        b_beta_kernel<<<sg, 256, 0, cs>>>(sysv, sc, nsys, flags + 1);
+        b_pupdate_kernel<float><<<B.nch, kBT, 0, cs>>>(B.chunks, B.probs, p32, r32, sc, kc);
         GVT_LAUNCHED(5, "batched CG iteration");
         return GVT_OK;
     };
@@ -627,6 +817,7 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
         cudaGraph_t g; cudaGraphExec_t e;
         ~GraphGuard() { if (e) cudaGraphExecDestroy(e); if (g) cudaGraphDestroy(g); }
     } guard{graph, gexec};
+    const int graph_kernels = 9;
 
     // ---- iterative refinement: FP64 residual, FP32 inner CG on the correction
     std::vector<double> hrn(nsys), hskip(nsys, 0.0);
@@ -636,9 +827,9 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
     for (int outer = 0; outer <= opts.max_refine; ++outer) {
         // r64 = y - (K a + lambda a)
         BCHK(apply<double>(B, B.M64, B.N64, a64, S64, w64, lam, grid1, s));
-        b_residual_kernel<<<B.P, kBT, 0, s>>>(B.probs, ypk, w64, r64, k, kc);
-        b_dot_kernel<double><<<B.P, kBT, 0, s>>>(B.probs, r64, r64, kc, rn);
-        count_launches(2);
+        b_residual_kernel<<<B.nch, kBT, 0, s>>>(B.chunks, B.probs, ypk, w64, r64, k, kc);
+        count_launches(1);
+        sys_dot<double>(B, r64, r64, part, rn, s);
         if (cudaMemcpyAsync(hrn.data(), rn, 8 * (size_t)nsys, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return ret(cuda_fail(cudaGetLastError(), "batched residual"));
@@ -664,17 +855,17 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
         if (cudaMemcpyAsync(rn, hrn.data(), 8 * (size_t)nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(skip, hskip.data(), 8 * (size_t)nsys, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return ret(cuda_fail(cudaGetLastError(), "batched upload"));
-        b_scale_kernel<<<B.P, kBT, 0, s>>>(B.probs, r64, rn, b32, r32, p32, c32, kc);
-        b_dot_kernel<float><<<B.P, kBT, 0, s>>>(B.probs, r32, r32, kc, part);
+        b_scale_kernel<<<B.nch, kBT, 0, s>>>(B.chunks, B.probs, r64, rn, b32, r32, p32, c32, kc);
+        count_launches(1);
+        sys_dot<float>(B, r32, r32, part, sysv, s);
         const double itol = std::max(opts.inner_tol, 1e-6);
-        b_init_scal_kernel<<<sg, 256, 0, s>>>(part, sc, nsys, k, kc, itol, skip);
-        count_launches(3);
+        b_init_scal_kernel<<<sg, 256, 0, s>>>(sysv, sc, nsys, k, kc, itol, skip);
+        count_launches(1);
         int64_t it = 0;
         while (total_it + it < opts.max_iter) {
-            if (cudaMemsetAsync(flags + 1, 0, 4, s) != cudaSuccess ||
-                cudaGraphLaunch(gexec, s) != cudaSuccess)
+            if (cudaMemsetAsync(flags + 1, 0, 4, s) != cudaSuccess || cudaGraphLaunch(gexec, s) != cudaSuccess)
                 return ret(cuda_fail(cudaGetLastError(), "graph launch"));
-            count_launches(7);
+            count_launches(graph_kernels);
             ++it;
             if (it % check == 0) {
                 int hf[2];
@@ -685,7 +876,7 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
             }
         }
         total_it += it;
-        b_correct_kernel<<<B.P, kBT, 0, s>>>(B.probs, a64, c32, rn, kc);
+        b_correct_kernel<<<B.nch, kBT, 0, s>>>(B.chunks, B.probs, a64, c32, rn, kc);
         count_launches(1);
     }
     info->iterations = total_it;
