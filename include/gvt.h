@@ -275,6 +275,11 @@ typedef struct gvt_solve_opts {
     double inner_tol;        /* MIXED_IR inner relative tolerance (default 1e-3) */
     int32_t max_refine;      /* MIXED_IR outer steps (default 30) */
     int32_t check_every;     /* CG iterations between host convergence checks (default 1) */
+    int32_t precond_budget;  /* flexible-CG iterations allowed (per inner solve in MIXED_IR) before
+                                the solve falls back to plain CG from the current iterate;
+                                0 (default): max_iter / 2 */
+    const struct gvt_precond* precond;  /* learned preconditioner for flexible CG (NULL: plain CG);
+                                           applies to the FP64 CG and to MIXED_IR's inner solves */
 } gvt_solve_opts;
 
 typedef struct gvt_solve_info {
@@ -283,7 +288,12 @@ typedef struct gvt_solve_info {
     int32_t status;          /* gvt_status of the solve */
     double rel_residual;     /* final ||y - (K+lambda I)a|| / ||y||, recomputed in FP64 */
     double time_ms;          /* wall-clock time of the solve on the host */
+    int32_t precond_fallback;  /* 1 if flexible CG broke down or ran out of its budget and
+                                  plain CG took over (the preconditioner is then ignored) */
+    int32_t reserved;
 } gvt_solve_info;
+
+typedef struct gvt_precond gvt_precond;
 
 /* Fill `o` with the defaults listed in gvt_solve_opts. */
 gvt_status gvt_solve_opts_default(gvt_solve_opts* o);
@@ -305,6 +315,76 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
                             const gvt_matrix* M, const gvt_matrix* N,
                             const double* y, double lambda, double* a,
                             const gvt_solve_opts* opts, gvt_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------ learned preconditioner */
+
+/*
+ * A learned symmetric positive definite preconditioner P ~ (K + lambda I)^{-1}
+ * for the training pairs of a plan.  A small MLP (6 -> 128 -> 128 -> 33, ReLU)
+ * maps per-pair features -- the kernel diagonals M[d,d], N[t,t], log(1 + degree)
+ * of the pair's drug and target, and the signed logs sign(x) log(1 + |x|) of the
+ * kernel-graph degrees g1 = K 1 and g2 = K (g1 / mean g1) (two power-iteration
+ * steps of the pairwise kernel matrix K), each normalised to zero mean and unit
+ * deviation over the pairs -- to D_i = c softplus(o_0) and V_i = o_{1..32}
+ * (c: a fixed output scale, see gvt_precond_scale);
+ *     P r = S (I + V V^T)^{-1} S r,   S = diag(sqrt(D)),
+ * a diagonal matrix minus a rank-32 term (Woodbury form), SPD for any network
+ * output.  The paper solves with an unpreconditioned method (Sec. 6); this is
+ * an addition used with flexible CG, whose true residual stays the judge.
+ * Parameters: gvt_precond_num_params() floats, layout W1[128x6] b1[128]
+ * W2[128x128] b2[128] W3[33x128] b3[33] (row-major).
+ */
+int64_t gvt_precond_num_params(void);
+
+/* Create for a training plan, the pairwise kernel `desc` and its FP64 kernel
+ * matrices (the features need two products with K), with initial parameters
+ * theta_host.  Synchronises. */
+gvt_status gvt_precond_create(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                              const gvt_matrix* N, const float* theta_host, void* stream, gvt_precond** out);
+gvt_status gvt_precond_destroy(gvt_precond* p);
+
+/* Copy parameters to (set = 0) or from (set != 0) host memory.  Synchronises. */
+gvt_status gvt_precond_params(gvt_precond* p, float* theta_host, int32_t set, void* stream);
+
+/* Normalisation (host, 12 floats: mean[6], deviation[6]) and normalised
+ * features (device, n x 6 row-major); either pointer may be NULL. */
+gvt_status gvt_precond_features(gvt_precond* p, float* mu_sd_host, float* X_dev, void* stream);
+
+/* Network outputs o (device, n x 33 row-major) for the current parameters. */
+gvt_status gvt_precond_outputs(gvt_precond* p, float* O_dev, void* stream);
+
+/* z = P r for device vectors of n elements, dtype GVT_F32 or GVT_F64. */
+gvt_status gvt_precond_apply(gvt_precond* p, const void* r, void* z, int32_t dtype, void* stream);
+
+/* Loss  L = (1/K) sum_k ||P r_k - e_k||^2 / ||e_k||^2  over K <= 16 pairs
+ * (R, E: device FP32, n x K column-major) and its gradient with respect to the
+ * parameters (host, num_params floats), by the library's forward and backward
+ * kernels.  Either output may be NULL.  Synchronises. */
+gvt_status gvt_precond_loss_grad(gvt_precond* p, const float* R, const float* E, int64_t K, double* loss_host,
+                                 float* grad_host, void* stream);
+
+/* Output scale c of D = c softplus(o_0): read into *get and/or set from *set
+ * (either may be NULL).  The first gvt_precond_train call sets
+ * c = sum e.e / sum r.e over its training pairs (the least-squares fit of
+ * r ~ e / c, close to 1 / lambda). */
+gvt_status gvt_precond_scale(gvt_precond* p, double* get, const double* set);
+
+/* `steps` Adam steps (learning rate lr) on minibatches of `batch` <= 16
+ * consecutive columns of the K_total pairs (R, E as above), cycling.
+ * loss_history (host, may be NULL) receives each step's minibatch loss. */
+gvt_status gvt_precond_train(gvt_precond* p, const float* R, const float* E, int64_t K_total, int32_t steps,
+                             int32_t batch, double lr, double* loss_history, void* stream);
+
+/*
+ * Training data for the preconditioner from the exact solver: plain FP64 CG
+ * from a = 0 on (K_desc + lambda I) a = y; at the iterations listed in iters
+ * (host, ascending, `count` of them) the residual r_k and the correction
+ * e_k = a_star - a_k (a_star: device FP64, the converged solution) are stored
+ * as FP32 columns of R and E (device, n x count).  Synchronises.
+ */
+gvt_status gvt_cg_record_pairs(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                               const gvt_matrix* N, const double* y, double lambda, const double* a_star,
+                               const int64_t* iters, int64_t count, float* R, float* E, void* stream);
 
 /* ------------------------------------------------------------ batched solves */
 

@@ -228,6 +228,11 @@ template <class T>
 gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
                           const gvt_matrix* N, const T* v, T* u, cudaStream_t s);
 
+// ---------------------------------------------------------------- learned preconditioner
+template <class T>
+gvt_status precond_apply(gvt_precond* p, const T* r, T* z, cudaStream_t s);
+int64_t precond_size(const gvt_precond* p);
+
 // ---------------------------------------------------------------- vector kernels (CG)
 template <class T>
 gvt_status vec_zero(T* x, int64_t n, cudaStream_t s);

@@ -22,7 +22,7 @@ namespace {
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
 
-enum Scal { SC_RR = 0, SC_PW, SC_ALPHA, SC_BETA, SC_FLAG, SC_RR0, SC_TMP, SC_COUNT };
+enum Scal { SC_RR = 0, SC_PW, SC_ALPHA, SC_BETA, SC_FLAG, SC_RR0, SC_TMP, SC_RZ, SC_ZW, SC_COUNT };
 
 __device__ double block_sum(double x)
 {
@@ -90,8 +90,29 @@ finalize_kernel(const double* __restrict__ part, int nb, double* __restrict__ sc
         sc[SC_RR] = acc;
         sc[SC_RR0] = acc;
         sc[SC_FLAG] = 0.0;
-    } else {                    // plain dot into SC_TMP
+    } else if (what == 3) {     // plain dot into SC_TMP
         sc[SC_TMP] = acc;
+    } else if (what == 4) {     // flexible CG start: rz = r.z
+        sc[SC_RZ] = acc;
+        if (!isfinite(acc) || !(acc > 0.0)) sc[SC_FLAG] = 1.0;
+    } else if (what == 5) {     // flexible CG: alpha = rz / pw
+        sc[SC_PW] = acc;
+        if (!(acc > 0.0) || !isfinite(acc)) {
+            sc[SC_FLAG] = 1.0;
+            sc[SC_ALPHA] = 0.0;
+        } else {
+            sc[SC_ALPHA] = sc[SC_RZ] / acc;
+        }
+    } else if (what == 6) {     // rr only
+        sc[SC_RR] = acc;
+        if (!isfinite(acc)) sc[SC_FLAG] = 1.0;
+    } else if (what == 7) {     // z.w
+        sc[SC_ZW] = acc;
+    } else {                    // what == 8: Polak-Ribiere beta = z'.(r' - r) / rz = -alpha z'.w / rz
+        const double rz = sc[SC_RZ];
+        sc[SC_BETA] = rz != 0.0 ? -sc[SC_ALPHA] * sc[SC_ZW] / rz : 0.0;
+        sc[SC_RZ] = acc;
+        if (!isfinite(acc) || !(acc > 0.0)) sc[SC_FLAG] = 1.0;
     }
 }
 
@@ -144,6 +165,16 @@ __global__ void axpy_f32_kernel(double* __restrict__ a, const float* __restrict_
         a[i] += scale * (double)c[i];
 }
 
+// R = (float) r ; E = (float) (a_star - x)
+__global__ void record_kernel(const double* __restrict__ r, const double* __restrict__ x,
+                              const double* __restrict__ a_star, int64_t n, float* __restrict__ R, float* __restrict__ E)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        R[i] = (float)r[i];
+        E[i] = (float)(a_star[i] - x[i]);
+    }
+}
+
 template <class T>
 __global__ void copy_kernel(T* __restrict__ dst, const T* __restrict__ src, int64_t n)
 {
@@ -159,14 +190,15 @@ unsigned vgrid(int64_t n)
     return (unsigned)g;
 }
 
-// Plain CG on (K + lambda I) x = b with operator dtype T; x has type TA.
-// x starts at zero.  Returns iterations used through *iters and the final
-// recursive relative residual through *rel.
+// CG on (K + lambda I) x = b with operator dtype T; x has type TA and starts
+// at zero.  With a preconditioner P this is flexible CG (Polak-Ribiere beta,
+// z = P r; z is a scratch vector).  Returns iterations used through *iters and
+// the final recursive relative residual through *rel.
 template <class T, class TA>
 gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, const gvt_matrix* N,
                   const T* b, double bnorm, double lam, TA* x, T* r, T* p, T* w, double* part, double* sc,
                   double* hsc, double tol, int64_t max_iter, int check_every, int64_t* iters, double* rel,
-                  cudaStream_t s)
+                  cudaStream_t s, gvt_precond* P = nullptr, T* z = nullptr)
 {
     const int64_t n = plan->n_in;
     *iters = 0;
@@ -176,20 +208,43 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
         return GVT_OK;
     }
     copy_kernel<T><<<vgrid(n), 256, 0, s>>>(r, b, n);
-    copy_kernel<T><<<vgrid(n), 256, 0, s>>>(p, b, n);
     dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
     finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 2);
-    GVT_LAUNCHED(4, "cg init");
+    GVT_LAUNCHED(3, "cg init");
+    if (P) {
+        GVT_CHECK(precond_apply<T>(P, r, z, s));
+        copy_kernel<T><<<vgrid(n), 256, 0, s>>>(p, z, n);
+        dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(r, z, n, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 4);
+        GVT_LAUNCHED(3, "fcg init");
+    } else {
+        copy_kernel<T><<<vgrid(n), 256, 0, s>>>(p, b, n);
+        GVT_LAUNCH_CHECK("cg init");
+    }
     if (check_every < 1) check_every = 1;
     int64_t it = 0;
     while (it < max_iter) {
         GVT_CHECK(pairwise_apply<T>(plan, desc, M, N, p, w, s));
         shift_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lam, n, part);
-        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
-        update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
-        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
-        pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
-        GVT_LAUNCHED(5, "cg iteration");
+        if (!P) {
+            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
+            update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
+            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
+            pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
+            GVT_LAUNCHED(5, "cg iteration");
+        } else {
+            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 5);
+            update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
+            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 6);
+            GVT_LAUNCHED(4, "fcg iteration");
+            GVT_CHECK(precond_apply<T>(P, r, z, s));
+            dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(z, w, n, part);
+            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 7);
+            dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(r, z, n, part);
+            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 8);
+            pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, z, n, sc);
+            GVT_LAUNCHED(5, "fcg iteration");
+        }
         ++it;
         if (it % check_every == 0 || it == max_iter) {
             GVT_CUDA(cudaMemcpyAsync(hsc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -245,6 +300,8 @@ gvt_status gvt_solve_opts_default(gvt_solve_opts* o)
     o->inner_tol = 1e-3;
     o->max_refine = 30;
     o->check_every = 1;
+    o->precond_budget = 0;
+    o->precond = nullptr;
     return GVT_OK;
 }
 
@@ -283,6 +340,11 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         return ret(GVT_ERR_UNSUPPORTED);
     }
     const int64_t n = plan->n_in;
+    gvt_precond* P = const_cast<gvt_precond*>(opts.precond);
+    if (P && precond_size(P) != n) {
+        set_error("gvt_krr_cg_solve: the preconditioner was built for a different number of pairs");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
     if (n > 0 && (!y || !a)) {
         set_error("gvt_krr_cg_solve: y or a is NULL");
         return ret(GVT_ERR_INVALID_ARG);
@@ -298,12 +360,16 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool homo = desc->homogeneous != 0;
     const gvt_matrix* Nn = homo ? M : N;
+    // flexible-CG iterations before the plain-CG fallback
+    const int64_t pbudget = opts.precond_budget > 0 ? std::min<int64_t>(opts.precond_budget, opts.max_iter)
+                                                    : std::max<int64_t>(1, opts.max_iter / 2);
 
     // ---- solver workspace
     Arena& ws = h->solve_ws;
     ws.reset();
     const size_t o_r = ws.take(8 * n), o_p = ws.take(8 * n), o_w = ws.take(8 * n), o_y = ws.take(8 * n);
     const size_t o_part = ws.take(8 * kRedBlocks), o_sc = ws.take(8 * SC_COUNT);
+    size_t o_z = (P && opts.mode == GVT_SOLVE_FP64_CG) ? ws.take(8 * n) : 0;
     size_t o_m32 = 0, o_n32 = 0, o_r32 = 0, o_p32 = 0, o_w32 = 0, o_c32 = 0, o_q32 = 0;
     const bool mixed = opts.mode == GVT_SOLVE_MIXED_IR;
     if (mixed) {
@@ -311,6 +377,7 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         if (!homo) o_n32 = ws.take(4 * (size_t)Nn->rows * Nn->ld);
         o_r32 = ws.take(4 * n); o_p32 = ws.take(4 * n); o_w32 = ws.take(4 * n); o_c32 = ws.take(4 * n);
         o_q32 = ws.take(4 * n);
+        if (P) o_z = ws.take(4 * n);
     }
     gvt_status st = ws.commit(s);
     if (st != GVT_OK) return ret(st);
@@ -351,8 +418,21 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         double rel = 1.0;
         // CG on the correction: stop when ||r|| <= rel_tol * ||y||
         st = cg_run<double, double>(plan, desc, M, Nn, ytmp, rn, lambda, a, r, p, w, part, sc, hsc,
-                                    opts.rel_tol * ynorm / rn, opts.max_iter, opts.check_every, &its, &rel, s);
+                                    opts.rel_tol * ynorm / rn, P ? pbudget : opts.max_iter, opts.check_every,
+                                    &its, &rel, s, P, P ? (double*)(base + o_z) : nullptr);
         info->iterations = its;
+        if (P && (st == GVT_ERR_NOT_CONVERGED || st == GVT_ERR_BREAKDOWN)) {
+            // fallback: plain CG from the current iterate with the remaining iterations
+            info->precond_fallback = 1;
+            st = fp64_residual(plan, desc, M, Nn, y, a, lambda, w, ytmp, part, sc, hsc, &rn, s);
+            if (st != GVT_OK) return ret(st);
+            if (rn / ynorm <= opts.rel_tol) return finish(GVT_OK);
+            int64_t its2 = 0;
+            st = cg_run<double, double>(plan, desc, M, Nn, ytmp, rn, lambda, a, r, p, w, part, sc, hsc,
+                                        opts.rel_tol * ynorm / rn, opts.max_iter - its, opts.check_every, &its2,
+                                        &rel, s);
+            info->iterations = its + its2;
+        }
         return finish(st);
     }
 
@@ -393,8 +473,10 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         const double inner_tol = std::max(opts.inner_tol, 0.5 * opts.rel_tol * ynorm / rn);
         const int saved_engine = plan->h->stage1_engine;
         if (opts.inner_dtype == GVT_BF16) plan->h->stage1_engine = GVT_STAGE1_TC_BF16X3;
+        const int64_t inner_budget = P ? std::min(pbudget, opts.max_iter - total) : opts.max_iter - total;
         st = cg_run<float, float>(plan, desc, &M32, &N32, r32, 1.0, lambda, c32, q32, p32, w32, part, sc,
-                                  hsc, inner_tol, opts.max_iter - total, opts.check_every, &its, &rel, s);
+                                  hsc, inner_tol, inner_budget, opts.check_every, &its, &rel, s,
+                                  P, P ? (float*)(base + o_z) : nullptr);
         plan->h->stage1_engine = saved_engine;
         if (opts.inner_dtype == GVT_BF16) {
             int word = 0;
@@ -409,7 +491,12 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
             }
         }
         total += its;
-        if (st == GVT_ERR_BREAKDOWN) {
+        if (P && (st == GVT_ERR_NOT_CONVERGED || st == GVT_ERR_BREAKDOWN)) {
+            // fallback: the remaining inner solves run plain CG; a broken-down correction is dropped
+            info->precond_fallback = 1;
+            P = nullptr;
+            if (st == GVT_ERR_BREAKDOWN) continue;
+        } else if (st == GVT_ERR_BREAKDOWN) {
             info->iterations = total;
             return finish(st);
         }
@@ -418,6 +505,61 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
     }
     info->iterations = total;
     return finish(GVT_ERR_NOT_CONVERGED);
+}
+
+gvt_status gvt_cg_record_pairs(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                               const gvt_matrix* N, const double* y, double lambda, const double* a_star,
+                               const int64_t* iters, int64_t count, float* R, float* E, void* stream)
+{
+    if (!h || !plan || !desc || !M || !y || !a_star || !iters || count < 1 || !R || !E || !plan->out_is_in ||
+        !(lambda > 0.0) || M->dtype != GVT_F64) {
+        set_error("gvt_cg_record_pairs: bad argument");
+        return GVT_ERR_INVALID_ARG;
+    }
+    for (int64_t j = 1; j < count; ++j)
+        if (iters[j] <= iters[j - 1] || iters[0] < 0) {
+            set_error("gvt_cg_record_pairs: iterations must be ascending and >= 0");
+            return GVT_ERR_INVALID_ARG;
+        }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = plan->n_in;
+    const gvt_matrix* Nn = desc->homogeneous ? M : N;
+    Arena& ws = h->solve_ws;
+    ws.reset();
+    const size_t o_x = ws.take(8 * n), o_r = ws.take(8 * n), o_p = ws.take(8 * n), o_w = ws.take(8 * n);
+    const size_t o_part = ws.take(8 * kRedBlocks), o_sc = ws.take(8 * SC_COUNT);
+    GVT_CHECK(ws.commit(s));
+    char* base = ws.base();
+    double* x = (double*)(base + o_x);
+    double* r = (double*)(base + o_r);
+    double* p = (double*)(base + o_p);
+    double* w = (double*)(base + o_w);
+    double* part = (double*)(base + o_part);
+    double* sc = (double*)(base + o_sc);
+    GVT_CHECK(vec_zero<double>(x, n, s));
+    copy_kernel<double><<<vgrid(n), 256, 0, s>>>(r, y, n);
+    copy_kernel<double><<<vgrid(n), 256, 0, s>>>(p, y, n);
+    dot_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
+    finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 2);
+    GVT_LAUNCHED(4, "record init");
+    int64_t j = 0;
+    for (int64_t it = 0; j < count; ++it) {
+        if (it == iters[j]) {
+            record_kernel<<<vgrid(n), 256, 0, s>>>(r, x, a_star, n, R + j * n, E + j * n);
+            GVT_LAUNCH_CHECK("record");
+            ++j;
+            if (j == count) break;
+        }
+        GVT_CHECK(pairwise_apply<double>(plan, desc, M, Nn, p, w, s));
+        shift_dot_kernel<double><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lambda, n, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
+        update_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
+        pupdate_kernel<double><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
+        GVT_LAUNCHED(5, "record iteration");
+    }
+    GVT_CUDA(cudaStreamSynchronize(s));
+    return GVT_OK;
 }
 
 }  // extern "C"

@@ -49,12 +49,12 @@ class gvt_matrix(ctypes.Structure):
 class gvt_solve_opts(ctypes.Structure):
     _fields_ = [("rel_tol", c_dbl), ("max_iter", c_i64), ("mode", c_i32),
                 ("inner_dtype", c_i32), ("inner_tol", c_dbl), ("max_refine", c_i32),
-                ("check_every", c_i32)]
+                ("check_every", c_i32), ("precond_budget", c_i32), ("precond", c_vp)]
 
 
 class gvt_solve_info(ctypes.Structure):
     _fields_ = [("iterations", c_i64), ("refinements", c_i32), ("status", c_i32),
-                ("rel_residual", c_dbl), ("time_ms", c_dbl)]
+                ("rel_residual", c_dbl), ("time_ms", c_dbl), ("precond_fallback", c_i32), ("reserved", c_i32)]
 
 
 class gvt_kernel_stats(ctypes.Structure):
@@ -105,6 +105,19 @@ SIGNATURES = [
     ("gvt_krr_cg_solve_batched", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, _P(gvt_solve_opts), c_vp,
                                          _P(gvt_solve_info), c_vp]),
     ("gvt_set_stage1_engine", c_i32, [c_vp, c_i32]),
+    ("gvt_precond_num_params", c_i64, []),
+    ("gvt_precond_create", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
+                                   _P(c_vp)]),
+    ("gvt_precond_destroy", c_i32, [c_vp]),
+    ("gvt_precond_params", c_i32, [c_vp, c_vp, c_i32, c_vp]),
+    ("gvt_precond_features", c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    ("gvt_precond_outputs", c_i32, [c_vp, c_vp, c_vp]),
+    ("gvt_precond_apply", c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
+    ("gvt_precond_loss_grad", c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    ("gvt_precond_scale", c_i32, [c_vp, c_vp, c_vp]),
+    ("gvt_precond_train", c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_vp, c_vp]),
+    ("gvt_cg_record_pairs", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
+                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     ("gvt_check_device_errors", c_i32, [c_vp, c_vp]),
     ("gvt_tc_gemm_bf16", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]),
     ("gvt_matvec_static", c_i32, [c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
@@ -262,6 +275,104 @@ def krr_solve_batched(handle, problems, lambdas, rel_tol=1e-6, inner_tol=1e-3, m
     return [a.t() for a in outs], st, info, rr
 
 
+class Precond:
+    """Learned preconditioner of a training plan (gvt_precond_*)."""
+
+    def __init__(self, handle, plan, kind, M, N, theta, symmetric=True, stream=None):
+        import numpy as np
+        self.n_params = int(load().gvt_precond_num_params())
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self.n_params
+        self.p = c_vp()
+        _call("gvt_precond_create", handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
+              ctypes.byref(matrix(N, symmetric)) if N is not None else None, th.ctypes.data_as(c_vp),
+              stream_ptr(stream), ctypes.byref(self.p))
+        self.n = plan.n_in
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _call("gvt_precond_params", self.p, out.ctypes.data_as(c_vp), 0, stream_ptr())
+        return out
+
+    def set_params(self, theta):
+        import numpy as np
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _call("gvt_precond_params", self.p, th.ctypes.data_as(c_vp), 1, stream_ptr())
+
+    def features(self):
+        import numpy as np
+        torch = _torch()
+        musd = np.zeros(12, dtype=np.float32)
+        X = torch.empty((self.n, 6), dtype=torch.float32, device="cuda")
+        _call("gvt_precond_features", self.p, musd.ctypes.data_as(c_vp), ptr(X), stream_ptr())
+        torch.cuda.synchronize()
+        return musd[:6], musd[6:], X
+
+    def outputs(self):
+        torch = _torch()
+        O = torch.empty((self.n, 33), dtype=torch.float32, device="cuda")
+        _call("gvt_precond_outputs", self.p, ptr(O), stream_ptr())
+        torch.cuda.synchronize()
+        return O
+
+    def apply(self, r):
+        z = _torch().empty_like(r)
+        _call("gvt_precond_apply", self.p, ptr(r), ptr(z), dtype_code(r), stream_ptr())
+        return z
+
+    def loss_grad(self, R, E):
+        """R, E: CUDA float32 tensors n x K (K <= 16)."""
+        import numpy as np
+        Rc, Ec = R.t().contiguous(), E.t().contiguous()   # column-major n x K
+        loss = c_dbl()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        _call("gvt_precond_loss_grad", self.p, ptr(Rc), ptr(Ec), R.shape[1], ctypes.byref(loss),
+              g.ctypes.data_as(c_vp), stream_ptr())
+        return loss.value, g
+
+    def scale(self, value=None):
+        get = c_dbl()
+        if value is not None:
+            v = c_dbl(value)
+            _call("gvt_precond_scale", self.p, ctypes.byref(get), ctypes.byref(v))
+        else:
+            _call("gvt_precond_scale", self.p, ctypes.byref(get), None)
+        return get.value
+
+    def train(self, R, E, steps, batch=8, lr=1e-3):
+        import numpy as np
+        Rc, Ec = R.t().contiguous(), E.t().contiguous()
+        hist = np.zeros(max(steps, 1))
+        _call("gvt_precond_train", self.p, ptr(Rc), ptr(Ec), R.shape[1], steps, batch, float(lr),
+              hist.ctypes.data_as(c_vp), stream_ptr())
+        return hist[:steps]
+
+    def close(self):
+        if getattr(self, "p", None) is not None:
+            _call("gvt_precond_destroy", self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cg_record_pairs(handle, plan, kind, M, N, y, lam, a_star, iters, symmetric=True, stream=None):
+    """(R, E) float32 n x len(iters): residuals and corrections a* - a_k of plain FP64 CG."""
+    import numpy as np
+    torch = _torch()
+    it = np.ascontiguousarray(iters, dtype=np.int64)
+    R = torch.empty((len(it), plan.n_in), dtype=torch.float32, device="cuda")
+    E = torch.empty_like(R)
+    _call("gvt_cg_record_pairs", handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
+          ctypes.byref(matrix(N, symmetric)) if N is not None else None, ptr(y), float(lam), ptr(a_star),
+          it.ctypes.data_as(c_vp), len(it), ptr(R), ptr(E), stream_ptr(stream))
+    return R.t(), E.t()
+
+
 def gvt_set_stage1_engine(h, engine):
     _call("gvt_set_stage1_engine", h, engine)
 
@@ -413,13 +524,15 @@ def gaussian_kernel(handle, X, Y=None, gamma=1.0, dtype=None, stream=None):
 
 def krr_cg_solve(handle, plan, kind, M, N, y, lam, a0=None, mode=GVT_SOLVE_FP64_CG, rel_tol=1e-6,
                  max_iter=10000, inner_tol=1e-3, check_every=1, symmetric=True, stream=None,
-                 inner_dtype=GVT_F32):
+                 inner_dtype=GVT_F32, precond=None, precond_budget=0):
     """Solve (K + lam I) a = y; returns (a, status, info)."""
     torch = _torch()
     a = torch.zeros_like(y) if a0 is None else a0.clone()
     o = gvt_solve_opts_default()
     o.rel_tol, o.max_iter, o.mode, o.inner_tol, o.check_every = rel_tol, max_iter, mode, inner_tol, check_every
     o.inner_dtype = inner_dtype
+    o.precond = precond.p if precond is not None else None
+    o.precond_budget = precond_budget
     st, info = gvt_krr_cg_solve(handle.h, plan.p, _desc(kind), matrix(M, symmetric),
                                 matrix(N, symmetric) if N is not None else None,
                                 ptr(y), float(lam), ptr(a), o, stream_ptr(stream))

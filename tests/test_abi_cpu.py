@@ -61,8 +61,9 @@ def test_struct_layout_matches_c(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(gvt_term), sizeof(gvt_desc), sizeof(gvt_matrix),
          sizeof(gvt_solve_opts), sizeof(gvt_solve_info));
-  printf("%zu %zu %zu %zu\\n", offsetof(gvt_desc, terms), offsetof(gvt_matrix, dtype),
-         offsetof(gvt_solve_opts, inner_tol), offsetof(gvt_solve_info, rel_residual));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(gvt_desc, terms), offsetof(gvt_matrix, dtype),
+         offsetof(gvt_solve_opts, inner_tol), offsetof(gvt_solve_info, rel_residual),
+         offsetof(gvt_solve_opts, precond), offsetof(gvt_solve_info, precond_fallback));
   return 0;
 }
 """)
@@ -74,7 +75,8 @@ int main(void) {
     assert sizes == [ctypes.sizeof(gvt.gvt_term), ctypes.sizeof(gvt.gvt_desc), ctypes.sizeof(gvt.gvt_matrix),
                      ctypes.sizeof(gvt.gvt_solve_opts), ctypes.sizeof(gvt.gvt_solve_info)]
     assert offs == [gvt.gvt_desc.terms.offset, gvt.gvt_matrix.dtype.offset,
-                    gvt.gvt_solve_opts.inner_tol.offset, gvt.gvt_solve_info.rel_residual.offset]
+                    gvt.gvt_solve_opts.inner_tol.offset, gvt.gvt_solve_info.rel_residual.offset,
+                    gvt.gvt_solve_opts.precond.offset, gvt.gvt_solve_info.precond_fallback.offset]
 
 
 EXPECTED_TERMS = {"kronecker": 1, "gaussian": 1, "linear": 2, "poly2d": 3, "cartesian": 2,
@@ -143,4 +145,5 @@ def test_argument_errors_return_status_and_message(lib):
 def test_solve_defaults(lib):
     o = gvt.gvt_solve_opts_default()
     assert o.rel_tol == 1e-6 and o.mode == gvt.GVT_SOLVE_FP64_CG and o.inner_tol == 1e-3
+    assert o.precond_budget == 0 and not o.precond
     assert gvt.gvt_version() >= 10000
