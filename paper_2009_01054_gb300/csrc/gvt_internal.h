@@ -220,7 +220,7 @@ size_t dense_stage1_workspace(int64_t Y, int64_t K, int64_t X);
 // S[Y x X] = B[Y x K] W with W densified from the sources (keys[si][j] = column x of entry j)
 gvt_status dense_stage1(const float* B, int64_t ldb, int64_t Y, int64_t K, int square, const S1Sources& srcs,
                         const int32_t* const keys[kMaxSources], int64_t n, const float* v, int64_t X, float* S,
-                        int64_t lds, void* ws, int* err, cudaStream_t s);
+                        int64_t lds, void* ws, int reuse_a, int* err, cudaStream_t s);
 
 // ---------------------------------------------------------------- pairwise driver
 // u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).

@@ -244,6 +244,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
 
     // ---- two-sided groups, grouped by shared stage 1
     std::vector<bool> done(C.two.size(), false);
+    // the dense stage 1's BF16 split of its factor stays valid in the workspace for the
+    // next group with the same factor, square mode and extents
+    const void* split_of = nullptr;
+    int split_sq = -1;
+    int64_t split_Y = -1, split_K = -1;
     T* S = reinterpret_cast<T*>(base + off_S);
     for (size_t gi = 0; gi < C.two.size(); ++gi) {
         if (done[gi]) continue;
@@ -275,9 +280,14 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             const int64_t K = in_range(plan, ib);
             StatScope st(h, s, GVT_STAT_STAGE1, 2.0 * 3.0 * Y * (double)((K + 63) / 64 * 64) * X,
                          2.0 * (3.0 * (Y + X) * ((K + 63) / 64 * 64)) + sz * Y * X + E * (8 + sz));
+            const int reuse = split_of == Bm->data && split_sq == sq_mode(g.fb) && split_Y == Y && split_K == K;
             GVT_CHECK(dense_stage1(reinterpret_cast<const float*>(Bm->data), Bm->ld, Y, K, sq_mode(g.fb), srcs, keys,
                                    plan->n_in, reinterpret_cast<const float*>(v), X, reinterpret_cast<float*>(S), lds,
-                                   base + off_tc, handle_err_word(h), s));
+                                   base + off_tc, reuse, handle_err_word(h), s));
+            split_of = Bm->data;
+            split_sq = sq_mode(g.fb);
+            split_Y = Y;
+            split_K = K;
         } else if (g.fb == GVT_FACTOR_IDENTITY) {
             GVT_CHECK(vec_zero<T>(S, Y * lds, s));
             StatScope st(h, s, GVT_STAT_STAGE1, E, sz * Y * X + E * (8 + sz));
