@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--engine", default="simt", choices=["simt", "tc"],
-                    help="stage-1 engine of the FP32 products: sparse SIMT, or tcgen05 BF16x3 on densified W")
+    ap.add_argument("--engine", default="auto", choices=["simt", "tc", "tc16", "auto"],
+                    help="engine of the FP32 products: sparse SIMT stages; tc = stage 1 as a tcgen05 BF16x3 "
+                         "GEMM; tc16 = both stages as tcgen05 FP16x3 GEMMs; auto = per-stage cost model")
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=256)
@@ -163,16 +164,25 @@ def cpu_oracle_rate(p, seconds, rows_per_call=64, seed=0):
     return rate, el, rows_done, orc.num_threads()
 
 
+# arithmetic of the products per engine: FP32 SIMT, or 16-bit hi/lo splits on the tensor cores
+# with FP32 accumulation (the measured error against FP64 is reported beside it)
+DTYPE_OF_ENGINE = {"simt": "f32", "tc": "bf16x3 stage 1 + f32 stage 2", "tc16": "f16x3 (f32 accumulate)",
+                   "auto": "f16x3 (f32 accumulate) where dense, else f32"}
+
+KERNEL_SOURCE = {"stage1_dense_kernel": "stages.cu", "stage2_dense_kernel": "stages.cu",
+                 "gemv_rows_kernel": "stages.cu", "tc_gemm_kernel": "tc_gemm.cu"}
+
+
 def traffic_for(kernel_name):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2009_01054_gb300", "csrc", "stages.cu"), "rb").read()
-        if rec.get("stages_cu_sha256") != hashlib.sha256(src).hexdigest():
+            rec = json.load(f).get("kernels", {}).get(kernel_name)
+        src = open(os.path.join(ROOT, "paper_2009_01054_gb300", "csrc", KERNEL_SOURCE[kernel_name]), "rb").read()
+        if not rec or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
             return None
-        return rec.get("kernels", {}).get(kernel_name, {}).get("dram_bytes_per_launch")
+        return rec.get("dram_bytes_per_launch")
     except Exception:
         return None
 
@@ -240,8 +250,9 @@ def run_gvt(args, ws, rank, local):
     descs = [gvt.gvt_desc_make(k) for k in KINDS]
     Mm = gvt.matrix(M, symmetric=True)
     sp = gvt.stream_ptr()
-    if args.engine == "tc":
-        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_TC_BF16X3)
+    engine_code = {"simt": gvt.GVT_STAGE1_SIMT, "tc": gvt.GVT_STAGE1_TC_BF16X3, "tc16": gvt.GVT_STAGES_TC_F16X3,
+                   "auto": gvt.GVT_STAGES_AUTO}[args.engine]
+    gvt.gvt_set_stage1_engine(H.h, engine_code)
     stream = torch.cuda.current_stream()
     vp = gvt.ptr(v)
     up = [gvt.ptr(U[i]) for i in range(len(KINDS))]
@@ -266,7 +277,6 @@ def run_gvt(args, ws, rank, local):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    gvt.gvt_stats_enable(H.h, True)
     l0 = gvt.gvt_launch_count()
     for k in range(K):
         flush.zero_()
@@ -277,6 +287,13 @@ def run_gvt(args, ws, rank, local):
     launches = gvt.gvt_launch_count() - l0
     barrier()
     clk = clocks.stop()
+    # the same K steps again with the library's per-stage CUDA events on (kept out of the timed
+    # steps above so that `value` carries no instrumentation): the roofline's launch durations
+    gvt.gvt_stats_enable(H.h, True)
+    for k in range(K):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
     stats = gvt.gvt_stats_read(H.h)
     gvt.gvt_stats_enable(H.h, False)
     step_ms = sum(a.elapsed_time(b) for a, b in ev) / K
@@ -287,37 +304,48 @@ def run_gvt(args, ws, rank, local):
     pts = pair_terms_per_step(p.n)
     value = ws * pts / (step_ms_max / 1e3)
 
-    # ---- roofline of the dominant stage
+    # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
     dom = max(("stage1", "stage2", "one_sided"), key=lambda k: stats[k]["ms"])
-    st = stats[dom]
-    per_launch_ms = st["ms"] / max(st["launches"], 1)
-    flops_l = st["flops"] / max(st["launches"], 1)
-    bytes_l = st["bytes"] / max(st["launches"], 1)
-    ai = flops_l / max(bytes_l, 1.0)
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    ridge = FP32_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
-    if args.engine == "tc" and dom == "stage1":
+    tg = stats["tc_gemm"]
+    if tg["launches"] > 0 and tg["ms"] >= max(stats[k]["ms"] for k in ("stage1", "stage2", "one_sided")) / 2:
+        # the dense engines: the split GEMM is the dominant kernel (its launches are a part of both
+        # stages' time); FP16 and BF16 run at the same nominal tensor rate, so the measured BF16 peak
+        # applies to the FP16 splits unchanged
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        achieved = flops_l / (per_launch_ms / 1e3) / 1e12
+        per_launch_ms = tg["ms"] / tg["launches"]
+        achieved = tg["flops"] / tg["ms"] / 1e9
+        useful = (stats["stage1"]["flops"] + stats["stage2"]["flops"]) / max(tg["flops"], 1.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
-                "frac": achieved / bf16, "peak_source": peak_src + " bf16 burst",
-                "note": "dense BF16x3 GEMM flops (3 split products over the densified W), split/densify "
-                        "kernels inside the timed scope"}
-    elif ai > ridge:
-        achieved = flops_l / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:
-        achieved = bytes_l / (per_launch_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": peak_src}
-    kname = {"stage1": "tc_gemm_kernel" if args.engine == "tc" else "stage1_dense_kernel",
-             "stage2": "stage2_dense_kernel", "one_sided": "gemv_rows_kernel"}[dom]
-    roof.update({"kernel": kname, "traffic": traffic_for(kname), "ms_per_launch": per_launch_ms,
-                 "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
-                 "hbm_frac": (bytes_l / (per_launch_ms / 1e3) / 1e9) / hbm})
+                "frac": achieved / bf16, "peak_source": peak_src + " bf16 burst (fp16 nominal ratio 1)",
+                "kernel": "tc_gemm_kernel", "traffic": traffic_for("tc_gemm_kernel"),
+                "ms_per_launch": per_launch_ms, "launches_per_step": tg["launches"] // K,
+                "algorithmic_flops_per_launch": tg["flops"] / tg["launches"],
+                "algorithmic_bytes_per_launch": tg["bytes"] / tg["launches"],
+                "note": "flops of the split GEMM C = A' B'^T (2 M N K, K = 3 x the 64-rounded inner length: "
+                        "hi*hi + hi*lo + lo*hi); the stages' useful GVT flops are %.1f%% of them" % (100 * useful)}
+        dom = None
+    if dom is not None:
+        st = stats[dom]
+        per_launch_ms = st["ms"] / max(st["launches"], 1)
+        flops_l = st["flops"] / max(st["launches"], 1)
+        bytes_l = st["bytes"] / max(st["launches"], 1)
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ridge = FP32_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
+        if flops_l / max(bytes_l, 1.0) > ridge:
+            achieved = flops_l / (per_launch_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        else:
+            achieved = bytes_l / (per_launch_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "peak_source": peak_src}
+        kname = {"stage1": "stage1_dense_kernel", "stage2": "stage2_dense_kernel",
+                 "one_sided": "gemv_rows_kernel"}[dom]
+        roof.update({"kernel": kname, "traffic": traffic_for(kname), "ms_per_launch": per_launch_ms,
+                     "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
+                     "hbm_frac": (bytes_l / (per_launch_ms / 1e3) / 1e9) / hbm})
     stage_summary = {k: {"launches": stats[k]["launches"] // K,
                          "ms_per_step": stats[k]["ms"] / K,
                          "tflops": (stats[k]["flops"] / max(stats[k]["ms"], 1e-9)) / 1e9,
@@ -347,10 +375,30 @@ def run_gvt(args, ws, rank, local):
            "h2d_bytes_per_step": int(vh.numel() * 4), "d2h_bytes_per_step": int(Uh.numel() * 4),
            "ms_per_step": float(t.item())}
 
+    # ---- the same steps on the FP32 SIMT engine, for comparison (device-timed like `value`)
+    engines = None
+    if args.engine != "simt":
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+        for _ in range(3):
+            step()
+        ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            ev3[k][0].record(stream)
+            step()
+            ev3[k][1].record(stream)
+        torch.cuda.synchronize()
+        simt_ms = sum(a.elapsed_time(b) for a, b in ev3) / K
+        engines = {"simt_f32": {"ms_per_step": simt_ms, "value": ws * pts / (simt_ms / 1e3), "unit": UNIT},
+                   args.engine: {"ms_per_step": step_ms_max, "value": value, "unit": UNIT}}
+        gvt.gvt_set_stage1_engine(H.h, engine_code)
+
     # ---- KRR solve: plain FP64 CG vs mixed-precision refinement
     accuracy = None
     if rank == 0:
         accuracy = sampled_error(p, M, plan, gvt, torch, dev)
+        accuracy["fp32_tolerance"] = 1e-5
     gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
     tc_gemm = bench_tc_gemm(H, gvt, torch, dev, peaks) if rank == 0 else None
     solve = None
@@ -370,14 +418,16 @@ def run_gvt(args, ws, rank, local):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
                "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_OF_ENGINE[args.engine], "data": "synthetic",
                "config": {"workload": WORKLOAD, "m": p.m, "q": p.m, "n": p.n, "nhat": p.n,
                           "kernels": KINDS, "kronecker_terms": sum(TERMS.values()),
                           "pair_terms_per_step": pts,
                           "l2": "flushed (512 MB write) before every timed step, outside the events",
+                          "roofline_timing": "per-stage CUDA events of the library, over a second pass of the same "
+                                             "K steps (the timed pass runs without them)",
                           "parallelism": "replicas: independent problems per rank (seed = rank)"},
                "roofline": roof, "stages": stage_summary, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clk, "gpu_launches": launches, "engine": args.engine,
+               "clocks": clk, "gpu_launches": launches, "engine": args.engine, "engines": engines,
                "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve,
                "batched": batched}
         print(json.dumps(out), flush=True)
@@ -442,21 +492,24 @@ def bench_solve(H, gvt, torch, dev, lambdas):
     y = torch.as_tensor(p.y, device=dev)
     res = {"workload": "merget-shaped: m=2000, q=250, 128-d, n=120k (24%), Kronecker of Gaussians, "
                        "target FP64 rel. residual 1e-6", "runs": {}}
-    variants = (("fp64_cg", gvt.GVT_SOLVE_FP64_CG, gvt.GVT_F32),
-                ("mixed_ir_f32", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32),
-                ("mixed_ir_tc_bf16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_BF16))
+    variants = (("fp64_cg", gvt.GVT_SOLVE_FP64_CG, gvt.GVT_F32, gvt.GVT_STAGE1_SIMT),
+                ("mixed_ir_f32", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32, gvt.GVT_STAGE1_SIMT),
+                ("mixed_ir_tc_bf16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_BF16, gvt.GVT_STAGE1_SIMT),
+                ("mixed_ir_tc_f16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32, gvt.GVT_STAGES_TC_F16X3))
     for lam in lambdas:
         r = {}
-        for name, mode, inner in variants:
+        for name, mode, inner, engine in variants:
+            gvt.gvt_set_stage1_engine(H.h, engine)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=10,
                                            max_iter=20000, inner_dtype=inner)
             torch.cuda.synchronize()
             wall = (time.perf_counter() - t0) * 1e3
+            gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
             r[name] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
                        "refinements": int(info.refinements), "rel_residual": info.rel_residual}
-        for name in ("mixed_ir_f32", "mixed_ir_tc_bf16x3"):
+        for name in ("mixed_ir_f32", "mixed_ir_tc_bf16x3", "mixed_ir_tc_f16x3"):
             if r[name]["status"] == "GVT_OK" and r["fp64_cg"]["status"] == "GVT_OK":
                 r[name]["speedup_vs_fp64_cg"] = r["fp64_cg"]["ms"] / r[name]["ms"]
         res["runs"]["lambda=%g" % lam] = r

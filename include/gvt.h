@@ -223,19 +223,29 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x,
                                void* stream);
 
 /*
- * Engine of stage 1 for FP32 products of dense x dense terms.
- *  GVT_STAGE1_SIMT      : sparse scatter-accumulate over the sorted pairs (default).
- *  GVT_STAGE1_TC_BF16X3 : W is densified and S = B W runs as a tcgen05 BF16 GEMM
- *                         on hi/lo splits of both operands (hi*hi + hi*lo + lo*hi,
- *                         each product accurate to ~1e-5 relative, FP32
- *                         accumulation); the stage ordering then minimises the
- *                         stage-2 length.  Worth it when W is dense (n / (q m)
- *                         above a few percent).  Stage 2 stays FP32.
- * Affects later products made with plans of this handle; FP64 products ignore it.
+ * Engine of the GVT stages for FP32 products of dense x dense terms (Theorem 1's
+ * two products with W densified; the engine changes how they are computed, not
+ * what).  FP64 products ignore it and always run the SIMT stages.
+ *  GVT_STAGE1_SIMT      : stage 1 a sparse scatter-accumulate over the sorted pairs,
+ *                         stage 2 a sampled gather-dot; FP32 arithmetic (default).
+ *  GVT_STAGE1_TC_BF16X3 : stage 1 only as a tcgen05 GEMM on BF16 hi/lo splits of both
+ *                         operands (hi*hi + hi*lo + lo*hi, FP32 accumulation; products
+ *                         accurate to ~1e-5 relative); the stage ordering then
+ *                         minimises the stage-2 length.  Stage 2 stays SIMT FP32.
+ *  GVT_STAGES_TC_F16X3  : both stages as tcgen05 GEMMs on FP16 hi/lo splits, every row
+ *                         scaled by a power of two first (products accurate to ~2^-21
+ *                         relative, FP32 class); stage 2 computes A S^T densely and
+ *                         reads out the sampled entries.
+ *  GVT_STAGES_AUTO      : per stage, GVT_STAGES_TC_F16X3 where a cost model (dense
+ *                         GEMM time vs sparse SIMT time at measured GB300 rates)
+ *                         favours it -- W dense enough -- and SIMT elsewhere.
+ * Affects later products made with plans of this handle.
  */
 typedef enum gvt_stage1_engine {
     GVT_STAGE1_SIMT = 0,
-    GVT_STAGE1_TC_BF16X3 = 1
+    GVT_STAGE1_TC_BF16X3 = 1,
+    GVT_STAGES_TC_F16X3 = 2,
+    GVT_STAGES_AUTO = 3
 } gvt_stage1_engine;
 
 gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine);
@@ -427,7 +437,9 @@ typedef enum gvt_stat_kind {
     GVT_STAT_STAGE1 = 0,     /* stage 1: S = B W (sparse scatter-accumulate) */
     GVT_STAT_STAGE2 = 1,     /* stage 2: sampled gather-dot */
     GVT_STAT_ONE_SIDED = 2,  /* one-sided terms: segment sums, GEMV, gather */
-    GVT_STAT_COUNT = 3
+    GVT_STAT_TC_GEMM = 3,    /* the tcgen05 GEMM launches of the dense engines alone (also counted
+                                inside their stage's record); flops = 2 M N K of the split GEMM */
+    GVT_STAT_COUNT = 4
 } gvt_stat_kind;
 
 typedef struct gvt_kernel_stats {

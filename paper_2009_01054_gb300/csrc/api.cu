@@ -484,7 +484,7 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x, c
 
 gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine)
 {
-    if (!h || (engine != GVT_STAGE1_SIMT && engine != GVT_STAGE1_TC_BF16X3)) {
+    if (!h || engine < GVT_STAGE1_SIMT || engine > GVT_STAGES_AUTO) {
         set_error("gvt_set_stage1_engine: bad handle or engine");
         return GVT_ERR_INVALID_ARG;
     }

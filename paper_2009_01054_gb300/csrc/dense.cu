@@ -1,0 +1,324 @@
+// Operands of the dense (tensor-core) stages.
+//
+// A dense x dense Kronecker term can run both GVT stages as GEMMs
+// (Theorem 1's two products with W densified):
+//   stage 1   S[Y x X]  = B[Y x K] W[K x X],        W^T row x holds coef * v_j at column bcol_j
+//   stage 2   C[mb x Y] = A[mb x X] S[Y x X]^T,     u_i += C[arow_i, srow_i]
+// Each FP32 operand is split into a 3K'-wide 16-bit operand (K' = K rounded
+// up to 64) so that one GEMM of the splits gives hi*hi + hi*lo + lo*hi:
+//   left  operand  [hi | hi | lo]      right operand  [hi | lo | hi]
+// Two split formats:
+//   BF16 : hi = bf16(x), lo = bf16(x - hi); no scaling.  Products are
+//          accurate to about 3 * 2^-17 relative.
+//   FP16 : each row is first scaled by a power of two s_r that puts its
+//          largest magnitude in [2^13, 2^14); hi = fp16(s x), lo = fp16(s x - hi).
+//          hi and lo carry 22 significant bits, the dropped lo*lo term is
+//          below 2^-22 relative, so products are accurate to about 2^-21 --
+//          FP32-class.  The GEMM epilogue multiplies by 1/s_row and 1/s_col
+//          (exact powers of two).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gvt_internal.h"
+
+namespace gvt {
+namespace {
+
+constexpr int kSplitThreads = 256;
+constexpr int64_t kRowSmemMax = 160 * 1024;   // widest W^T row (bytes) densified in shared memory
+
+__device__ __forceinline__ void split8_bf16(const float (&x)[8], uint4& hi, uint4& lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * e] - hf.x, x[2 * e + 1] - hf.y);
+        h[e] = *reinterpret_cast<const uint32_t*>(&hb);
+        l[e] = *reinterpret_cast<const uint32_t*>(&lb);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void split8_f16(const float (&x)[8], float s, uint4& hi, uint4& lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float a = x[2 * e] * s, b = x[2 * e + 1] * s;
+        const __half2 hh = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(hh);
+        const __half2 lh = __floats2half2_rn(a - hf.x, b - hf.y);
+        h[e] = *reinterpret_cast<const uint32_t*>(&hh);
+        l[e] = *reinterpret_cast<const uint32_t*>(&lh);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// power-of-two scale putting amax in [2^13, 2^14); 1 for zero or non-finite rows
+__device__ __forceinline__ void row_scale(float amax, float& s, float& inv)
+{
+    if (!(amax > 0.f) || !isfinite(amax)) {
+        s = 1.f;
+        inv = 1.f;
+        return;
+    }
+    int e;
+    frexpf(amax, &e);   // amax = f 2^e, f in [0.5, 1)
+    e = max(e, -100);
+    s = ldexpf(1.f, 14 - e);
+    inv = ldexpf(1.f, e - 14);
+}
+
+__device__ __forceinline__ float block_max(float v, float* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    float m = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+    return m;
+}
+
+__device__ __forceinline__ void load8(const float* sp, int64_t k0, int64_t cols, int square, float (&x)[8])
+{
+    if (k0 + 8 <= cols && (reinterpret_cast<uintptr_t>(sp) & 15) == 0) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(sp));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(sp) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = (k0 + e < cols) ? sp[e] : 0.f;
+    }
+    if (square) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] *= x[e];
+    }
+}
+
+__device__ __forceinline__ void store3(uint4* d, int64_t q, int64_t per_row, int pattern_b, const uint4& hi,
+                                       const uint4& lo)
+{
+    d[q] = hi;
+    d[per_row + q] = pattern_b ? lo : hi;
+    d[2 * per_row + q] = pattern_b ? hi : lo;
+}
+
+// One CTA per row: dst row r = 3-part split of src row r (zero beyond cols).
+template <bool F16>
+__global__ void __launch_bounds__(kSplitThreads)
+split_rows_kernel(const float* __restrict__ src, int64_t ld, int64_t cols, int square, int pattern_b,
+                  uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp)
+{
+    __shared__ float red[kSplitThreads / 32];
+    const int64_t r = blockIdx.x;
+    const float* row = src + r * ld;
+    const int64_t per_row = kp / 8;
+    float s = 1.f;
+    if (F16) {
+        float m = 0.f;
+        for (int64_t q = threadIdx.x; q * 8 < cols; q += blockDim.x) {
+            float x[8];
+            load8(row + q * 8, q * 8, cols, square, x);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(x[e]));
+        }
+        float inv;
+        row_scale(block_max(m, red), s, inv);
+        if (threadIdx.x == 0) inv_scale[r] = inv;
+    }
+    uint4* d = dst + r * 3 * per_row;
+    for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
+        float x[8];
+        load8(row + q * 8, q * 8, cols, square, x);
+        uint4 hi, lo;
+        if (F16) split8_f16(x, s, hi, lo);
+        else split8_bf16(x, hi, lo);
+        store3(d, q, per_row, pattern_b, hi, lo);
+    }
+}
+
+// One CTA per row x of W^T: accumulate the row's entries (its segment of every
+// source) in shared memory, then write the [hi | lo | hi] split of the row.
+template <bool F16>
+__global__ void __launch_bounds__(kSplitThreads)
+densify_split_kernel(S1Sources srcs, const float* __restrict__ v, uint4* __restrict__ dst,
+                     float* __restrict__ inv_scale, int64_t kp)
+{
+    extern __shared__ float wrow[];
+    __shared__ float red[kSplitThreads / 32];
+    const int64_t x = blockIdx.x;
+    for (int64_t k = threadIdx.x; k < kp; k += blockDim.x) wrow[k] = 0.f;
+    __syncthreads();
+    // sources one after another, so that a cell written by several sources sums in a fixed
+    // order (within a source the cells of distinct pairs are distinct)
+#pragma unroll
+    for (int si = 0; si < kMaxSources; ++si) {
+        if (si >= srcs.count) break;
+        const S1Source sr = srcs.src[si];
+        const int32_t j0 = sr.seg[x], j1 = sr.seg[x + 1];
+        const float c = (float)sr.coef;
+        for (int32_t j = j0 + (int32_t)threadIdx.x; j < j1; j += (int32_t)blockDim.x)
+            atomicAdd(&wrow[sr.bcol[j]], c * v[sr.perm[j]]);
+        __syncthreads();
+    }
+    const int64_t per_row = kp / 8;
+    float s = 1.f;
+    if (F16) {
+        float m = 0.f;
+        for (int64_t k = threadIdx.x; k < kp; k += blockDim.x) m = fmaxf(m, fabsf(wrow[k]));
+        float inv;
+        row_scale(block_max(m, red), s, inv);
+        if (threadIdx.x == 0) inv_scale[x] = inv;
+    }
+    uint4* d = dst + x * 3 * per_row;
+    for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
+        float xs[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xs[e] = wrow[q * 8 + e];
+        uint4 hi, lo;
+        if (F16) split8_f16(xs, s, hi, lo);
+        else split8_bf16(xs, hi, lo);
+        store3(d, q, per_row, 1, hi, lo);
+    }
+}
+
+// rows too wide for shared memory: W^T[x, t] += coef * v[perm_j] in global memory
+__global__ void densify_kernel(S1Sources srcs, const int32_t* __restrict__ key0, const int32_t* __restrict__ key1,
+                               const int32_t* __restrict__ key2, const int32_t* __restrict__ key3, int64_t n,
+                               const float* __restrict__ v, float* __restrict__ Wt, int64_t kp)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int si = 0; si < kMaxSources; ++si) {
+            if (si >= srcs.count) break;
+            const int32_t* key = si == 0 ? key0 : si == 1 ? key1 : si == 2 ? key2 : key3;
+            const S1Source& sr = srcs.src[si];
+            atomicAdd(&Wt[(int64_t)key[j] * kp + sr.bcol[j]], (float)sr.coef * v[sr.perm[j]]);
+        }
+    }
+}
+
+__global__ void zero_f32_kernel(float* __restrict__ x, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0.f;
+}
+
+// u[perm_i] += C[arow_i, srow_i]
+__global__ void gather_c_kernel(const float* __restrict__ C, int64_t ldc, const int32_t* __restrict__ arow,
+                                const int32_t* __restrict__ srow, const int32_t* __restrict__ perm, int64_t n,
+                                float* __restrict__ u)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[perm[i]] += C[(int64_t)arow[i] * ldc + srow[i]];
+}
+
+unsigned g1(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+int64_t dense_kp(int64_t K) { return (K + 63) / 64 * 64; }
+
+size_t dense_operand_bytes(int64_t rows, int64_t K)
+{
+    return al256(2 * (size_t)rows * 3 * (size_t)dense_kp(K)) + al256(4 * (size_t)std::max<int64_t>(rows, 1));
+}
+
+DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K)
+{
+    DenseOperand o;
+    o.data = base;
+    o.inv_scale = reinterpret_cast<float*>(static_cast<char*>(base) + al256(2 * (size_t)rows * 3 * (size_t)dense_kp(K)));
+    o.rows = rows;
+    o.kp = dense_kp(K);
+    return o;
+}
+
+size_t dense_w_scratch_bytes(int64_t X, int64_t K)
+{
+    return 4 * (size_t)dense_kp(K) <= (size_t)kRowSmemMax ? 0 : al256(4 * (size_t)X * (size_t)dense_kp(K));
+}
+
+gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t cols, int square, bool f16,
+                            int pattern_b, const DenseOperand& dst, cudaStream_t s)
+{
+    if (rows <= 0) return GVT_OK;
+    if (rows > INT32_MAX) {
+        set_error("dense split: too many rows");
+        return GVT_ERR_UNSUPPORTED;
+    }
+    uint4* d = static_cast<uint4*>(dst.data);
+    if (f16)
+        split_rows_kernel<true><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
+                                                                         dst.inv_scale, dst.kp);
+    else
+        split_rows_kernel<false><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
+                                                                          dst.inv_scale, dst.kp);
+    GVT_LAUNCH_CHECK("dense split rows");
+    return GVT_OK;
+}
+
+gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSources], int64_t n, const float* v,
+                         int64_t X, bool f16, const DenseOperand& dst, float* wide_scratch, cudaStream_t s)
+{
+    if (X <= 0) return GVT_OK;
+    const int64_t kp = dst.kp;
+    uint4* d = static_cast<uint4*>(dst.data);
+    if (4 * kp <= kRowSmemMax) {
+        const size_t smem = 4 * (size_t)kp;
+        static bool attr = false;
+        if (!attr) {
+            GVT_CUDA(cudaFuncSetAttribute(densify_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kRowSmemMax));
+            GVT_CUDA(cudaFuncSetAttribute(densify_split_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kRowSmemMax));
+            attr = true;
+        }
+        if (f16) densify_split_kernel<true><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp);
+        else densify_split_kernel<false><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp);
+        GVT_LAUNCH_CHECK("densify and split W");
+        return GVT_OK;
+    }
+    zero_f32_kernel<<<g1(X * kp), 256, 0, s>>>(wide_scratch, X * kp);
+    GVT_LAUNCH_CHECK("zero W");
+    if (n > 0) {
+        densify_kernel<<<g1(n), 256, 0, s>>>(srcs, keys[0], keys[1], keys[2], keys[3], n, v, wide_scratch, kp);
+        GVT_LAUNCH_CHECK("densify");
+    }
+    return dense_split_rows(wide_scratch, kp, X, kp, 0, f16, 1, dst, s);
+}
+
+gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
+                      cudaStream_t s)
+{
+    if (a.kp != b.kp) {
+        set_error("dense stage: operand widths differ");
+        return GVT_ERR_INVALID_ARG;
+    }
+    return tc_gemm(a.data, 3 * a.kp, b.data, 3 * b.kp, C, ldc, a.rows, b.rows, 3 * a.kp, f16,
+                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s);
+}
+
+gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s)
+{
+    if (outs.n <= 0) return GVT_OK;
+    gather_c_kernel<<<g1(outs.n), 256, 0, s>>>(C, ldc, outs.arow, outs.srow, outs.perm, outs.n, u);
+    GVT_LAUNCH_CHECK("dense stage 2 gather");
+    return GVT_OK;
+}
+
+}  // namespace gvt

@@ -181,6 +181,8 @@ struct S2Outputs {
 template <class T>
 gvt_status stage2_dense(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
                         const S2Outputs& outs, double coef, T* u, cudaStream_t s);
+// u[perm_i] += C[arow_i, srow_i] (the dense stage 2's sampled read-out)
+gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s);
 // A = identity: u[perm_i] += coef * S[srow_i, arow_i] (arow_i < X)
 template <class T>
 gvt_status stage2_identity(const T* S, int64_t lds, int64_t X, const S2Outputs& outs, double coef,
@@ -213,14 +215,36 @@ size_t dtype_size(int dt);
 // ---------------------------------------------------------------- tensor-core stage 1
 // Device error word of a handle (bounded waits in tensor-core kernels report here).
 inline int* handle_err_word(gvt_handle* h) { return static_cast<int*>(h->status.ptr) + 16; }
+// C[M x N] = row_scale[m] col_scale[n] (A B^T)[m, n] on the tensor cores; A, B both FP16 (f16) or
+// both BF16, K-major; the scales may be NULL.
+gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                   int64_t N, int64_t K, bool f16, const float* row_scale, const float* col_scale, int* err,
+                   cudaStream_t s);
 // C[M x N] (FP32, ld ldc) = A[M x K] B[N x K]^T, A and B BF16 K-major (K % 64 == 0).
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                         int64_t N, int64_t K, int* err, cudaStream_t s);
-size_t dense_stage1_workspace(int64_t Y, int64_t K, int64_t X);
-// S[Y x X] = B[Y x K] W with W densified from the sources (keys[si][j] = column x of entry j)
-gvt_status dense_stage1(const float* B, int64_t ldb, int64_t Y, int64_t K, int square, const S1Sources& srcs,
-                        const int32_t* const keys[kMaxSources], int64_t n, const float* v, int64_t X, float* S,
-                        int64_t lds, void* ws, int reuse_a, int* err, cudaStream_t s);
+
+// A split operand of the dense stages: rows x 3kp 16-bit values ([hi|hi|lo] or
+// [hi|lo|hi]), and for FP16 splits the inverse power-of-two scale of every row.
+struct DenseOperand {
+    void* data = nullptr;
+    float* inv_scale = nullptr;
+    int64_t rows = 0;
+    int64_t kp = 0;   // K rounded up to 64
+};
+int64_t dense_kp(int64_t K);
+size_t dense_operand_bytes(int64_t rows, int64_t K);
+DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K);
+size_t dense_w_scratch_bytes(int64_t X, int64_t K);
+// rows of a row-major FP32 matrix (entries squared if `square`), pattern_b: [hi|lo|hi] instead of [hi|hi|lo]
+gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t cols, int square, bool f16,
+                            int pattern_b, const DenseOperand& dst, cudaStream_t s);
+// W^T (X rows, [hi|lo|hi]) from the sources of a stage-1 group (keys[si][j] = column x of entry j)
+gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSources], int64_t n, const float* v,
+                         int64_t X, bool f16, const DenseOperand& dst, float* wide_scratch, cudaStream_t s);
+// C[a.rows x b.rows] = a b^T with the FP16 row scales applied
+gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
+                      cudaStream_t s);
 
 // ---------------------------------------------------------------- pairwise driver
 // u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).

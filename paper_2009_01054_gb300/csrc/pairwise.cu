@@ -43,6 +43,19 @@ struct Compiled {
     std::vector<OneSided> one;
 };
 
+// Engine choice of GVT_STAGES_AUTO for one stage: the dense FP16x3 GEMM (rows x cols
+// outputs, inner length K) against the sparse SIMT stage doing simt_flops useful flops.
+// Rates measured on GB300 at the homogeneous m = q = 2000 workload: SIMT stages about
+// 4.5e12 useful flop/s, the split GEMM about 0.9e15 flop/s, the split and densify passes
+// about 3e12 B/s, and about 15 us of fixed cost per dense stage.
+bool dense_pays(int64_t rows, int64_t cols, int64_t K, double simt_flops)
+{
+    const double kp = (double)dense_kp(K);
+    const double t_dense = 6.0 * rows * cols * kp / 0.9e15 +
+                           (6.0 * (double)(rows + cols) * kp + 4.0 * (double)rows * cols) / 3e12 + 15e-6;
+    return t_dense < simt_flops / 4.5e12;
+}
+
 int64_t out_range(const gvt_plan* p, int c) { return c == GVT_FIRST ? p->m_rows : p->q_rows; }
 int64_t in_range(const gvt_plan* p, int c) { return c == GVT_FIRST ? p->m_cols : p->q_cols; }
 
@@ -175,9 +188,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     const bool homo = desc->homogeneous != 0;
     const gvt_matrix* mats[2] = {M, homo ? M : N};
     gvt_handle* h = plan->h;
-    const bool tc = sizeof(T) == 4 && h->stage1_engine == GVT_STAGE1_TC_BF16X3;
+    // engine of the dense x dense groups of FP32 products (FP64 products always run the SIMT stages)
+    const int engine = sizeof(T) == 4 ? h->stage1_engine : (int)GVT_STAGE1_SIMT;
+    const bool f16 = engine == GVT_STAGES_TC_F16X3 || engine == GVT_STAGES_AUTO;
     Compiled C;
-    GVT_CHECK(compile(plan, desc, mats, tc, C));
+    GVT_CHECK(compile(plan, desc, mats, engine == GVT_STAGE1_TC_BF16X3, C));
 
     const int64_t n_out = plan->n_out;
 
@@ -209,15 +224,49 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         one_elems = std::max(one_elems, F->cols + F->rows);
     }
     const size_t off_one = one_elems > 0 ? ws.take(sizeof(T) * (size_t)one_elems) : 0;
-    size_t tc_bytes = 0;
-    if (tc)
-        for (auto& g : C.two)
-            if (is_dense(g.fa) && is_dense(g.fb)) {
-                const int ib = g.recipe.begin()->first.second;
-                const int64_t X = in_range(plan, g.recipe.begin()->first.first);
-                tc_bytes = std::max(tc_bytes, dense_stage1_workspace(out_range(plan, g.ob), in_range(plan, ib), X));
+    // ---- dense-stage decisions (same grouping as the execution loop below) and their workspace
+    std::vector<char> tc1(C.two.size(), 0), tc2(C.two.size(), 0);
+    size_t slot_bytes = 0, w_bytes = 0, s_bytes = 0, c_bytes = 0, wide_bytes = 0;
+    if (engine != GVT_STAGE1_SIMT) {
+        std::vector<bool> seen(C.two.size(), false);
+        for (size_t gi = 0; gi < C.two.size(); ++gi) {
+            if (seen[gi]) continue;
+            const TwoSided& g = C.two[gi];
+            const int64_t X = in_range(plan, g.recipe.begin()->first.first);
+            const int64_t Y = out_range(plan, g.ob);
+            const int ib = g.recipe.begin()->first.second;
+            bool same_ib = true;
+            for (auto& r : g.recipe) same_ib = same_ib && in_range(plan, r.first.second) == in_range(plan, ib);
+            const int64_t K = in_range(plan, ib);
+            if (is_dense(g.fa) && is_dense(g.fb) && same_ib && Y > 0 && X > 0 && K > 0) {
+                const double entries = (double)g.recipe.size() * plan->n_in;
+                tc1[gi] = engine == GVT_STAGES_AUTO ? dense_pays(Y, X, K, 2.0 * Y * entries) : 1;
             }
-    const size_t off_tc = tc_bytes > 0 ? ws.take(tc_bytes) : 0;
+            if (tc1[gi]) {
+                slot_bytes = std::max(slot_bytes, dense_operand_bytes(Y, K));
+                w_bytes = std::max(w_bytes, dense_operand_bytes(X, K));
+                wide_bytes = std::max(wide_bytes, dense_w_scratch_bytes(X, K));
+            }
+            for (size_t gj = gi; gj < C.two.size(); ++gj) {
+                const TwoSided& g2 = C.two[gj];
+                if (seen[gj] || g2.fb != g.fb || g2.recipe != g.recipe || out_range(plan, g2.ob) != Y) continue;
+                seen[gj] = true;
+                const int64_t mb = out_range(plan, g2.oa);
+                if (!f16 || !is_dense(g2.fa) || mb <= 0) continue;
+                tc2[gj] = engine == GVT_STAGES_AUTO ? dense_pays(mb, Y, X, 2.0 * X * (double)n_out) : 1;
+                if (!tc2[gj]) continue;
+                slot_bytes = std::max(slot_bytes, dense_operand_bytes(mb, X));
+                s_bytes = std::max(s_bytes, dense_operand_bytes(Y, X));
+                c_bytes = std::max(c_bytes, sizeof(float) * (size_t)mb * (size_t)round_up(Y, 4));
+            }
+        }
+    }
+    const size_t off_slot0 = slot_bytes ? ws.take(slot_bytes) : 0;
+    const size_t off_slot1 = slot_bytes ? ws.take(slot_bytes) : 0;
+    const size_t off_w = w_bytes ? ws.take(w_bytes) : 0;
+    const size_t off_s2 = s_bytes ? ws.take(s_bytes) : 0;
+    const size_t off_c2 = c_bytes ? ws.take(c_bytes) : 0;
+    const size_t off_wide = wide_bytes ? ws.take(wide_bytes) : 0;
     GVT_CHECK(ws.commit(s));
     char* base = ws.base();
 
@@ -244,11 +293,36 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
 
     // ---- two-sided groups, grouped by shared stage 1
     std::vector<bool> done(C.two.size(), false);
-    // the dense stage 1's BF16 split of its factor stays valid in the workspace for the
-    // next group with the same factor, square mode and extents
-    const void* split_of = nullptr;
-    int split_sq = -1;
-    int64_t split_Y = -1, split_K = -1;
+    // Split factors live in two slots; a split stays valid for later groups (and for
+    // stage 2) that need the same factor, square mode, extents and format.
+    struct Slot {
+        const void* ptr = nullptr;
+        int sq = -1, pattern = -1;
+        int64_t rows = -1, K = -1;
+        size_t off = 0;
+        int64_t used = -1;
+    } slots[2];
+    slots[0].off = off_slot0;
+    slots[1].off = off_slot1;
+    int64_t tick = 0;
+    auto factor_operand = [&](const gvt_matrix* F, int sq, int64_t rows, int64_t K, DenseOperand& out) -> gvt_status {
+        for (auto& sl : slots)
+            if (sl.ptr == F->data && sl.sq == sq && sl.rows == rows && sl.K == K && sl.pattern == 0) {
+                sl.used = ++tick;
+                out = dense_operand_at(base + sl.off, rows, K);
+                return GVT_OK;
+            }
+        Slot& sl = slots[0].used <= slots[1].used ? slots[0] : slots[1];
+        out = dense_operand_at(base + sl.off, rows, K);
+        GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s));
+        sl.ptr = F->data;
+        sl.sq = sq;
+        sl.rows = rows;
+        sl.K = K;
+        sl.pattern = 0;
+        sl.used = ++tick;
+        return GVT_OK;
+    };
     T* S = reinterpret_cast<T*>(base + off_S);
     for (size_t gi = 0; gi < C.two.size(); ++gi) {
         if (done[gi]) continue;
@@ -268,26 +342,27 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         }
         const double E = (double)srcs.count * (double)plan->n_in;
         const double sz = (double)sizeof(T);
-        bool same_ib = true;   // every source's W row ids share one id range (the K of the GEMM)
-        for (auto& r : g.recipe)
-            same_ib = same_ib && in_range(plan, r.first.second) == in_range(plan, g.recipe.begin()->first.second);
-        if (tc && is_dense(g.fa) && is_dense(g.fb) && same_ib) {
+        if (tc1[gi]) {
             const int ib = g.recipe.begin()->first.second;
             const gvt_matrix* Bm = mats[base_matrix(g.fb, homo)];
             const int32_t* keys[kMaxSources] = {nullptr, nullptr, nullptr, nullptr};
             int k = 0;
             for (auto& r : g.recipe) keys[k++] = plan->in_by[r.first.first].key;
             const int64_t K = in_range(plan, ib);
-            StatScope st(h, s, GVT_STAT_STAGE1, 2.0 * 3.0 * Y * (double)((K + 63) / 64 * 64) * X,
-                         2.0 * (3.0 * (Y + X) * ((K + 63) / 64 * 64)) + sz * Y * X + E * (8 + sz));
-            const int reuse = split_of == Bm->data && split_sq == sq_mode(g.fb) && split_Y == Y && split_K == K;
-            GVT_CHECK(dense_stage1(reinterpret_cast<const float*>(Bm->data), Bm->ld, Y, K, sq_mode(g.fb), srcs, keys,
-                                   plan->n_in, reinterpret_cast<const float*>(v), X, reinterpret_cast<float*>(S), lds,
-                                   base + off_tc, reuse, handle_err_word(h), s));
-            split_of = Bm->data;
-            split_sq = sq_mode(g.fb);
-            split_Y = Y;
-            split_K = K;
+            const double kp = (double)dense_kp(K);
+            // the stage's algorithmic work (the same figures as the SIMT engine); the GEMM's own
+            // executed flops are recorded under GVT_STAT_TC_GEMM
+            StatScope st(h, s, GVT_STAT_STAGE1, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E,
+                         sz * Y * (double)K + sz * Y * X + E * (8 + sz) + srcs.count * 4.0 * (X + 1));
+            DenseOperand a1, b1 = dense_operand_at(base + off_w, X, K);
+            GVT_CHECK(factor_operand(Bm, sq_mode(g.fb), Y, K, a1));
+            GVT_CHECK(dense_split_w(srcs, keys, plan->n_in, reinterpret_cast<const float*>(v), X, f16, b1,
+                                    reinterpret_cast<float*>(base + off_wide), s));
+            {
+                StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * X * 3.0 * kp,
+                             2.0 * 3.0 * kp * (Y + X) + 4.0 * Y * X);
+                GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s));
+            }
         } else if (g.fb == GVT_FACTOR_IDENTITY) {
             GVT_CHECK(vec_zero<T>(S, Y * lds, s));
             StatScope st(h, s, GVT_STAT_STAGE1, E, sz * Y * X + E * (8 + sz));
@@ -311,6 +386,22 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             if (g2.fa == GVT_FACTOR_IDENTITY) {
                 StatScope st(h, s, GVT_STAT_STAGE2, (double)n_out, (double)n_out * (12 + 3 * sz));
                 GVT_CHECK(stage2_identity<T>(S, lds, X, outs, 1.0, u, s));
+            } else if (tc2[gj]) {
+                const int64_t mb = out_range(plan, g2.oa);
+                const int64_t ldc2 = round_up(Y, 4);
+                const double kp = (double)dense_kp(X);
+                StatScope st(h, s, GVT_STAT_STAGE2, (sq_mode(g2.fa) ? 3.0 : 2.0) * X * n_out,
+                             sz * ((double)mb * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
+                DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X);
+                GVT_CHECK(factor_operand(mats[base_matrix(g2.fa, homo)], sq_mode(g2.fa), mb, X, a2));
+                GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s));
+                float* C2 = reinterpret_cast<float*>(base + off_c2);
+                {
+                    StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * 3.0 * kp,
+                                 2.0 * 3.0 * kp * (mb + Y) + 4.0 * mb * Y);
+                    GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s));
+                }
+                GVT_CHECK(dense_gather(C2, ldc2, outs, reinterpret_cast<float*>(u), s));
             } else {
                 const FactorView<T>& A = fv[base_matrix(g2.fa, homo)];
                 const double arows = (double)out_range(plan, g2.oa);

@@ -27,7 +27,7 @@ HOMOGENEOUS = {"symmetric", "antisymmetric", "ranking", "mlpk"}
 GVT_FACTOR_M, GVT_FACTOR_N, GVT_FACTOR_M_SQ, GVT_FACTOR_N_SQ, GVT_FACTOR_ONES, GVT_FACTOR_IDENTITY = range(6)
 GVT_FIRST, GVT_SECOND = 0, 1
 GVT_SOLVE_FP64_CG, GVT_SOLVE_MIXED_IR = 0, 1
-GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3 = 0, 1
+GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3, GVT_STAGES_TC_F16X3, GVT_STAGES_AUTO = 0, 1, 2, 3
 GVT_MAX_TERMS = 16
 
 
@@ -61,8 +61,8 @@ class gvt_kernel_stats(ctypes.Structure):
     _fields_ = [("launches", c_i64), ("ms", c_dbl), ("flops", c_dbl), ("bytes", c_dbl)]
 
 
-GVT_STAT_STAGE1, GVT_STAT_STAGE2, GVT_STAT_ONE_SIDED, GVT_STAT_COUNT = 0, 1, 2, 3
-STAT_NAMES = ["stage1", "stage2", "one_sided"]
+GVT_STAT_STAGE1, GVT_STAT_STAGE2, GVT_STAT_ONE_SIDED, GVT_STAT_TC_GEMM, GVT_STAT_COUNT = 0, 1, 2, 3, 4
+STAT_NAMES = ["stage1", "stage2", "one_sided", "tc_gemm"]
 
 
 class gvt_problem(ctypes.Structure):

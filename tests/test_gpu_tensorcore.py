@@ -6,6 +6,11 @@
   oracle: each product of hi/lo splits is accurate to 3 * 2^-18 relative, so
   the normwise error is bounded by 1.2e-5 * sum|terms| / |u|; the test
   asserts 1e-4 and prints the measured error;
+* both stages on the tensor cores with FP16 hi/lo splits of power-of-two
+  scaled rows (GVT_STAGES_TC_F16X3), and the cost-model engine
+  (GVT_STAGES_AUTO), for all nine kernels on ragged heterogeneous and
+  homogeneous samples, training and cross-kernel prediction plans, against the
+  FP64 oracle within the FP32 tolerance 1e-5;
 * a mixed-precision solve whose inner operator uses the tensor cores reaches
   the FP64 relative residual 1e-6 checked by the oracle.
 """
@@ -101,4 +106,118 @@ def test_mixed_ir_with_tensor_core_inner_operator(H):
     print("bf16x3 inner: %d inner iterations, %d refinements, oracle residual %.2e"
           % (info.iterations, info.refinements, rr))
     assert rr <= 1.05e-6
+    plan.close()
+
+
+ALL_KINDS = ["kronecker", "gaussian", "linear", "poly2d", "cartesian", "symmetric", "antisymmetric", "ranking",
+             "mlpk"]
+
+
+def _engine_product(H, engine, plan, kind, M, N, v, predict=False):
+    gvt.gvt_set_stage1_engine(H.h, engine)
+    try:
+        f = gvt.predict if predict else gvt.pairwise_kernel_matvec
+        u = f(plan, kind, M, N, v).double().cpu().numpy()
+        gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    return u
+
+
+@pytest.mark.parametrize("engine", [gvt.GVT_STAGES_TC_F16X3, gvt.GVT_STAGES_AUTO])
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_f16x3_stages_meet_the_fp32_tolerance(H, engine, kind):
+    """Training product on a ragged sample: 300 x 80 (heterogeneous) or 300 x 300 (homogeneous kernels),
+    none of the extents a multiple of the 64-wide split or the 128-row GEMM tile."""
+    rng = np.random.default_rng(11)
+    m, q, dim = 300, (300 if kind in gvt.HOMOGENEOUS else 80), 12
+    Xd = rng.standard_normal((m, dim))
+    Xt = Xd if kind in gvt.HOMOGENEOUS else rng.standard_normal((q, dim))
+    n = int(0.3 * m * q)
+    d, t = synth.random_pairs(rng, n, m, q)
+    v = rng.standard_normal(n)
+    g = 1.0 / dim
+    M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=g, dtype=torch.float32)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=g, dtype=torch.float32)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t)
+    vv = torch.as_tensor(v, dtype=torch.float32, device=DEV)
+    u = _engine_product(H, engine, plan, kind, M, N, vv)
+    ref = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, vv.double().cpu().numpy())
+    err = normwise(u, ref)
+    print("%s engine %d: error vs FP64 %.2e" % (kind, engine, err))
+    assert err <= 1e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", ["kronecker", "linear", "cartesian", "mlpk"])
+def test_f16x3_cross_kernel_prediction(H, kind):
+    """Prediction for pairs of unseen objects: M_pred (mbar x m) and N_pred (qbar x q) rectangular."""
+    rng = np.random.default_rng(12)
+    homo = kind in gvt.HOMOGENEOUS
+    m, q, mb, qb, dim = 260, (260 if homo else 130), 70, (70 if homo else 90), 10
+    Xd, Xdn = rng.standard_normal((m, dim)), rng.standard_normal((mb, dim))
+    Xt, Xtn = (Xd, Xdn) if homo else (rng.standard_normal((q, dim)), rng.standard_normal((qb, dim)))
+    g = 1.0 / dim
+    n, nh = int(0.35 * m * q), 3000
+    d, t = synth.random_pairs(rng, n, m, q)
+    dh, th = rng.integers(0, mb, nh).astype(np.int32), rng.integers(0, qb, nh).astype(np.int32)
+    if kind == "cartesian":   # identity factors need one id space: predict on training objects
+        mb, qb, Xdn, Xtn = m, q, Xd, Xt
+        dh, th = rng.integers(0, m, nh).astype(np.int32), rng.integers(0, q, nh).astype(np.int32)
+    Mp = gvt.gaussian_kernel(H, torch.as_tensor(Xdn, device=DEV), torch.as_tensor(Xd, device=DEV), gamma=g,
+                             dtype=torch.float32)
+    Np = gvt.gaussian_kernel(H, torch.as_tensor(Xtn, device=DEV), torch.as_tensor(Xt, device=DEV), gamma=g,
+                             dtype=torch.float32)
+    Mo = orc.gaussian_kernel(Xdn, Xd, gamma=g)
+    No = orc.gaussian_kernel(Xtn, Xt, gamma=g)
+    plan = gvt.Plan(H, tuple(Mp.shape), tuple(Np.shape), d, t, dh, th)
+    a = rng.standard_normal(n)
+    aa = torch.as_tensor(a, dtype=torch.float32, device=DEV)
+    u = _engine_product(H, gvt.GVT_STAGES_TC_F16X3, plan, kind, Mp, Np, aa, predict=True)
+    ref = orc.pairwise_matvec(kind, Mo, No, dh, th, d, t, aa.double().cpu().numpy())
+    err = normwise(u, ref)
+    print("%s prediction, FP16x3 stages: error vs FP64 %.2e" % (kind, err))
+    assert err <= 1e-5
+    plan.close()
+
+
+def test_auto_engine_on_a_dense_sample_and_mixed_solve(H):
+    """A dense homogeneous sample (600 objects, 28 % of the pairs), where the cost model picks the
+    tensor-core stages, and a mixed-precision solve whose inner FP32 operator runs under that engine."""
+    rng = np.random.default_rng(13)
+    m, dim = 600, 16
+    X = rng.standard_normal((m, dim))
+    g = 1.0 / dim
+    n = 100000
+    d, t = synth.random_pairs(rng, n, m, m)
+    M32 = gvt.gaussian_kernel(H, torch.as_tensor(X, device=DEV), gamma=g, dtype=torch.float32)
+    M64 = gvt.gaussian_kernel(H, torch.as_tensor(X, device=DEV), gamma=g)
+    Mo = orc.gaussian_kernel(X, gamma=g)
+    plan = gvt.Plan(H, tuple(M32.shape), tuple(M32.shape), d, t)
+    v = rng.standard_normal(n)
+    u = _engine_product(H, gvt.GVT_STAGES_AUTO, plan, "kronecker", M32, M32,
+                        torch.as_tensor(v, dtype=torch.float32, device=DEV))
+    rows = rng.choice(n, 200, replace=False)
+    ref = orc.pairwise_matvec("kronecker", Mo, Mo, d[rows], t[rows], d, t, v.astype(np.float32).astype(np.float64))
+    err = float(np.max(np.abs(u[rows] - ref)) / np.max(np.abs(ref)))
+    print("auto engine, dense sample: error vs FP64 on 200 sampled rows %.2e" % err)
+    assert err <= 1e-5
+    y = rng.standard_normal(n)
+    lam = 1e-1
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
+    try:
+        a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M64, M64, torch.as_tensor(y, device=DEV), lam,
+                                       mode=gvt.GVT_SOLVE_MIXED_IR)
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    assert st == 0
+    # the FP64 residual of the returned solution, recomputed on sampled rows by the oracle
+    Ka = orc.pairwise_matvec("kronecker", Mo, Mo, d[rows], t[rows], d, t, a.cpu().numpy())
+    r = y[rows] - Ka - lam * a.cpu().numpy()[rows]
+    print("auto engine mixed solve: %d inner iterations, %d refinements, reported residual %.2e, "
+          "sampled-row residual max %.2e" % (info.iterations, info.refinements, info.rel_residual,
+                                             np.max(np.abs(r))))
+    assert info.rel_residual <= 1e-6
+    assert np.max(np.abs(r)) <= 1e-5 * np.max(np.abs(y))
     plan.close()
