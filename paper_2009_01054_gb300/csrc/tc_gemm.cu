@@ -6,7 +6,8 @@
 // tile of C (optionally one K slice of it, reduced with atomic adds):
 //   warp 0, one thread : TMA producer -- cp.async.bulk.tensor 2-D loads of
 //                        128 x 64 (A) and BN x 64 (B) tiles, 128-byte swizzle,
-//                        into a TC_STAGES-deep ring, completion on mbarriers;
+//                        into a ring of tc_stages<BN>() slots (as many as fit
+//                        in shared memory), completion on mbarriers;
 //   warp 1, one thread : MMA issuer -- tcgen05.mma kind::f16 (BF16 or FP16 in,
 //                        both operands the same type, FP32 accumulate in TMEM),
 //                        K = 16 per instruction, then tcgen05.commit to free the
@@ -37,15 +38,16 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;            // BF16 elements in one 128-byte swizzle row
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_STAGES = 8;
+constexpr size_t TC_SMEM_LIMIT = 227 * 1024;
 constexpr int TC_THREADS = 320;           // producer warp, MMA warp, 8 folding warps
 constexpr int TC_FOLD_WARPS = 8;
 constexpr int TC_CHUNK = 4;               // k-blocks (4 x 64 = 256 of K) per accumulation chunk
 constexpr long long TC_TIMEOUT_CYCLES = 4000000000ll;   // about 2 s at 2 GHz
 
 struct TcShared {
-    uint64_t full[TC_STAGES];
-    uint64_t empty[TC_STAGES];
+    uint64_t full[TC_MAX_STAGES];
+    uint64_t empty[TC_MAX_STAGES];
     uint64_t acc_full[2];    // chunk accumulated into TMEM buffer b
     uint64_t acc_empty[2];   // folding warps have read buffer b
     uint32_t tmem_base;
@@ -186,10 +188,26 @@ __host__ __device__ constexpr uint32_t idesc_f16kind_f32()
            ((uint32_t)(TC_BM >> 4) << 24);
 }
 
+// ring depth: as many A + B stages as fit in shared memory beside the barriers
 template <int BN>
-constexpr size_t tc_smem_bytes()
+__host__ __device__ constexpr int tc_stages()
 {
-    return (size_t)TC_STAGES * (TC_BM + BN) * TC_BK * 2 + sizeof(TcShared) + 1024;
+    constexpr size_t stage = (size_t)(TC_BM + BN) * TC_BK * 2;
+    constexpr size_t n = (TC_SMEM_LIMIT - sizeof(TcShared) - 1024) / stage;
+    return n > (size_t)TC_MAX_STAGES ? TC_MAX_STAGES : (int)n;
+}
+
+template <int BN>
+__host__ __device__ constexpr size_t tc_smem_bytes()
+{
+    return (size_t)tc_stages<BN>() * (TC_BM + BN) * TC_BK * 2 + sizeof(TcShared) + 1024;
+}
+
+// TMEM columns of the two accumulators, rounded up to a power of two
+template <int BN>
+__host__ __device__ constexpr uint32_t tc_tmem_cols()
+{
+    return 2 * BN <= 128 ? 128u : 2 * BN <= 256 ? 256u : 512u;
 }
 
 template <int BN, bool F16>
@@ -200,11 +218,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                int* __restrict__ err)
 {
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "UMMA N");
+    constexpr int TC_STAGES = tc_stages<BN>();
+    static_assert(TC_STAGES >= 2, "ring depth");
     constexpr int A_BYTES = TC_BM * TC_BK * 2;
     constexpr int B_BYTES = BN * TC_BK * 2;
     constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     constexpr int HALF = BN / 2;            // columns one folding warp owns
-    constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulators
+    constexpr uint32_t TMEM_COLS = tc_tmem_cols<BN>();  // two accumulators
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment of the shared-space offset (swizzle atoms, descriptor base offset 0)
     unsigned char* tiles = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -314,16 +334,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             tc_fence_after();
 #pragma unroll
-            for (int j = 0; j < HALF; j += 32) {
-                uint32_t r0[16], r1[16];
+            for (int j = 0; j < HALF; j += 16) {
+                uint32_t r0[16];
                 tmem_ld16(tl + (uint32_t)(b * BN + j), r0);
-                tmem_ld16(tl + (uint32_t)(b * BN + j + 16), r1);
                 tmem_ld_wait();
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    acc[j + e] += __uint_as_float(r0[e]);
-                    acc[j + 16 + e] += __uint_as_float(r1[e]);
-                }
+                for (int e = 0; e < 16; ++e) acc[j + e] += __uint_as_float(r0[e]);
             }
             tc_fence_before();
             __syncwarp();
@@ -448,12 +464,17 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
         return GVT_ERR_UNSUPPORTED;
     }
     GVT_CHECK(get_encode());
-    // widest N tile that still gives >= 64 output tiles (fewer split-K partial sums to reduce)
+    // widest N tile that still gives >= 64 output tiles (fewer split-K partial sums to reduce);
+    // 224 instead of 256 where it fills more of the 152 SMs in the same single wave
     const int64_t gx = (M + TC_BM - 1) / TC_BM;
     int BN = 256;
     while (BN > 64 && gx * ((N + BN - 1) / BN) < 64) BN /= 2;
     if (N <= 64) BN = 64;
     else if (N <= 128 && BN > 128) BN = 128;
+    if (BN == 256 && N > 256) {
+        const int64_t t256 = gx * ((N + 255) / 256), t224 = gx * ((N + 223) / 224);
+        if (t256 < t224 && t224 <= 152) BN = 224;
+    }
     CUtensorMap ma, mb;
     GVT_CHECK(make_map(&ma, A, M, K, lda, TC_BM, f16));
     GVT_CHECK(make_map(&mb, B, N, K, ldb, BN, f16));
@@ -462,10 +483,12 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
     if (f16) {
         if (BN == 64) return launch_tc<64, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
         if (BN == 128) return launch_tc<128, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+        if (BN == 224) return launch_tc<224, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
         return launch_tc<256, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
     }
     if (BN == 64) return launch_tc<64, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
     if (BN == 128) return launch_tc<128, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    if (BN == 224) return launch_tc<224, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
     return launch_tc<256, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
 }
 

@@ -39,7 +39,8 @@ def normwise(u, ref):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (129, 17, 64), (300, 250, 192), (2000, 250, 6144),
-                                   (1000, 1000, 1024), (37, 300, 128), (4000, 100, 512), (640, 2000, 2048)])
+                                   (1000, 1000, 1024), (37, 300, 128), (4000, 100, 512), (640, 2000, 2048),
+                                   (2000, 1800, 512)])
 def test_tc_gemm_bf16(H, M, N, K):
     g = torch.Generator(device=DEV).manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(M, K, generator=g, device=DEV).to(torch.bfloat16)
