@@ -238,7 +238,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             bool same_ib = true;
             for (auto& r : g.recipe) same_ib = same_ib && in_range(plan, r.first.second) == in_range(plan, ib);
             const int64_t K = in_range(plan, ib);
-            if (is_dense(g.fa) && is_dense(g.fb) && same_ib && Y > 0 && X > 0 && K > 0) {
+            if (is_dense(g.fb) && same_ib && Y > 0 && X > 0 && K > 0) {   // stage 1 needs a dense B only
                 const double entries = (double)g.recipe.size() * plan->n_in;
                 tc1[gi] = engine == GVT_STAGES_AUTO ? dense_pays(Y, X, K, 2.0 * Y * entries) : 1;
             }

@@ -181,15 +181,21 @@ template <class T>
 __global__ void stage1_identity_kernel(S1Sources srcs, const T* __restrict__ v, T* __restrict__ S,
                                        int64_t lds, int64_t Y, int64_t X)
 {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < X;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        for (int si = 0; si < srcs.count; ++si) {
-            const S1Source& sr = srcs.src[si];
+    // one warp per column x: its lanes take the segment's entries, sources one after the
+    // other (a cell hit by several sources, or by a repeated pair, sums through atomics)
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < X; x += nw) {
+#pragma unroll
+        for (int si = 0; si < kMaxSources; ++si) {
+            if (si >= srcs.count) break;
+            const S1Source sr = srcs.src[si];
             const T coef = (T)sr.coef;
-            for (int32_t j = sr.seg[x]; j < sr.seg[x + 1]; ++j) {
+            for (int32_t j = sr.seg[x] + lane; j < sr.seg[x + 1]; j += 32) {
                 const int32_t y = sr.bcol[j];
-                if (y < Y) S[(int64_t)y * lds + x] += coef * v[sr.perm[j]];
+                if (y < Y) atomicAdd(&S[(int64_t)y * lds + x], coef * v[sr.perm[j]]);
             }
+            __syncwarp();
         }
     }
 }
@@ -474,7 +480,7 @@ gvt_status stage1_identity(const S1Sources& srcs, const T* v, T* S, int64_t lds,
                            int64_t X, cudaStream_t s)
 {
     if (Y <= 0 || X <= 0) return GVT_OK;
-    stage1_identity_kernel<T><<<grid1d(X, 128), 128, 0, s>>>(srcs, v, S, lds, Y, X);
+    stage1_identity_kernel<T><<<grid1d(X * 32, 256), 256, 0, s>>>(srcs, v, S, lds, Y, X);
     GVT_LAUNCH_CHECK("stage1_identity");
     return GVT_OK;
 }
