@@ -188,13 +188,15 @@ __host__ __device__ constexpr uint32_t idesc_f16kind_f32()
            ((uint32_t)(TC_BM >> 4) << 24);
 }
 
-// ring depth: as many A + B stages as fit in shared memory beside the barriers
+// ring depth: as many A + B stages as fit in shared memory beside the barriers; narrow tiles
+// keep a 4-deep ring so that two CTAs share an SM (their grids are the split-K ones)
 template <int BN>
 __host__ __device__ constexpr int tc_stages()
 {
     constexpr size_t stage = (size_t)(TC_BM + BN) * TC_BK * 2;
     constexpr size_t n = (TC_SMEM_LIMIT - sizeof(TcShared) - 1024) / stage;
-    return n > (size_t)TC_MAX_STAGES ? TC_MAX_STAGES : (int)n;
+    constexpr int cap = BN <= 64 ? 4 : TC_MAX_STAGES;
+    return n > (size_t)cap ? cap : (int)n;
 }
 
 template <int BN>

@@ -18,9 +18,10 @@ stand in for them:
   batched     256 problems, problem b drawn with seed+b: m, q ~ U{32..512},
               density ~ U[0.05, 0.6], 32-d, gamma=1/32, labels as merget,
               16 lambdas logspace(-4, 0).
-  zipf        m=q=20000, 256-d, gamma=1/256, 10M unique pairs whose drug and
-              target ranks follow a Zipf(1.1) law truncated to the id range,
-              mapped through a random permutation of ids (kernel-filling scale).
+  zipf        m=q=20000, 256-d, gamma=1/256, 10M unique pairs with power-law
+              degrees: Zipf(1.1) weights on drug and target ids (through a random
+              permutation of the ids) and cell (d, t) drawn with probability
+              min(1, c w_d w_t) (kernel-filling scale).
 """
 from dataclasses import dataclass, field
 from typing import List, Optional
@@ -126,37 +127,67 @@ def batched(n_problems=256, seed=0):
     return [batched_problem(b, seed) for b in range(n_problems)]
 
 
-def _zipf_ids(rng, size, n_ids, s, perm):
-    ranks = np.arange(1, n_ids + 1, dtype=np.float64)
-    cdf = np.cumsum(ranks ** (-s))
-    cdf /= cdf[-1]
-    r = np.searchsorted(cdf, rng.random(size), side="right")
-    return perm[np.minimum(r, n_ids - 1)]
+def _zipf_weights(n_ids, s, perm):
+    """Weight rank^-s of every id, ranks assigned through the permutation `perm`."""
+    w = np.empty(n_ids)
+    w[perm] = np.arange(1, n_ids + 1, dtype=np.float64) ** (-s)
+    return w
 
 
-def zipf(seed=0, m=20000, dim=256, n=10_000_000, s=1.1, chunk=4_000_000):
-    """Homogeneous-sized problem with Zipf(s) degrees on drugs and targets.
+def _expected_degree_scale(wd, wt, n):
+    """c such that sum_{d,t} min(1, c wd wt) = n (bisection; per drug the cells with
+    c wd wt >= 1 are counted from the sorted target weights)."""
+    ws = np.sort(wt)[::-1]
+    pref = np.concatenate([[0.0], np.cumsum(ws)])
+    neg = -ws
 
-    Pairs are drawn in chunks and duplicates rejected until n unique remain.
+    def total(c):
+        k = np.searchsorted(neg, -1.0 / (c * wd), side="right")   # targets with c wd wt >= 1
+        return float(np.sum(k + c * wd * (pref[-1] - pref[k])))
+
+    lo, hi = 0.0, 1.0
+    while total(hi) < n:
+        hi *= 2.0
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < n:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def zipf(seed=0, m=20000, dim=256, n=10_000_000, s=1.1, labels=False, rows_per_chunk=500):
+    """Heterogeneous m x m problem (kernel-filling scale) with power-law degrees.
+
+    Drug and target ids get Zipf(s) weights w (rank^-s over a random permutation of
+    the ids).  Cell (d, t) is a pair with probability min(1, c w_d w_t) (an
+    expected-degree model: degrees follow the power law, capped at the id range),
+    c set so that a little more than n pairs are expected; n of the drawn pairs are
+    then kept at random, in drug-major order.  Labels (the bilinear signal) only
+    when `labels`, since they cost a pass over all pairs.
     """
     rng = np.random.default_rng(seed)
     Xd = rng.standard_normal((m, dim))
     Xt = rng.standard_normal((m, dim))
-    perm_d = rng.permutation(m)
-    perm_t = rng.permutation(m)
-    seen = np.zeros(0, dtype=np.int64)
-    while len(seen) < n:
-        dd = _zipf_ids(rng, chunk, m, s, perm_d)
-        tt = _zipf_ids(rng, chunk, m, s, perm_t)
-        key = dd.astype(np.int64) * m + tt
-        _, first = np.unique(key, return_index=True)
-        key = key[np.sort(first)]                       # first occurrence, draw order
-        new = key[~np.isin(key, seen)]
-        seen = np.concatenate([seen, new[: n - len(seen)]])
-    d = (seen // m).astype(np.int32)
-    t = (seen % m).astype(np.int32)
-    y = _bilinear_labels(rng, Xd, Xt, d, t)
-    return PairProblem("zipf", m, m, Xd, Xt, 1.0 / dim, d, t, y=y, lambdas=[1e-2, 1e-4])
+    wd = _zipf_weights(m, s, rng.permutation(m))
+    wt = _zipf_weights(m, s, rng.permutation(m))
+    c = _expected_degree_scale(wd, wt, n + 6.0 * np.sqrt(n))
+    ds, ts = [], []
+    for d0 in range(0, m, rows_per_chunk):
+        P = np.minimum(1.0, c * wd[d0:d0 + rows_per_chunk, None] * wt[None, :])
+        dd, tt = np.nonzero(rng.random(P.shape) < P)
+        ds.append((dd + d0).astype(np.int32))
+        ts.append(tt.astype(np.int32))
+    d = np.concatenate(ds)
+    t = np.concatenate(ts)
+    if len(d) < n:
+        raise RuntimeError("zipf: drew %d pairs, fewer than %d" % (len(d), n))
+    keep = np.sort(rng.choice(len(d), n, replace=False))
+    d, t = d[keep], t[keep]
+    y = _bilinear_labels(rng, Xd, Xt, d, t) if labels else None
+    v = rng.standard_normal(n)
+    return PairProblem("zipf", m, m, Xd, Xt, 1.0 / dim, d, t, v=v, y=y, lambdas=[1e-2, 1e-4])
 
 
 def random_pairs(rng, n, m_ids, q_ids):
