@@ -73,6 +73,17 @@ def dist_setup():
     return ws, rank, local
 
 
+def job_rate(step_ms, units_per_step, ws, dist, device):
+    """Whole-job rate of replicas: every rank processes units_per_step per step; the job's
+    step time is the slowest rank's (max over ranks), so the rate is ws * units / max time."""
+    import torch
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, ws * units_per_step / (ms / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -297,12 +308,8 @@ def run_gvt(args, ws, rank, local):
     stats = gvt.gvt_stats_read(H.h)
     gvt.gvt_stats_enable(H.h, False)
     step_ms = sum(a.elapsed_time(b) for a, b in ev) / K
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t.item())
     pts = pair_terms_per_step(p.n)
-    value = ws * pts / (step_ms_max / 1e3)
+    step_ms_max, value = job_rate(step_ms, pts, ws, dist, dev)
 
     # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
@@ -368,12 +375,10 @@ def run_gvt(args, ws, rank, local):
         ev2[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev2) / Ke
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e = {"value": ws * pts / (float(t.item()) / 1e3), "unit": UNIT,
+    e2e_ms_max, e2e_value = job_rate(e2e_ms, pts, ws, dist, dev)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(vh.numel() * 4), "d2h_bytes_per_step": int(Uh.numel() * 4),
-           "ms_per_step": float(t.item())}
+           "ms_per_step": e2e_ms_max}
 
     # ---- the same steps on the FP32 SIMT engine, for comparison (device-timed like `value`)
     engines = None
