@@ -200,6 +200,15 @@ gvt_status gemv_rows(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, co
 // u[i] += z[idx[i]]  for i < n
 template <class T>
 gvt_status gather_add(const T* z, const int32_t* idx, int64_t n, T* u, cudaStream_t s);
+// One-sided groups on the same factor share one pass over it (up to kMaxOneSidedShare):
+// z[g*ldz + r] = sum_{x < X} F[r, x] * svecs[g*lds + x], and u[i] += sum_g z_g[idx_g[i]].
+constexpr int kMaxOneSidedShare = 4;
+template <class T>
+gvt_status gemv_rows_multi(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svecs, int64_t lds,
+                           int count, T* z, int64_t ldz, cudaStream_t s);
+template <class T>
+gvt_status gather_add_multi(const T* const* z, const int32_t* const* idx, int count, int64_t n, T* u,
+                            cudaStream_t s);
 
 // Bt[c*ldt + r] = B[r*ldb + c]
 template <class T>

@@ -221,7 +221,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     int64_t one_elems = 0;
     for (auto& g : C.one) {
         const gvt_matrix* F = mats[base_matrix(g.f, homo)];
-        one_elems = std::max(one_elems, F->cols + F->rows);
+        one_elems = std::max(one_elems, kMaxOneSidedShare * (F->cols + F->rows));
     }
     const size_t off_one = one_elems > 0 ? ws.take(sizeof(T) * (size_t)one_elems) : 0;
     // ---- dense-stage decisions (same grouping as the execution loop below) and their workspace
@@ -412,27 +412,49 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         }
     }
 
-    // ---- one-sided groups
-    for (auto& g : C.one) {
-        const gvt_matrix* Fm = mats[base_matrix(g.f, homo)];
-        T* sv = reinterpret_cast<T*>(base + off_one);
-        T* z = sv + Fm->cols;
-        const double sz = (double)sizeof(T);
-        const int64_t R = out_range(plan, g.oc);
-        const double Xc = (double)Fm->cols;
-        StatScope st(h, s, GVT_STAT_ONE_SIDED,
-                     (double)g.sources.size() * plan->n_in + (sq_mode(g.f) ? 3.0 : 2.0) * R * Xc + n_out,
-                     (double)g.sources.size() * plan->n_in * (4 + sz) + sz * (R * Xc + Xc + R) +
-                         (double)n_out * (4 + 3 * sz));
-        GVT_CHECK(vec_zero<T>(sv, Fm->cols, s));
-        for (auto& src : g.sources) {
-            const Order& o = plan->in_by[src.first];
-            GVT_CHECK(segment_sums<T>(o.seg, o.perm, in_range(plan, src.first), v, src.second, sv, s));
+    // ---- one-sided groups; those on the same factor (data and square mode) share one pass over it
+    std::vector<bool> od(C.one.size(), false);
+    for (size_t i = 0; i < C.one.size(); ++i) {
+        if (od[i]) continue;
+        const gvt_matrix* Fm = mats[base_matrix(C.one[i].f, homo)];
+        const int sq = sq_mode(C.one[i].f);
+        std::vector<size_t> L{i};
+        od[i] = true;
+        for (size_t j = i + 1; j < C.one.size() && (int)L.size() < kMaxOneSidedShare; ++j)
+            if (!od[j] && mats[base_matrix(C.one[j].f, homo)]->data == Fm->data && sq_mode(C.one[j].f) == sq) {
+                L.push_back(j);
+                od[j] = true;
+            }
+        const int G = (int)L.size();
+        int64_t R = 0;
+        double nsrc = 0.0;
+        for (size_t g : L) {
+            R = std::max(R, out_range(plan, C.one[g].oc));
+            nsrc += (double)C.one[g].sources.size();
         }
-        GVT_CHECK(gemv_rows<T>(static_cast<const T*>(Fm->data), Fm->ld, sq_mode(g.f), R,
-                               Fm->cols, sv, z, s));
-        const int32_t* idx = (g.oc == GVT_FIRST) ? plan->d_out : plan->t_out;
-        GVT_CHECK(gather_add<T>(z, idx, n_out, u, s));
+        const int64_t Xc = Fm->cols;
+        T* sv = reinterpret_cast<T*>(base + off_one);
+        T* z = sv + (size_t)G * Xc;
+        const double sz = (double)sizeof(T);
+        StatScope st(h, s, GVT_STAT_ONE_SIDED,
+                     nsrc * plan->n_in + G * ((sq ? 3.0 : 2.0) * R * (double)Xc) + (double)G * n_out,
+                     nsrc * plan->n_in * (4 + sz) + sz * (R * (double)Xc + G * ((double)Xc + R)) +
+                         (double)n_out * (G * 4 + 2 * sz));
+        GVT_CHECK(vec_zero<T>(sv, (int64_t)G * Xc, s));
+        const T* zs[kMaxOneSidedShare];
+        const int32_t* idxs[kMaxOneSidedShare];
+        for (int k = 0; k < G; ++k) {
+            const OneSided& g = C.one[L[k]];
+            for (auto& src : g.sources) {
+                const Order& o = plan->in_by[src.first];
+                GVT_CHECK(segment_sums<T>(o.seg, o.perm, in_range(plan, src.first), v, src.second,
+                                          sv + (size_t)k * Xc, s));
+            }
+            zs[k] = z + (size_t)k * R;
+            idxs[k] = (g.oc == GVT_FIRST) ? plan->d_out : plan->t_out;
+        }
+        GVT_CHECK(gemv_rows_multi<T>(static_cast<const T*>(Fm->data), Fm->ld, sq, R, Xc, sv, Xc, G, z, R, s));
+        GVT_CHECK(gather_add_multi<T>(zs, idxs, G, n_out, u, s));
     }
     return GVT_OK;
 }

@@ -342,6 +342,53 @@ __global__ void gemv_rows_kernel(const T* __restrict__ F, int64_t ldf, int64_t R
     }
 }
 
+// z_g[r] = sum_x F[r, x] s_g[x] for G vectors s_g = s + g lds in one pass over F
+template <class T, int MODE, int G>
+__global__ void gemv_rows_multi_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
+                                       const T* __restrict__ s, int64_t lds, T* __restrict__ z, int64_t ldz)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += nw) {
+        const T* row = F + r * ldf;
+        T acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = T(0);
+        for (int64_t x = lane; x < X; x += 32) {
+            const T f = MODE == FM_SQUARE ? row[x] * row[x] : row[x];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = fma(f, s[g * lds + x], acc[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
+            if (lane == 0) z[g * ldz + r] = acc[g];
+        }
+    }
+}
+
+template <class T>
+struct GatherSet {
+    const T* z[kMaxOneSidedShare];
+    const int32_t* idx[kMaxOneSidedShare];
+    int count;
+};
+
+// u[i] += sum_g z_g[idx_g[i]]
+template <class T>
+__global__ void gather_add_multi_kernel(GatherSet<T> gs, int64_t n, T* __restrict__ u)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T acc = T(0);
+#pragma unroll
+        for (int g = 0; g < kMaxOneSidedShare; ++g)
+            if (g < gs.count) acc += gs.z[g][gs.idx[g][i]];
+        u[i] += acc;
+    }
+}
+
 template <class T>
 __global__ void gather_add_kernel(const T* __restrict__ z, const int32_t* __restrict__ idx, int64_t n,
                                   T* __restrict__ u)
@@ -535,6 +582,44 @@ gvt_status gemv_rows(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, co
 }
 
 template <class T>
+gvt_status gemv_rows_multi(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svecs, int64_t lds,
+                           int count, T* z, int64_t ldz, cudaStream_t s)
+{
+    if (R <= 0 || count <= 0) return GVT_OK;
+    const unsigned g = grid1d(R * 32, 256, 152 * 16);
+#define GVT_GEMV_MULTI(G)                                                                                    \
+    if (mode == FM_SQUARE)                                                                                   \
+        gemv_rows_multi_kernel<T, FM_SQUARE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);         \
+    else                                                                                                     \
+        gemv_rows_multi_kernel<T, FM_DENSE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);
+    switch (count) {
+    case 1: GVT_GEMV_MULTI(1) break;
+    case 2: GVT_GEMV_MULTI(2) break;
+    case 3: GVT_GEMV_MULTI(3) break;
+    default: GVT_GEMV_MULTI(4) break;
+    }
+#undef GVT_GEMV_MULTI
+    GVT_LAUNCH_CHECK("gemv_rows_multi");
+    return GVT_OK;
+}
+
+template <class T>
+gvt_status gather_add_multi(const T* const* z, const int32_t* const* idx, int count, int64_t n, T* u,
+                            cudaStream_t s)
+{
+    if (n <= 0 || count <= 0) return GVT_OK;
+    GatherSet<T> gs{};
+    gs.count = count < kMaxOneSidedShare ? count : kMaxOneSidedShare;
+    for (int g = 0; g < gs.count; ++g) {
+        gs.z[g] = z[g];
+        gs.idx[g] = idx[g];
+    }
+    gather_add_multi_kernel<T><<<grid1d(n, 256), 256, 0, s>>>(gs, n, u);
+    GVT_LAUNCH_CHECK("gather_add_multi");
+    return GVT_OK;
+}
+
+template <class T>
 gvt_status gather_add(const T* z, const int32_t* idx, int64_t n, T* u, cudaStream_t s)
 {
     if (n <= 0) return GVT_OK;
@@ -626,6 +711,10 @@ gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t
     template gvt_status gemv_rows<T>(const T*, int64_t, int, int64_t, int64_t, const T*, T*,         \
                                      cudaStream_t);                                                 \
     template gvt_status gather_add<T>(const T*, const int32_t*, int64_t, T*, cudaStream_t);         \
+    template gvt_status gemv_rows_multi<T>(const T*, int64_t, int, int64_t, int64_t, const T*, int64_t, int, \
+                                           T*, int64_t, cudaStream_t);                                   \
+    template gvt_status gather_add_multi<T>(const T* const*, const int32_t* const*, int, int64_t, T*,     \
+                                            cudaStream_t);                                               \
     template gvt_status transpose<T>(const T*, int64_t, int64_t, int64_t, T*, int64_t,              \
                                      cudaStream_t);                                                 \
     template gvt_status vec_zero<T>(T*, int64_t, cudaStream_t);

@@ -197,20 +197,58 @@ def test_results_are_bitwise_reproducible(H):
 
 
 @pytest.mark.slow
-def test_full_size_homogeneous_all_kernels_sampled(H):
-    """m = q = 2000, n = 200k (the benchmark workload), FP32 on the GPU, 256 sampled outputs
-    checked against the FP64 oracle (each against all 200k inputs)."""
+@pytest.mark.parametrize("engine", [gvt.GVT_STAGE1_SIMT, gvt.GVT_STAGES_AUTO])
+def test_full_size_homogeneous_all_kernels_sampled(H, engine):
+    """m = q = 2000, n = 200k (the benchmark workload), FP32 on the GPU on the SIMT engine and
+    on the automatic engine the benchmark times (dense tensor-core stages at this density),
+    256 sampled outputs checked against the FP64 oracle (each against all 200k inputs)."""
     p = synth.homogeneous(0)
     M = gpu_gauss(H, p.Xd, p.gamma, torch.float32)
     Mo = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
     plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
     v = to_dev(p.v, torch.float32)
     idx = np.random.default_rng(0).choice(p.n, 256, replace=False)
-    for kind in KINDS:
-        u = gvt.pairwise_kernel_matvec(plan, kind, M, M, v).double().cpu().numpy()
-        ref = orc.pairwise_matvec(kind, Mo, Mo, p.d[idx], p.t[idx], p.d, p.t, p.v.astype(np.float32))
-        assert normwise(u[idx], ref) <= 1e-5, kind
+    gvt.gvt_set_stage1_engine(H.h, engine)
+    try:
+        for kind in KINDS:
+            u = gvt.pairwise_kernel_matvec(plan, kind, M, M, v).double().cpu().numpy()
+            ref = orc.pairwise_matvec(kind, Mo, Mo, p.d[idx], p.t[idx], p.d, p.t, p.v.astype(np.float32))
+            assert normwise(u[idx], ref) <= 1e-5, kind
+        gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
     plan.close()
+
+
+def test_dense_engine_edge_cases(H):
+    """The FP16x3 tensor-core stages on degenerate inputs: no input pairs, one pair, all pairs in
+    one column, repeated pairs, id ranges below one 64-wide split block."""
+    rng = np.random.default_rng(19)
+    m, q = 37, 29
+    Xd, Xt = rng.standard_normal((m, 4)), rng.standard_normal((q, 4))
+    M = gpu_gauss(H, Xd, 0.25, torch.float32)
+    N = gpu_gauss(H, Xt, 0.25, torch.float32)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=0.25), orc.gaussian_kernel(Xt, gamma=0.25)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_TC_F16X3)
+    try:
+        do, to = synth.random_pairs(rng, 10, m, q)
+        u = run(H, "kronecker", M, N, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0), do, to)
+        assert np.all(u == 0) and u.shape == (10,)
+        u = run(H, "mlpk", M, None, np.array([3], np.int32), np.array([5], np.int32), np.array([2.0]),
+                np.array([1, 5], np.int32), np.array([2, 3], np.int32), m_shape=(m, m), q_shape=(m, m))
+        ref = orc.pairwise_matvec("mlpk", Mo, None, [1, 5], [2, 3], [3], [5], np.float32([2.0]))
+        assert normwise(u, ref) <= 1e-5
+        d = np.zeros(5000, np.int32)                       # one drug column
+        t = rng.integers(0, q, 5000).astype(np.int32)      # many repeated pairs
+        v = rng.standard_normal(5000).astype(np.float32)
+        do, to = synth.random_pairs(rng, 33, m, q)
+        for kind in ["kronecker", "cartesian", "linear", "poly2d"]:
+            u = run(H, kind, M, N, d, t, v, do, to)
+            ref = orc.pairwise_matvec(kind, Mo, No, do, to, d, t, v.astype(np.float64))
+            assert normwise(u, ref) <= 1e-5, kind
+        gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
 
 
 @pytest.mark.parametrize("kind", ["kronecker", "symmetric", "poly2d"])
