@@ -364,16 +364,30 @@ def run_gvt(args, ws, rank, local):
     Uh = torch.empty((len(KINDS), p.n), dtype=torch.float32).pin_memory()
     Ke = max(10, K // 5)
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+    copy_stream = torch.cuda.Stream()
+    done = [torch.cuda.Event() for _ in KINDS]
+
+    def step_e2e():
+        # v in from pinned memory; each kernel's result goes back on a copy stream while the
+        # next product runs; the step ends when the last copy has landed
+        v.copy_(vh, non_blocking=True)
+        for i, d in enumerate(descs):
+            gvt.gvt_pairwise_kernel_matvec(plan.p, d, Mm, Mm, vp, up[i], 1, gvt.GVT_F32, sp)
+            done[i].record(stream)
+            copy_stream.wait_event(done[i])
+            with torch.cuda.stream(copy_stream):
+                Uh[i].copy_(U[i], non_blocking=True)
+        stream.wait_stream(copy_stream)
+
     barrier()
     torch.cuda.synchronize()
     for k in range(Ke):
         flush.zero_()
         ev2[k][0].record(stream)
-        v.copy_(vh, non_blocking=True)
-        step()
-        Uh.copy_(U, non_blocking=True)
+        step_e2e()
         ev2[k][1].record(stream)
     torch.cuda.synchronize()
+    assert torch.equal(Uh[-1], U[-1].cpu())
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev2) / Ke
     e2e_ms_max, e2e_value = job_rate(e2e_ms, pts, ws, dist, dev)
     e2e = {"value": e2e_value, "unit": UNIT,
