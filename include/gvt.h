@@ -340,7 +340,7 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
  *     P r = S (I + V V^T)^{-1} S r,   S = diag(sqrt(D)),
  * a diagonal matrix minus a rank-32 term (Woodbury form), SPD for any network
  * output.  The paper solves with an unpreconditioned method (Sec. 6); this is
- * an addition used with flexible CG, whose true residual stays the judge.
+ * an addition used with flexible CG; the true FP64 residual still decides convergence.
  * Parameters: gvt_precond_num_params() floats, layout W1[128x6] b1[128]
  * W2[128x128] b2[128] W3[33x128] b3[33] (row-major).
  */
