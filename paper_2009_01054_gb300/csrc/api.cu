@@ -235,6 +235,7 @@ gvt_status gvt_destroy(gvt_handle* h)
     h->ws.buf.release();
     h->solve_ws.buf.release();
     h->status.release();
+    for (auto& e : h->factor_cache) e.buf.release();
     if (h->host_scalars) cudaFreeHost(h->host_scalars);
     delete h;
     return GVT_OK;

@@ -68,6 +68,18 @@ struct Arena {
     char* base() const { return static_cast<char*>(buf.ptr); }
 };
 
+// A split copy of a kernel matrix kept across products while a solve holds its matrices fixed.
+struct FactorCacheEntry {
+    const void* ptr = nullptr;
+    int64_t ld = 0, rows = 0, K = 0;
+    int sq = -1;
+    bool f16 = false;
+    bool valid = false;
+    uint64_t used = 0;
+    DevBuf buf;
+};
+constexpr int kFactorCacheEntries = 4;
+
 }  // namespace gvt
 
 struct gvt_handle {
@@ -80,7 +92,24 @@ struct gvt_handle {
     std::map<std::tuple<int, int64_t, int>, int> batch_tune;   // batched stage-1 tile choice
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;
+    int factor_cache_depth = 0;     // > 0 while a solve keeps its kernel matrices unchanged
+    uint64_t factor_cache_tick = 0;
+    gvt::FactorCacheEntry factor_cache[gvt::kFactorCacheEntries];
 };
+
+namespace gvt {
+// While alive, the dense engines reuse split copies of kernel matrices across products (the
+// caller guarantees the matrices do not change); the copies are dropped when the last scope ends.
+struct FactorCacheScope {
+    gvt_handle* h;
+    explicit FactorCacheScope(gvt_handle* h_) : h(h_) { ++h->factor_cache_depth; }
+    ~FactorCacheScope()
+    {
+        if (--h->factor_cache_depth == 0)
+            for (auto& e : h->factor_cache) e.valid = false;
+    }
+};
+}  // namespace gvt
 
 namespace gvt {
 // Bracket one stage launch with events when statistics are on.

@@ -306,6 +306,31 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     slots[1].off = off_slot1;
     int64_t tick = 0;
     auto factor_operand = [&](const gvt_matrix* F, int sq, int64_t rows, int64_t K, DenseOperand& out) -> gvt_status {
+        if (h->factor_cache_depth > 0) {   // a solve holds the matrices fixed: keep splits across products
+            for (auto& e : h->factor_cache)
+                if (e.valid && e.ptr == F->data && e.ld == F->ld && e.rows == rows && e.K == K && e.sq == sq &&
+                    e.f16 == f16) {
+                    e.used = ++h->factor_cache_tick;
+                    out = dense_operand_at(e.buf.ptr, rows, K);
+                    return GVT_OK;
+                }
+            FactorCacheEntry* lru = &h->factor_cache[0];   // an empty entry, else the least recently used
+            for (auto& e : h->factor_cache)
+                if (!e.valid ? lru->valid || e.used < lru->used : lru->valid && e.used < lru->used) lru = &e;
+            lru->valid = false;
+            GVT_CHECK(lru->buf.reserve(dense_operand_bytes(rows, K), s));
+            out = dense_operand_at(lru->buf.ptr, rows, K);
+            GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s));
+            lru->ptr = F->data;
+            lru->ld = F->ld;
+            lru->rows = rows;
+            lru->K = K;
+            lru->sq = sq;
+            lru->f16 = f16;
+            lru->valid = true;
+            lru->used = ++h->factor_cache_tick;
+            return GVT_OK;
+        }
         for (auto& sl : slots)
             if (sl.ptr == F->data && sl.sq == sq && sl.rows == rows && sl.K == K && sl.pattern == 0) {
                 sl.used = ++tick;

@@ -360,6 +360,7 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool homo = desc->homogeneous != 0;
     const gvt_matrix* Nn = homo ? M : N;
+    FactorCacheScope keep_splits(h);   // M and N stay fixed for the whole solve
     // flexible-CG iterations before the plain-CG fallback
     const int64_t pbudget = opts.precond_budget > 0 ? std::min<int64_t>(opts.precond_budget, opts.max_iter)
                                                     : std::max<int64_t>(1, opts.max_iter / 2);

@@ -222,3 +222,48 @@ def test_auto_engine_on_a_dense_sample_and_mixed_solve(H):
     assert info.rel_residual <= 1e-6
     assert np.max(np.abs(r)) <= 1e-5 * np.max(np.abs(y))
     plan.close()
+
+
+def test_split_copies_do_not_outlive_a_solve(H):
+    """A solve keeps split copies of its kernel matrices across its products; a later solve on
+    other matrices in the same workspace must not see them (it converges as on a fresh handle)."""
+    rng = np.random.default_rng(21)
+    m, q, dim = 300, 160, 12
+    n = int(0.3 * m * q)
+    d, t = synth.random_pairs(rng, n, m, q)
+    y = rng.standard_normal(n)
+    lam = 1e-1
+    runs = []
+    for scale in (1.0, 0.5):
+        Xd, Xt = scale * rng.standard_normal((m, dim)), rng.standard_normal((q, dim))
+        M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=1.0 / dim)
+        N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=1.0 / dim)
+        runs.append((Xd, Xt, M, N))
+    plan = gvt.Plan(H, (m, m), (q, q), d, t)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_TC_F16X3)
+    try:
+        its = []
+        for Xd, Xt, M, N in runs:
+            a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, torch.as_tensor(y, device=DEV), lam,
+                                           mode=gvt.GVT_SOLVE_MIXED_IR)
+            assert st == 0
+            Mo, No = orc.gaussian_kernel(Xd, gamma=1.0 / dim), orc.gaussian_kernel(Xt, gamma=1.0 / dim)
+            mv = lambda x: orc.pairwise_matvec("kronecker", Mo, No, d, t, d, t, x)
+            assert orc.relative_residual(mv, a.cpu().numpy(), y, lam) <= 1.05e-6
+            its.append((info.iterations, info.refinements))
+        H2 = gvt.Handle()
+        gvt.gvt_set_stage1_engine(H2.h, gvt.GVT_STAGES_TC_F16X3)
+        plan2 = gvt.Plan(H2, (m, m), (q, q), d, t)
+        _, st, info2 = gvt.krr_cg_solve(H2, plan2, "kronecker", runs[1][2], runs[1][3],
+                                        torch.as_tensor(y, device=DEV), lam, mode=gvt.GVT_SOLVE_MIXED_IR)
+        print("second solve: %d inner iterations, %d refinements; on a fresh handle %d, %d"
+              % (its[1][0], its[1][1], info2.iterations, info2.refinements))
+        # a stale split of the first matrices would turn every inner solve into one for the wrong
+        # operator (more refinements or no convergence); split-K rounding order moves counts a little
+        assert st == 0 and info2.refinements == its[1][1]
+        assert abs(info2.iterations - its[1][0]) <= 0.25 * info2.iterations + 3
+        plan2.close()
+        H2.close()
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    plan.close()
