@@ -67,3 +67,78 @@ def test_kernel_filling_scale_sampled_parity(H):
         assert err <= tol
         del M, N, v, u
     plan.close()
+
+
+def test_merget_scale_products_and_mixed_solve(H):
+    """m = 2000 drugs, q = 250 targets, 128-d, 120k pairs (24 %): the products of every engine
+    the solve section of the benchmark uses, on 200 sampled rows against the FP64 oracle, and a
+    mixed-precision solve on the FP16x3 tensor-core engine whose FP64 residual the oracle
+    recomputes over all 120k pairs."""
+    p = synth.merget(0)
+    rng = np.random.default_rng(8)
+    rows = np.sort(rng.choice(p.n, 200, replace=False))
+    Mo = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+    No = orc.gaussian_kernel(p.Xt, gamma=p.gamma)
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=DEV), gamma=p.gamma)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=DEV), gamma=p.gamma)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    v = rng.standard_normal(p.n)
+    v32 = v.astype(np.float32).astype(np.float64)
+    ref32 = orc.pairwise_matvec("kronecker", Mo, No, p.d[rows], p.t[rows], p.d, p.t, v32)
+    for engine, tol in ((gvt.GVT_STAGE1_SIMT, 1e-5), (gvt.GVT_STAGES_TC_F16X3, 1e-5),
+                        (gvt.GVT_STAGES_AUTO, 1e-5), (gvt.GVT_STAGE1_TC_BF16X3, 1e-4)):
+        gvt.gvt_set_stage1_engine(H.h, engine)
+        try:
+            u = gvt.pairwise_kernel_matvec(plan, "kronecker", M.float(), N.float(),
+                                           torch.as_tensor(v32, dtype=torch.float32, device=DEV))
+            gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+        finally:
+            gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+        err = float(np.max(np.abs(u.double().cpu().numpy()[rows] - ref32)) / np.max(np.abs(ref32)))
+        print("engine %d: error vs FP64 on 200 rows %.2e" % (engine, err))
+        assert err <= tol, engine
+    u64 = gvt.pairwise_kernel_matvec(plan, "kronecker", M, N, torch.as_tensor(v, device=DEV))
+    ref = orc.pairwise_matvec("kronecker", Mo, No, p.d[rows], p.t[rows], p.d, p.t, v)
+    assert float(np.max(np.abs(u64.cpu().numpy()[rows] - ref)) / np.max(np.abs(ref))) <= 1e-10
+    lam = 1e-2
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_TC_F16X3)
+    try:
+        a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, torch.as_tensor(p.y, device=DEV), lam,
+                                       mode=gvt.GVT_SOLVE_MIXED_IR, check_every=10, max_iter=20000)
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    assert st == 0
+    mv = lambda x: orc.pairwise_matvec("kronecker", Mo, No, p.d, p.t, p.d, p.t, x)
+    rr = orc.relative_residual(mv, a.cpu().numpy(), p.y, lam)
+    print("mixed solve (FP16x3 inner): %d inner iterations, %d refinements, oracle residual %.2e"
+          % (info.iterations, info.refinements, rr))
+    assert rr <= 1.05e-6
+    plan.close()
+
+
+def test_batched_full_size(H):
+    """The full batched configuration: 256 problems (m, q ~ U{32..512}, density ~ U[5 %, 60 %],
+    32-d) x 16 lambdas = 4096 systems in one batched solve to FP64 relative residual 1e-6; every
+    reported residual is within the target, and the oracle recomputes them for three problems."""
+    ps = synth.batched(256)
+    lambdas = list(ps[0].lambdas)
+    probs = []
+    for p in ps:
+        M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=DEV), gamma=p.gamma)
+        N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=DEV), gamma=p.gamma)
+        probs.append(dict(M=M, N=N, d=torch.as_tensor(p.d, device=DEV), t=torch.as_tensor(p.t, device=DEV),
+                          y=torch.as_tensor(p.y, device=DEV)))
+    A, st, info, rr = gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6)
+    assert st == 0
+    worst = max(max(r) for r in rr)
+    print("4096 systems, %d pairs: worst reported residual %.2e" % (sum(p.n for p in ps), worst))
+    assert worst <= 1e-6
+    for b in np.argsort([p.n for p in ps])[:3]:
+        p = ps[b]
+        Mo, No = orc.gaussian_kernel(p.Xd, gamma=p.gamma), orc.gaussian_kernel(p.Xt, gamma=p.gamma)
+        mv = lambda x: orc.pairwise_matvec("kronecker", Mo, No, p.d, p.t, p.d, p.t, x)
+        a = A[b].cpu().numpy()
+        for c, lam in enumerate(lambdas):
+            res = orc.relative_residual(mv, a[:, c], p.y, lam)
+            assert res <= 1.05e-6, (b, c, res)
+            assert abs(rr[b][c] - res) <= 1e-9 + 0.05 * res
