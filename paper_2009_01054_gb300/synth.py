@@ -190,6 +190,55 @@ def zipf(seed=0, m=20000, dim=256, n=10_000_000, s=1.1, labels=False, rows_per_c
     return PairProblem("zipf", m, m, Xd, Xt, 1.0 / dim, d, t, v=v, y=y, lambdas=[1e-2, 1e-4])
 
 
+@dataclass
+class SettingSplit:
+    """Training and test pairs of one prediction setting (Sec. 2): the test pairs index the
+    rows of the cross kernels K(X_test_objects, X_train_objects)."""
+    setting: int
+    Xd_train: np.ndarray        # drugs the model is trained on
+    Xt_train: np.ndarray
+    Xd_test: np.ndarray         # drugs the test pairs refer to (the training drugs in settings 1, 3)
+    Xt_test: np.ndarray
+    d: np.ndarray               # training pairs, ids into Xd_train / Xt_train
+    t: np.ndarray
+    y: np.ndarray
+    d_test: np.ndarray          # test pairs, ids into Xd_test / Xt_test
+    t_test: np.ndarray
+
+
+def setting_split(p, setting, test_frac=0.25, seed=0):
+    """Split the pairs of problem `p` for prediction setting 1-4 (Sec. 2):
+    1 random pairs held out (both objects seen in training); 2 pairs of held-out drugs (new
+    drugs, known targets); 3 pairs of held-out targets; 4 pairs whose drug and target are both
+    held out (training keeps only pairs with neither).  Held-out objects are a `test_frac`
+    share of the ids, drawn at random; ids are renumbered densely on both sides."""
+    rng = np.random.default_rng(seed)
+    y = p.y if p.y is not None else rng.standard_normal(p.n)
+    if setting == 1:
+        test = rng.random(p.n) < test_frac
+        return SettingSplit(1, p.Xd, p.Xt, p.Xd, p.Xt, p.d[~test], p.t[~test], y[~test],
+                            p.d[test], p.t[test])
+    new_d = rng.random(p.m) < test_frac if setting in (2, 4) else np.zeros(p.m, bool)
+    new_t = rng.random(p.q) < test_frac if setting in (3, 4) else np.zeros(p.q, bool)
+    nd, nt = new_d[p.d], new_t[p.t]
+    train = ~nd & ~nt
+    test = (nd | nt) if setting != 4 else (nd & nt)
+
+    def renumber(mask):
+        ids = np.full(len(mask), -1, np.int64)
+        ids[mask] = np.arange(int(mask.sum()))
+        return ids
+
+    keep_d, keep_t = ~new_d, ~new_t
+    tr_d, tr_t = renumber(keep_d), renumber(keep_t)
+    te_dmask = new_d if setting in (2, 4) else keep_d
+    te_tmask = new_t if setting in (3, 4) else keep_t
+    te_d, te_t = renumber(te_dmask), renumber(te_tmask)
+    return SettingSplit(setting, p.Xd[keep_d], p.Xt[keep_t], p.Xd[te_dmask], p.Xt[te_tmask],
+                        tr_d[p.d[train]].astype(np.int32), tr_t[p.t[train]].astype(np.int32), y[train],
+                        te_d[p.d[test]].astype(np.int32), te_t[p.t[test]].astype(np.int32))
+
+
 def random_pairs(rng, n, m_ids, q_ids):
     """n pairs drawn with replacement (duplicates allowed), for edge-case tests."""
     return (rng.integers(0, m_ids, n).astype(np.int32),
