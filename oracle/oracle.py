@@ -224,6 +224,58 @@ def cg_solve(matvec, y, lam, tol=1e-6, max_iter=10000, x0=None):
     return a, it, float(np.sqrt(rr) / ynorm)
 
 
+def minres_solve(matvec, y, lam, tol=1e-6, max_iter=10000, record_every=0):
+    """MINRES (Paige and Saunders) for (K + lam I) a = y, the solver of Sec. 6.
+
+    Lanczos vectors v_k of A = K + lam I started from y; the tridiagonal T_k is reduced by
+    Givens rotations, so that a_k minimises ||y - A a|| over the Krylov space K_k(A, y).
+    Column k of T_k holds beta_k (row k-1), alpha_k (row k) and beta_{k+1} (row k+1); after
+    the rotations k-2 and k-1 it becomes (eps_k, delta_k, gammabar_k) and rotation k removes
+    beta_{k+1}.  The right-hand side beta_1 e_1 turns into tau_k, and |phibar_k| = ||r_k||.
+    Directions d_k = (v_k - delta_k d_{k-1} - eps_k d_{k-2}) / gamma_k, a_k = a_{k-1} + tau_k d_k.
+    Stops when |phibar_k| / ||y|| <= tol.  Returns (a, iterations, |phibar|/||y||, records)
+    with records[j] = a_k for k = record_every * (j + 1).
+    """
+    y = np.asarray(y, dtype=np.float64)
+    n = len(y)
+    a = np.zeros(n)
+    beta1 = float(np.sqrt(y @ y))
+    if beta1 == 0.0:
+        return a, 0, 0.0, []
+    v_prev, v = np.zeros(n), y / beta1
+    beta = 0.0                      # beta_k (T[k-1, k]); zero for k = 1
+    c2, s2, c1, s1 = 1.0, 0.0, 1.0, 0.0   # rotations k-2 and k-1
+    d2, d1 = np.zeros(n), np.zeros(n)   # d_{k-2}, d_{k-1}
+    phibar = beta1
+    records = []
+    k = 0
+    while k < max_iter and abs(phibar) / beta1 > tol:
+        k += 1
+        w = matvec(v) + lam * v - beta * v_prev
+        alpha = float(v @ w)
+        w -= alpha * v
+        beta_next = float(np.sqrt(w @ w))
+        eps = s2 * beta
+        dprime = c2 * beta
+        delta = c1 * dprime + s1 * alpha
+        gbar = -s1 * dprime + c1 * alpha
+        gamma = float(np.hypot(gbar, beta_next))
+        c, s = gbar / gamma, beta_next / gamma
+        tau = c * phibar
+        phibar = -s * phibar
+        d = (v - delta * d1 - eps * d2) / gamma
+        a = a + tau * d
+        if record_every > 0 and k % record_every == 0:
+            records.append(a.copy())
+        d2, d1 = d1, d
+        c2, s2, c1, s1 = c1, s1, c, s
+        if beta_next == 0.0:
+            break
+        v_prev, v = v, w / beta_next
+        beta = beta_next
+    return a, k, abs(phibar) / beta1, records
+
+
 def relative_residual(matvec, a, y, lam):
     """||y - (K + lam I) a||_2 / ||y||_2 with the oracle's own matvec."""
     r = np.asarray(y, dtype=np.float64) - (matvec(a) + lam * np.asarray(a))
