@@ -326,6 +326,27 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
                             const double* y, double lambda, double* a,
                             const gvt_solve_opts* opts, gvt_solve_info* info, void* stream);
 
+/*
+ * MINRES on the same system (the solver of Sec. 6, which stops it early):
+ * Lanczos on K + lambda I from y with Givens rotations, so that the k-th iterate
+ * minimises ||y - (K + lambda I) a|| over span{y, A y, ..., A^{k-1} y}.  One FP64
+ * product per iteration; M, N FP64; the plan must be a training plan.
+ * a (device, n FP64): out only -- MINRES starts from zero.  Stops when the
+ * recursive residual norm reaches rel_tol * ||y|| or after max_iter steps.
+ * record_every > 0: the iterate after step record_every * (j + 1) is copied to
+ * column j of `records` (device, n x n_records FP64, column-major, caller-owned)
+ * for j < n_records -- the candidates of early stopping on a validation set.
+ * info (may be NULL): iterations, status, and rel_residual recomputed in FP64
+ * from the returned a.  Synchronises `stream` once per iteration.  Returns
+ * GVT_ERR_NOT_CONVERGED when max_iter ends the run (a holds the last iterate),
+ * GVT_ERR_BREAKDOWN on a zero rotation norm.
+ */
+gvt_status gvt_krr_minres_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
+                                const gvt_matrix* M, const gvt_matrix* N,
+                                const double* y, double lambda, double* a, double rel_tol,
+                                int64_t max_iter, int64_t record_every, int64_t n_records,
+                                double* records, gvt_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------ learned preconditioner */
 
 /*

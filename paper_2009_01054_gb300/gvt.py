@@ -17,6 +17,7 @@ c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, cty
 
 # ---------------------------------------------------------------- enums (gvt.h)
 GVT_OK = 0
+GVT_ERR_BREAKDOWN, GVT_ERR_NOT_CONVERGED, GVT_ERR_TIMEOUT = 6, 7, 8
 STATUS_NAMES = {0: "GVT_OK", 1: "GVT_ERR_INVALID_ARG", 2: "GVT_ERR_INDEX_OOB",
                 3: "GVT_ERR_UNSUPPORTED", 4: "GVT_ERR_ALLOC", 5: "GVT_ERR_CUDA",
                 6: "GVT_ERR_BREAKDOWN", 7: "GVT_ERR_NOT_CONVERGED", 8: "GVT_ERR_TIMEOUT"}
@@ -100,6 +101,8 @@ SIGNATURES = [
     ("gvt_stats_enable", c_i32, [c_vp, c_i32]),
     ("gvt_stats_read", c_i32, [c_vp, c_vp]),
     ("gvt_launch_count", c_i64, []),
+    ("gvt_krr_minres_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
+                                     c_vp, c_dbl, c_i64, c_i64, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
                                  c_vp, c_dbl, c_vp, _P(gvt_solve_opts), _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve_batched", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, _P(gvt_solve_opts), c_vp,
@@ -402,6 +405,18 @@ def gvt_krr_cg_solve(h, plan, desc, M, N, y, lam, a, opts, stream):
     return st, info
 
 
+def gvt_krr_minres_solve(h, plan, desc, M, N, y, lam, a, rel_tol, max_iter, record_every, n_records, records,
+                         stream):
+    """Returns (status, gvt_solve_info); NOT_CONVERGED / BREAKDOWN are returned, not raised."""
+    info = gvt_solve_info()
+    st = load().gvt_krr_minres_solve(h, plan, ctypes.byref(desc), ctypes.byref(M),
+                                     ctypes.byref(N) if N is not None else None, y, lam, a, rel_tol, max_iter,
+                                     record_every, n_records, records, ctypes.byref(info), stream)
+    if st not in (GVT_OK, 6, 7):
+        raise GvtError(st, "gvt_krr_minres_solve", last_error())
+    return st, info
+
+
 # ---------------------------------------------------------------- torch marshalling
 def _torch():
     import torch
@@ -520,6 +535,20 @@ def gaussian_kernel(handle, X, Y=None, gamma=1.0, dtype=None, stream=None):
     gvt_gaussian_kernel(handle.h, ptr(X), X.shape[0], ptr(Y), Y.shape[0], X.shape[1], float(gamma),
                         ptr(out), out.stride(0), dtype_code(out), stream_ptr(stream))
     return out
+
+
+def krr_minres_solve(handle, plan, kind, M, N, y, lam, rel_tol=1e-6, max_iter=10000, record_every=0,
+                     n_records=0, symmetric=True, stream=None):
+    """MINRES on (K + lam I) a = y; returns (a, status, info, records (n x n_records) or None)."""
+    torch = _torch()
+    a = torch.zeros_like(y)
+    rec = torch.zeros((n_records, y.numel()), dtype=torch.float64, device=y.device) \
+        if record_every > 0 and n_records > 0 else None
+    st, info = gvt_krr_minres_solve(handle.h, plan.p, _desc(kind), matrix(M, symmetric),
+                                    matrix(N, symmetric) if N is not None else None, ptr(y), float(lam), ptr(a),
+                                    float(rel_tol), int(max_iter), int(record_every), int(n_records),
+                                    ptr(rec) if rec is not None else None, stream_ptr(stream))
+    return a, st, info, (rec.t() if rec is not None else None)
 
 
 def krr_cg_solve(handle, plan, kind, M, N, y, lam, a0=None, mode=GVT_SOLVE_FP64_CG, rel_tol=1e-6,
