@@ -502,7 +502,8 @@ def bench_tc_gemm(H, gvt, torch, dev, peaks, reps=50):
 
 def bench_solve(H, gvt, torch, dev, lambdas):
     """Merget-shaped KRR (m=2000, q=250, n=120k, Kronecker kernel): wall time to FP64 rel.
-    residual 1e-6 for plain FP64 CG, FP32-inner refinement and tensor-core-inner refinement."""
+    residual 1e-6 for plain FP64 CG, FP32-inner refinement, tensor-core-inner refinement, and
+    the paper's FP64 MINRES."""
     from paper_2009_01054_gb300 import synth
     p = synth.merget(0)
     M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma)
@@ -528,6 +529,13 @@ def bench_solve(H, gvt, torch, dev, lambdas):
             gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
             r[name] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
                        "refinements": int(info.refinements), "rel_residual": info.rel_residual}
+        # the paper's own solver (Sec. 6): FP64 MINRES to the same residual
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a, st, info, _ = gvt.krr_minres_solve(H, plan, "kronecker", M, N, y, lam, rel_tol=1e-6, max_iter=20000)
+        torch.cuda.synchronize()
+        r["fp64_minres"] = {"ms": (time.perf_counter() - t0) * 1e3, "status": gvt.STATUS_NAMES[st],
+                            "iterations": int(info.iterations), "rel_residual": info.rel_residual}
         for name in ("mixed_ir_f32", "mixed_ir_tc_bf16x3", "mixed_ir_tc_f16x3"):
             if r[name]["status"] == "GVT_OK" and r["fp64_cg"]["status"] == "GVT_OK":
                 r[name]["speedup_vs_fp64_cg"] = r["fp64_cg"]["ms"] / r[name]["ms"]
