@@ -137,6 +137,20 @@ def gaussian_kernel(X, Y=None, gamma=1.0, nthreads=0):
     return K
 
 
+def tanimoto_kernel(Xb, Yb=None):
+    """Tanimoto (MinMax) kernel of binary vectors, Sec. 5:
+    K[a,b] = sum_i min(x_ai, y_bi) / sum_i max(x_ai, y_bi); 1 when both vectors are zero."""
+    X = np.asarray(Xb, dtype=np.float64)
+    Y = X if Yb is None else np.asarray(Yb, dtype=np.float64)
+    K = np.ones((X.shape[0], Y.shape[0]))
+    for a in range(X.shape[0]):
+        mn = np.minimum(X[a][None, :], Y).sum(axis=1)
+        mx = np.maximum(X[a][None, :], Y).sum(axis=1)
+        nz = mx > 0
+        K[a, nz] = mn[nz] / mx[nz]
+    return K
+
+
 def compensated_sum(x):
     x = _f64(x)
     return float(_load().orc_compensated_sum(_ptr(x), len(x)))

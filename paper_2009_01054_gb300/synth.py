@@ -239,6 +239,18 @@ def setting_split(p, setting, test_frac=0.25, seed=0):
                         te_d[p.d[test]].astype(np.int32), te_t[p.t[test]].astype(np.int32))
 
 
+def fingerprints(rng, rows, length, density):
+    """Random binary fingerprints: (bits as a rows x length 0/1 uint8 array, the same bit-packed
+    into rows x ceil(length / 32) uint32 words, bit j of word w = feature 32 w + j)."""
+    bits = (rng.random((rows, length)) < density).astype(np.uint8)
+    words = (length + 31) // 32
+    padded = np.zeros((rows, words * 32), np.uint8)
+    padded[:, :length] = bits
+    weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
+    packed = (padded.reshape(rows, words, 32).astype(np.uint64) * weights).sum(axis=2).astype(np.uint32)
+    return bits, packed
+
+
 def random_pairs(rng, n, m_ids, q_ids):
     """n pairs drawn with replacement (duplicates allowed), for edge-case tests."""
     return (rng.integers(0, m_ids, n).astype(np.int32),

@@ -340,3 +340,36 @@ def test_synthetic_shapes_keep_table5_densities():
     assert abs(synth.homogeneous(0, m=200, n=2000).n / (200 * 200) - 0.05) < 1e-9
     small = synth.small(0)
     assert len(set(zip(small.d, small.t)) & set(zip(small.d_pred, small.t_pred))) == 0
+
+
+def test_tanimoto_kernel_is_the_jaccard_index_and_psd():
+    """Tanimoto (MinMax) kernel of Sec. 5 on binary vectors: equal to |A & B| / |A | B| of the
+    index sets (brute force with Python sets), 1 on the diagonal and for two empty vectors,
+    0 for disjoint vectors, symmetric and positive semidefinite."""
+    rng = np.random.default_rng(31)
+    bits, _ = synth.fingerprints(rng, 25, 70, 0.2)
+    bits[3] = 0
+    bits[7] = 0                                   # two empty fingerprints
+    K = orc.tanimoto_kernel(bits)
+    sets = [set(np.flatnonzero(b)) for b in bits]
+    for a in range(25):
+        for b in range(25):
+            u = len(sets[a] | sets[b])
+            want = len(sets[a] & sets[b]) / u if u else 1.0
+            assert abs(K[a, b] - want) <= 1e-15
+    assert np.all(np.diag(K) == 1.0) and K[3, 7] == 1.0 and K[3, 0] == 0.0
+    x = np.zeros((2, 8), np.uint8)
+    x[0, :4] = 1
+    x[1, 4:] = 1
+    assert orc.tanimoto_kernel(x)[0, 1] == 0.0
+    np.testing.assert_array_equal(K, K.T)
+    assert np.linalg.eigvalsh(K).min() >= -1e-12 * np.abs(K).max()
+
+
+def test_fingerprint_packing_round_trip():
+    rng = np.random.default_rng(32)
+    bits, packed = synth.fingerprints(rng, 9, 77, 0.4)
+    assert packed.dtype == np.uint32 and packed.shape == (9, 3)
+    unpacked = ((packed[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(9, 96)[:, :77]
+    np.testing.assert_array_equal(unpacked, bits)
+    assert np.all((packed[:, 2] >> np.uint32(13)) == 0)   # bits past the length are zero
