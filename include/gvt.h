@@ -223,6 +223,18 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x,
                                void* stream);
 
 /*
+ * Tanimoto (MinMax) base kernel of binary fingerprints (Sec. 5):
+ *     K[a, b] = sum_i min(x_ai, y_bi) / sum_i max(x_ai, y_bi) = |x_a AND y_b| / |x_a OR y_b|,
+ * with K[a, b] = 1 when both fingerprints are empty.  X: rows_x x words, Y: rows_y x
+ * words, uint32 device arrays, bit-packed (bit j of word w is feature 32 w + j; bits past
+ * the fingerprint length must be zero); Y may equal X.  K: rows_x x rows_y, ld ldk,
+ * stored in out_dtype (GVT_F64, GVT_F32 or GVT_BF16); the ratio is formed in FP64.
+ */
+gvt_status gvt_tanimoto_kernel(gvt_handle* h, const uint32_t* X, int64_t rows_x,
+                               const uint32_t* Y, int64_t rows_y, int64_t words,
+                               void* K, int64_t ldk, int32_t out_dtype, void* stream);
+
+/*
  * Engine of the GVT stages for FP32 products of dense x dense terms (Theorem 1's
  * two products with W densified; the engine changes how they are computed, not
  * what).  FP64 products ignore it and always run the SIMT stages.

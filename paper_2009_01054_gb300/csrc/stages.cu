@@ -476,6 +476,45 @@ __global__ void gaussian_kernel_kernel(const double* __restrict__ X, int64_t rx,
     }
 }
 
+// Tanimoto (MinMax) kernel of binary fingerprints, Sec. 5:
+//   K[a, b] = |x_a AND y_b| / |x_a OR y_b|   (popcounts over `words` 32-bit words)
+// with K = 1 when both fingerprints are empty.  32 x 32 output tile per block.
+template <class D>
+__global__ void tanimoto_kernel_kernel(const uint32_t* __restrict__ X, int64_t rx, const uint32_t* __restrict__ Y,
+                                       int64_t ry, int64_t words, D* __restrict__ K, int64_t ldk)
+{
+    __shared__ uint32_t xs[32][33];
+    __shared__ uint32_t ys[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int64_t a0 = (int64_t)blockIdx.y * 32, b0 = (int64_t)blockIdx.x * 32;
+    uint32_t inter[4] = {0, 0, 0, 0}, uni[4] = {0, 0, 0, 0};
+    for (int64_t k0 = 0; k0 < words; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t a = a0 + r, b = b0 + r, k = k0 + tx;
+            xs[r][tx] = (a < rx && k < words) ? X[a * words + k] : 0u;
+            ys[r][tx] = (b < ry && k < words) ? Y[b * words + k] : 0u;
+        }
+        __syncthreads();
+        const int kmax = (words - k0 < 32) ? (int)(words - k0) : 32;
+        for (int kk = 0; kk < kmax; ++kk) {
+            const uint32_t yv = ys[tx][kk];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t xv = xs[ty + 8 * i][kk];
+                inter[i] += __popc(xv & yv);
+                uni[i] += __popc(xv | yv);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t a = a0 + ty + 8 * i, b = b0 + tx;
+        if (a < rx && b < ry)
+            K[a * ldk + b] = cvt<double, D>(uni[i] ? (double)inter[i] / (double)uni[i] : 1.0);
+    }
+}
+
 }  // namespace
 
 size_t dtype_size(int dt)
@@ -694,6 +733,30 @@ gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t
         return GVT_ERR_INVALID_ARG;
     }
     GVT_LAUNCH_CHECK("gaussian_kernel");
+    return GVT_OK;
+}
+
+gvt_status tanimoto_kernel(const uint32_t* X, int64_t rx, const uint32_t* Y, int64_t ry, int64_t words, void* K,
+                           int64_t ldk, int dtype, cudaStream_t s)
+{
+    if (rx <= 0 || ry <= 0) return GVT_OK;
+    dim3 grid((unsigned)((ry + 31) / 32), (unsigned)((rx + 31) / 32));
+    dim3 block(32, 8);
+    switch (dtype) {
+    case GVT_F64:
+        tanimoto_kernel_kernel<double><<<grid, block, 0, s>>>(X, rx, Y, ry, words, (double*)K, ldk);
+        break;
+    case GVT_F32:
+        tanimoto_kernel_kernel<float><<<grid, block, 0, s>>>(X, rx, Y, ry, words, (float*)K, ldk);
+        break;
+    case GVT_BF16:
+        tanimoto_kernel_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(X, rx, Y, ry, words, (__nv_bfloat16*)K, ldk);
+        break;
+    default:
+        set_error("tanimoto_kernel: bad dtype");
+        return GVT_ERR_INVALID_ARG;
+    }
+    GVT_LAUNCH_CHECK("tanimoto_kernel");
     return GVT_OK;
 }
 

@@ -101,6 +101,7 @@ SIGNATURES = [
     ("gvt_stats_enable", c_i32, [c_vp, c_i32]),
     ("gvt_stats_read", c_i32, [c_vp, c_vp]),
     ("gvt_launch_count", c_i64, []),
+    ("gvt_tanimoto_kernel", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_i64, c_i32, c_vp]),
     ("gvt_krr_minres_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
                                      c_vp, c_dbl, c_i64, c_i64, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
@@ -534,6 +535,17 @@ def gaussian_kernel(handle, X, Y=None, gamma=1.0, dtype=None, stream=None):
     out = torch.empty((X.shape[0], Y.shape[0]), dtype=dtype or torch.float64, device=X.device)
     gvt_gaussian_kernel(handle.h, ptr(X), X.shape[0], ptr(Y), Y.shape[0], X.shape[1], float(gamma),
                         ptr(out), out.stride(0), dtype_code(out), stream_ptr(stream))
+    return out
+
+
+def tanimoto_kernel(handle, Xp, Yp=None, dtype=None, stream=None):
+    """Tanimoto kernel of bit-packed fingerprints (CUDA int32 tensors of packed uint32 words)."""
+    torch = _torch()
+    Xp = Xp.to(torch.int32).contiguous()
+    Yp = Xp if Yp is None else Yp.to(torch.int32).contiguous()
+    out = torch.empty((Xp.shape[0], Yp.shape[0]), dtype=dtype or torch.float64, device=Xp.device)
+    _call("gvt_tanimoto_kernel", handle.h, ptr(Xp), Xp.shape[0], ptr(Yp), Yp.shape[0], Xp.shape[1], ptr(out),
+          out.stride(0), dtype_code(out), stream_ptr(stream))
     return out
 
 
