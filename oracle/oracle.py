@@ -238,6 +238,64 @@ def cg_solve(matvec, y, lam, tol=1e-6, max_iter=10000, x0=None):
     return a, it, float(np.sqrt(rr) / ynorm)
 
 
+def cg_multishift(matvec, y, lams, tol=1e-6, max_iter=10000):
+    """Multi-shift CG: (K + lam_s I) a_s = y for every lam_s from one Krylov space.
+
+    CG runs on the base system A = K + lam_0 I, lam_0 = min(lams); for the shift
+    sigma = lam_s - lam_0 the residual stays collinear, r_s = zeta r, with
+        zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+                     (alpha_k beta_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} alpha_{k-1} (1 + sigma alpha_k)),
+        alpha^s_k = alpha_k zeta_{k+1} / zeta_k,   beta^s_k = (zeta_{k+1} / zeta_k)^2 beta_k,
+        a_s += alpha^s_k p_s,   p_s = zeta_{k+1} r_{k+1} + beta^s_k p_s,
+    starting from alpha_{-1} = 1, beta_{-1} = 0, zeta_{-1} = zeta_0 = 1, p_s = y.
+    A shift stops updating once |zeta| ||r|| <= tol ||y||.  Returns (A: n x S, iterations,
+    relative residual estimates |zeta_s| ||r|| / ||y|| per shift, taken when it stopped).
+    """
+    y = np.asarray(y, dtype=np.float64)
+    lams = np.asarray(lams, dtype=np.float64)
+    S, n = len(lams), len(y)
+    lam0 = float(lams.min())
+    sig = lams - lam0
+    X = np.zeros((n, S))
+    P = np.tile(y[:, None], (1, S))
+    r = y.copy()
+    p = y.copy()
+    rr = float(r @ r)
+    ynorm = np.sqrt(rr)
+    if ynorm == 0.0:
+        return X, 0, np.zeros(S)
+    z_prev, z = np.ones(S), np.ones(S)
+    alpha_prev, beta_prev = 1.0, 0.0
+    done = np.zeros(S, bool)
+    res_final = np.zeros(S)
+    it = 0
+    while True:
+        res = np.abs(z) * np.sqrt(rr) / ynorm
+        newly = ~done & ((res <= tol) | (it >= max_iter))
+        res_final[newly] = res[newly]
+        done |= newly
+        if done.all():
+            break
+        w = matvec(p) + lam0 * p
+        alpha = rr / float(p @ w)
+        r_new = r - alpha * w
+        rr_new = float(r_new @ r_new)
+        beta = rr_new / rr
+        z_next = z * z_prev * alpha_prev / (alpha * beta_prev * (z_prev - z) + z_prev * alpha_prev * (1.0 + sig * alpha))
+        alpha_s = alpha * z_next / z
+        beta_s = (z_next / z) ** 2 * beta
+        for s in range(S):
+            if not done[s]:
+                X[:, s] += alpha_s[s] * P[:, s]
+                P[:, s] = z_next[s] * r_new + beta_s[s] * P[:, s]
+        p = r_new + beta * p
+        r, rr = r_new, rr_new
+        z_prev, z = np.where(done, z_prev, z), np.where(done, z, z_next)
+        alpha_prev, beta_prev = alpha, beta
+        it += 1
+    return X, it, res_final
+
+
 def minres_solve(matvec, y, lam, tol=1e-6, max_iter=10000, record_every=0):
     """MINRES (Paige and Saunders) for (K + lam I) a = y, the solver of Sec. 6.
 
