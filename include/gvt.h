@@ -339,6 +339,25 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
                             const gvt_solve_opts* opts, gvt_solve_info* info, void* stream);
 
 /*
+ * Multi-shift CG: the kernel ridge systems (K + lambda_s I) a_s = y for a whole sweep of
+ * n_lambda <= 32 regularisation values (host array, each > 0) from one Krylov space:
+ * CG on the base system with the smallest lambda, one FP64 product per iteration, and
+ * every other lambda advanced by the collinear-residual recurrences of shifted CG.
+ * A (device, n x n_lambda FP64, column-major, caller-owned) receives the solutions; a
+ * shift stops updating when its recursive residual reaches rel_tol * ||y||.
+ * rel_residuals (host, n_lambda, may be NULL): ||y - (K + lambda_s I) a_s|| / ||y||
+ * recomputed in FP64 (one more product per lambda).  info (may be NULL): iterations of
+ * the base system and the largest recomputed residual.  M, N FP64; a training plan.
+ * Synchronises `stream` once per iteration.  GVT_ERR_NOT_CONVERGED when max_iter ends
+ * the run first (A holds the last iterates).
+ */
+gvt_status gvt_krr_cg_solve_multishift(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
+                                       const gvt_matrix* M, const gvt_matrix* N, const double* y,
+                                       const double* lambdas, int32_t n_lambda, double* A,
+                                       double rel_tol, int64_t max_iter, double* rel_residuals,
+                                       gvt_solve_info* info, void* stream);
+
+/*
  * MINRES on the same system (the solver of Sec. 6, which stops it early):
  * Lanczos on K + lambda I from y with Givens rotations, so that the k-th iterate
  * minimises ||y - (K + lambda I) a|| over span{y, A y, ..., A^{k-1} y}.  One FP64

@@ -102,6 +102,8 @@ SIGNATURES = [
     ("gvt_stats_read", c_i32, [c_vp, c_vp]),
     ("gvt_launch_count", c_i64, []),
     ("gvt_tanimoto_kernel", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_i64, c_i32, c_vp]),
+    ("gvt_krr_cg_solve_multishift", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
+                                            c_i32, c_vp, c_dbl, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_minres_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
                                      c_vp, c_dbl, c_i64, c_i64, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
@@ -547,6 +549,25 @@ def tanimoto_kernel(handle, Xp, Yp=None, dtype=None, stream=None):
     _call("gvt_tanimoto_kernel", handle.h, ptr(Xp), Xp.shape[0], ptr(Yp), Yp.shape[0], Xp.shape[1], ptr(out),
           out.stride(0), dtype_code(out), stream_ptr(stream))
     return out
+
+
+def krr_cg_solve_multishift(handle, plan, kind, M, N, y, lambdas, rel_tol=1e-6, max_iter=10000, symmetric=True,
+                            stream=None):
+    """Multi-shift CG for a lambda sweep; returns (A (n x n_lambda), status, info, rel_residuals)."""
+    torch = _torch()
+    lam = (c_dbl * len(lambdas))(*[float(x) for x in lambdas])
+    rr = (c_dbl * len(lambdas))()
+    A = torch.zeros((len(lambdas), y.numel()), dtype=torch.float64, device=y.device)
+    info = gvt_solve_info()
+    st = load().gvt_krr_cg_solve_multishift(handle.h, plan.p, ctypes.byref(_desc(kind)),
+                                            ctypes.byref(matrix(M, symmetric)),
+                                            ctypes.byref(matrix(N, symmetric)) if N is not None else None,
+                                            ptr(y), ctypes.cast(lam, c_vp), len(lambdas), ptr(A), float(rel_tol),
+                                            int(max_iter), ctypes.cast(rr, c_vp), ctypes.byref(info),
+                                            stream_ptr(stream))
+    if st not in (GVT_OK, 6, 7):
+        raise GvtError(st, "gvt_krr_cg_solve_multishift", last_error())
+    return A.t(), st, info, [rr[k] for k in range(len(lambdas))]
 
 
 def krr_minres_solve(handle, plan, kind, M, N, y, lam, rel_tol=1e-6, max_iter=10000, record_every=0,
