@@ -646,13 +646,11 @@ gvt_status palloc(gvt_precond* p, P_** out, size_t count)
     return GVT_OK;
 }
 
+// set on every forward pass: the attribute belongs to the current device's context (cheap)
 gvt_status mlp_smem_attr()
 {
-    static bool done = false;
-    if (done) return GVT_OK;
     GVT_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
     GVT_CUDA(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
-    done = true;
     return GVT_OK;
 }
 
