@@ -244,12 +244,18 @@ def run_gvt(args, ws, rank, local):
     from paper_2009_01054_gb300 import build as gbuild
     from paper_2009_01054_gb300 import gvt
 
-    gbuild.build()
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # one builder per node; the other ranks load what it built
+    if local == 0:
+        gbuild.build()
+    if dist is not None:
+        dist.barrier()
+    if local != 0:
+        gbuild.build()
     dev = torch.device("cuda", local)
     p = workload(rank)
     H = gvt.Handle()

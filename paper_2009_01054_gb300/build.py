@@ -49,7 +49,8 @@ def build(force=False, verbose=False, extra_flags=()):
         if (not force and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t)):
             return obj, False
-        cmd = [nvcc] + _flags(extra_flags) + ["-c", src, "-o", obj + ".tmp"]
+        tmp = obj + ".tmp.%d" % os.getpid()   # concurrent builders never share a temporary
+        cmd = [nvcc] + _flags(extra_flags) + ["-c", src, "-o", tmp]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,7 +58,7 @@ def build(force=False, verbose=False, extra_flags=()):
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
         if verbose and r.stderr.strip():
             print(r.stderr, flush=True)
-        os.replace(obj + ".tmp", obj)
+        os.replace(tmp, obj)
         return obj, True
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
