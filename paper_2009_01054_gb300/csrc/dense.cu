@@ -158,15 +158,31 @@ densify_split_kernel(S1Sources srcs, const float* __restrict__ v, uint4* __restr
     for (int64_t k = threadIdx.x; k < kp; k += blockDim.x) wrow[k] = 0.f;
     __syncthreads();
     // sources one after another, so that a cell written by several sources sums in a fixed
-    // order (within a source the cells of distinct pairs are distinct)
+    // order; within a source the cells of distinct pairs are distinct, except for a source whose
+    // column is the key itself, whose whole segment sums into cell (x, x) by a fixed-order
+    // block reduction (results are reproducible bit for bit unless pairs repeat)
 #pragma unroll
     for (int si = 0; si < kMaxSources; ++si) {
         if (si >= srcs.count) break;
         const S1Source sr = srcs.src[si];
         const int32_t j0 = sr.seg[x], j1 = sr.seg[x + 1];
         const float c = (float)sr.coef;
-        for (int32_t j = j0 + (int32_t)threadIdx.x; j < j1; j += (int32_t)blockDim.x)
-            atomicAdd(&wrow[sr.bcol[j]], c * v[sr.perm[j]]);
+        if (sr.same) {
+            float acc = 0.f;
+            for (int32_t j = j0 + (int32_t)threadIdx.x; j < j1; j += (int32_t)blockDim.x) acc += c * v[sr.perm[j]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float t = 0.f;
+                for (int w = 0; w < kSplitThreads / 32; ++w) t += red[w];
+                wrow[x] += t;
+            }
+        } else {
+            for (int32_t j = j0 + (int32_t)threadIdx.x; j < j1; j += (int32_t)blockDim.x)
+                atomicAdd(&wrow[sr.bcol[j]], c * v[sr.perm[j]]);
+        }
         __syncthreads();
     }
     const int64_t per_row = kp / 8;

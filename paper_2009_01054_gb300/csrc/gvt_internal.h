@@ -180,6 +180,7 @@ struct S1Source {
     const int32_t* bcol;
     const int32_t* perm;
     double coef;
+    int same;   // bcol is the segment key itself: every entry of segment x lands in cell (x, x)
 };
 constexpr int kMaxSources = 4;
 struct S1Sources {

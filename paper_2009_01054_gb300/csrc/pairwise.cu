@@ -364,6 +364,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             sr.bcol = (r.first.first == r.first.second) ? o.key : o.other;
             sr.perm = o.perm;
             sr.coef = r.second;
+            sr.same = r.first.first == r.first.second ? 1 : 0;
         }
         const double E = (double)srcs.count * (double)plan->n_in;
         const double sz = (double)sizeof(T);

@@ -267,3 +267,20 @@ def test_split_copies_do_not_outlive_a_solve(H):
     finally:
         gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
     plan.close()
+
+
+def test_dense_engine_is_reproducible_without_split_k(H):
+    """The FP16x3 stages at the benchmark shape (2000 x 2000 GEMMs, no K split): MLPK -- whose
+    same-component terms sum whole segments into one W cell -- gives bit-identical results on
+    repeated runs."""
+    p = synth.homogeneous(0)
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=DEV), gamma=p.gamma, dtype=torch.float32)
+    plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=DEV)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_TC_F16X3)
+    try:
+        outs = [gvt.pairwise_kernel_matvec(plan, "mlpk", M, M, v).clone() for _ in range(3)]
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    plan.close()
