@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["simt", "tc", "tc16", "auto"],
                     help="engine of the FP32 products: sparse SIMT stages; tc = stage 1 as a tcgen05 BF16x3 "
                          "GEMM; tc16 = both stages as tcgen05 FP16x3 GEMMs; auto = per-stage cost model")
+    ap.add_argument("--streams", type=int, default=3,
+                    help="streams (each with its own handle and plan) over which the nine independent "
+                         "products of a step are spread")
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=256)
@@ -269,14 +272,39 @@ def run_gvt(args, ws, rank, local):
     sp = gvt.stream_ptr()
     engine_code = {"simt": gvt.GVT_STAGE1_SIMT, "tc": gvt.GVT_STAGE1_TC_BF16X3, "tc16": gvt.GVT_STAGES_TC_F16X3,
                    "auto": gvt.GVT_STAGES_AUTO}[args.engine]
-    gvt.gvt_set_stage1_engine(H.h, engine_code)
     stream = torch.cuda.current_stream()
     vp = gvt.ptr(v)
     up = [gvt.ptr(U[i]) for i in range(len(KINDS))]
+    # the nine products are independent: with S streams, product i runs on stream i % S with a
+    # handle and plan of its own, forked from and joined back into the main stream
+    S = max(1, args.streams)
+    extra_h = [gvt.Handle() for _ in range(S - 1)]
+    handles = [H] + extra_h
+    plans = [plan] + [gvt.Plan(h, (p.m, p.m), (p.m, p.m), p.d, p.t) for h in extra_h]
+    streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
+    sps = [sp] + [gvt.stream_ptr(st) for st in streams[1:]]
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in range(S)]
 
-    def step():
+    def set_engine(code):
+        for h in handles:
+            gvt.gvt_set_stage1_engine(h.h, code)
+
+    set_engine(engine_code)
+
+    def step(nstreams=S, after=None):
+        if nstreams > 1:
+            fork.record(stream)
+            for st in streams[1:nstreams]:
+                st.wait_event(fork)
         for i, d in enumerate(descs):
-            gvt.gvt_pairwise_kernel_matvec(plan.p, d, Mm, Mm, vp, up[i], 1, gvt.GVT_F32, sp)
+            j = i % nstreams
+            gvt.gvt_pairwise_kernel_matvec(plans[j].p, d, Mm, Mm, vp, up[i], 1, gvt.GVT_F32, sps[j])
+            if after is not None:
+                after(i, streams[j])
+        for j in range(1, nstreams):
+            joins[j].record(streams[j])
+            stream.wait_event(joins[j])
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for _ in range(max(args.warmup, 3)):
@@ -306,10 +334,11 @@ def run_gvt(args, ws, rank, local):
     clk = clocks.stop()
     # the same K steps again with the library's per-stage CUDA events on (kept out of the timed
     # steps above so that `value` carries no instrumentation): the roofline's launch durations
+    # (one stream: each launch's event-bracketed duration is its own, not shared with another stream's)
     gvt.gvt_stats_enable(H.h, True)
     for k in range(K):
         flush.zero_()
-        step()
+        step(nstreams=1)
     torch.cuda.synchronize()
     stats = gvt.gvt_stats_read(H.h)
     gvt.gvt_stats_enable(H.h, False)
@@ -373,16 +402,17 @@ def run_gvt(args, ws, rank, local):
     copy_stream = torch.cuda.Stream()
     done = [torch.cuda.Event() for _ in KINDS]
 
+    def copy_back(i, st):
+        done[i].record(st)
+        copy_stream.wait_event(done[i])
+        with torch.cuda.stream(copy_stream):
+            Uh[i].copy_(U[i], non_blocking=True)
+
     def step_e2e():
         # v in from pinned memory; each kernel's result goes back on a copy stream while the
-        # next product runs; the step ends when the last copy has landed
+        # next products run; the step ends when the last copy has landed
         v.copy_(vh, non_blocking=True)
-        for i, d in enumerate(descs):
-            gvt.gvt_pairwise_kernel_matvec(plan.p, d, Mm, Mm, vp, up[i], 1, gvt.GVT_F32, sp)
-            done[i].record(stream)
-            copy_stream.wait_event(done[i])
-            with torch.cuda.stream(copy_stream):
-                Uh[i].copy_(U[i], non_blocking=True)
+        step(after=copy_back)
         stream.wait_stream(copy_stream)
 
     barrier()
@@ -403,7 +433,7 @@ def run_gvt(args, ws, rank, local):
     # ---- the same steps on the FP32 SIMT engine, for comparison (device-timed like `value`)
     engines = None
     if args.engine != "simt":
-        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+        set_engine(gvt.GVT_STAGE1_SIMT)
         for _ in range(3):
             step()
         ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -417,7 +447,7 @@ def run_gvt(args, ws, rank, local):
         simt_ms = sum(a.elapsed_time(b) for a, b in ev3) / K
         engines = {"simt_f32": {"ms_per_step": simt_ms, "value": ws * pts / (simt_ms / 1e3), "unit": UNIT},
                    args.engine: {"ms_per_step": step_ms_max, "value": value, "unit": UNIT}}
-        gvt.gvt_set_stage1_engine(H.h, engine_code)
+        set_engine(engine_code)
 
     # ---- KRR solve: plain FP64 CG vs mixed-precision refinement
     accuracy = None
@@ -448,6 +478,7 @@ def run_gvt(args, ws, rank, local):
                           "kernels": KINDS, "kronecker_terms": sum(TERMS.values()),
                           "pair_terms_per_step": pts,
                           "l2": "flushed (512 MB write) before every timed step, outside the events",
+                          "streams": S,
                           "roofline_timing": "per-stage CUDA events of the library, over a second pass of the same "
                                              "K steps (the timed pass runs without them)",
                           "parallelism": "replicas: independent problems per rank (seed = rank)"},
@@ -456,8 +487,10 @@ def run_gvt(args, ws, rank, local):
                "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve,
                "batched": batched}
         print(json.dumps(out), flush=True)
-    plan.close()
-    H.close()
+    for pl in plans:
+        pl.close()
+    for h in handles:
+        h.close()
     if dist is not None:
         dist.destroy_process_group()
 
