@@ -296,6 +296,49 @@ def cg_multishift(matvec, y, lams, tol=1e-6, max_iter=10000):
     return X, it, res_final
 
 
+def klr_objective(f, a, y, lam):
+    """J = sum_i log(1 + exp(-y_i f_i)) + (lam / 2) a^T f  with f = K a (kernel logistic regression)."""
+    return float(np.sum(np.logaddexp(0.0, -y * f)) + 0.5 * lam * float(a @ f))
+
+
+def klr_newton(matvec, y, lam, newton_iters=30, cg_tol=1e-10, grad_tol=1e-10):
+    """Kernel logistic regression by Newton's method on the dual coefficients a (f = K a).
+
+    Gradient K (g + lam a) with g_i = -y_i sigmoid(-y_i f_i); Hessian K (W K + lam I), W_ii =
+    s_i (1 - s_i).  The Newton step solves (W K + lam I) d = b, b = -(g + lam a), through the SPD
+    system (W^1/2 K W^1/2 + lam I) c = W^1/2 K b and d = (b - W^1/2 c) / lam; a backtracking
+    line search halves the step until J decreases.  Stops when ||g + lam a|| <= grad_tol ||y||.
+    Returns (a, newton iterations, ||g + lam a|| / ||y||)."""
+    y = np.asarray(y, dtype=np.float64)
+    a = np.zeros_like(y)
+    f = np.zeros_like(y)
+    it = 0
+    rel = np.inf
+    while it < newton_iters:
+        s = 0.5 * (1.0 + np.tanh(0.5 * y * f))       # sigmoid(y f)
+        g = -y * (1.0 - s)                            # d/df log(1 + exp(-y f))
+        b = -(g + lam * a)
+        rel = float(np.linalg.norm(b) / np.linalg.norm(y))
+        if rel <= grad_tol:
+            break
+        w = s * (1.0 - s)
+        sw = np.sqrt(w)
+        Kb = matvec(b)
+        c, _, _ = cg_solve(lambda x: sw * matvec(sw * x), sw * Kb, lam, tol=cg_tol, max_iter=100000)
+        d = (b - sw * c) / lam
+        Kd = matvec(d)
+        J0 = klr_objective(f, a, y, lam)
+        step = 1.0
+        while step > 1e-12:
+            if klr_objective(f + step * Kd, a + step * d, y, lam) <= J0:
+                break
+            step *= 0.5
+        a = a + step * d
+        f = f + step * Kd
+        it += 1
+    return a, it, rel
+
+
 def minres_solve(matvec, y, lam, tol=1e-6, max_iter=10000, record_every=0):
     """MINRES (Paige and Saunders) for (K + lam I) a = y, the solver of Sec. 6.
 
