@@ -358,6 +358,26 @@ gvt_status gvt_krr_cg_solve_multishift(gvt_handle* h, gvt_plan* plan, const gvt_
                                        gvt_solve_info* info, void* stream);
 
 /*
+ * Kernel logistic regression with a pairwise kernel, by Newton's method on the dual
+ * coefficients (another loss through the same product; Sec. 7 names such extensions):
+ *     J(a) = sum_i log(1 + exp(-y_i f_i)) + (lambda / 2) a^T K a,   f = K a,  y_i = +-1.
+ * Each Newton step solves (W K + lambda I) d = -(g + lambda a) (g: loss gradient in f,
+ * W = diag(s (1 - s)), s = sigmoid(y f)) through the SPD system
+ * (W^1/2 K W^1/2 + lambda I) c = W^1/2 K b by CG to relative residual cg_tol (at most
+ * max_cg_iter iterations), d = (b - W^1/2 c) / lambda, then a backtracking line search
+ * halves the step until J decreases.  FP64 products; M, N FP64 and symmetric; a training
+ * plan.  y, a: device FP64 (a out; starts from zero).  Stops when ||g + lambda a|| <=
+ * grad_tol ||y|| or after newton_iters steps.  info (may be NULL): refinements = Newton
+ * steps, iterations = CG iterations in total, rel_residual = ||g + lambda a|| / ||y||.
+ * Returns GVT_ERR_NOT_CONVERGED when newton_iters (or an inner max_cg_iter) ends the run.
+ */
+gvt_status gvt_klr_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
+                                const gvt_matrix* M, const gvt_matrix* N, const double* y,
+                                double lambda, double* a, int32_t newton_iters, double cg_tol,
+                                double grad_tol, int64_t max_cg_iter, gvt_solve_info* info,
+                                void* stream);
+
+/*
  * MINRES on the same system (the solver of Sec. 6, which stops it early):
  * Lanczos on K + lambda I from y with Givens rotations, so that the k-th iterate
  * minimises ||y - (K + lambda I) a|| over span{y, A y, ..., A^{k-1} y}.  One FP64

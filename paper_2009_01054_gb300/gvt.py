@@ -104,6 +104,8 @@ SIGNATURES = [
     ("gvt_tanimoto_kernel", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_i64, c_i32, c_vp]),
     ("gvt_krr_cg_solve_multishift", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
                                             c_i32, c_vp, c_dbl, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
+    ("gvt_klr_newton_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl, c_vp,
+                                     c_i32, c_dbl, c_dbl, c_i64, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_minres_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
                                      c_vp, c_dbl, c_i64, c_i64, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
@@ -568,6 +570,21 @@ def krr_cg_solve_multishift(handle, plan, kind, M, N, y, lambdas, rel_tol=1e-6, 
     if st not in (GVT_OK, 6, 7):
         raise GvtError(st, "gvt_krr_cg_solve_multishift", last_error())
     return A.t(), st, info, [rr[k] for k in range(len(lambdas))]
+
+
+def klr_newton_solve(handle, plan, kind, M, N, y, lam, newton_iters=30, cg_tol=1e-10, grad_tol=1e-10,
+                     max_cg_iter=100000, symmetric=True, stream=None):
+    """Kernel logistic regression (labels +-1) by Newton's method; returns (a, status, info)."""
+    torch = _torch()
+    a = torch.zeros_like(y)
+    info = gvt_solve_info()
+    st = load().gvt_klr_newton_solve(handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
+                                     ctypes.byref(matrix(N, symmetric)) if N is not None else None, ptr(y),
+                                     float(lam), ptr(a), int(newton_iters), float(cg_tol), float(grad_tol),
+                                     int(max_cg_iter), ctypes.byref(info), stream_ptr(stream))
+    if st not in (GVT_OK, 6, 7):
+        raise GvtError(st, "gvt_klr_newton_solve", last_error())
+    return a, st, info
 
 
 def krr_minres_solve(handle, plan, kind, M, N, y, lam, rel_tol=1e-6, max_iter=10000, record_every=0,
