@@ -303,3 +303,32 @@ template <class T>
 gvt_status vec_zero(T* x, int64_t n, cudaStream_t s);
 
 }  // namespace gvt
+
+namespace gvt {
+// ---------------------------------------------------------------- host-driven Krylov solvers
+// (MINRES, multi-shift CG, the logistic Newton solver): dot products reduce to one partial
+// sum per block, which the host adds in a fixed order, so runs are reproducible.
+constexpr int kRedGrid = 512;      // blocks of a reduction launch
+constexpr int kRedBlock = 256;     // threads per block
+
+#ifdef __CUDACC__
+// block sum of v into part[slot * gridDim.x + blockIdx.x]; may be called twice in a row
+__device__ __forceinline__ void block_sum_slot(double v, double* __restrict__ part, int slot)
+{
+    __shared__ double sh[kRedBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kRedBlock / 32; ++i) t += sh[i];
+        part[(int64_t)slot * gridDim.x + blockIdx.x] = t;
+    }
+}
+#endif
+
+// out[k] = the fixed-order sum of slot k's kRedGrid partials (k < slots); synchronises s
+gvt_status host_reduce(const double* part_dev, int slots, std::vector<double>& host, double* out, cudaStream_t s);
+}  // namespace gvt

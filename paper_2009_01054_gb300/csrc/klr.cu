@@ -18,24 +18,8 @@
 namespace gvt {
 namespace {
 
-constexpr int kKlBlocks = 512;
-constexpr int kKlThreads = 256;
-
-__device__ __forceinline__ void kl_block_sum(double v, double* __restrict__ part, int slot, int nslots)
-{
-    __shared__ double sh[kKlThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kKlThreads / 32; ++i) t += sh[i];
-        part[(int64_t)slot * gridDim.x + blockIdx.x] = t;
-    }
-    (void)nslots;
-}
+constexpr int kKlBlocks = kRedGrid;
+constexpr int kKlThreads = kRedBlock;
 
 __device__ __forceinline__ double sigmoid_pos(double x) { return 0.5 * (1.0 + tanh(0.5 * x)); }
 
@@ -53,7 +37,7 @@ kl_prep(const double* __restrict__ f, const double* __restrict__ y, const double
         sw[i] = sqrt(s * (1.0 - s));
         acc += bi * bi;
     }
-    kl_block_sum(acc, part, 0, 1);
+    block_sum_slot(acc, part, 0);
 }
 
 __global__ void kl_mul(const double* __restrict__ x, const double* __restrict__ sw, int64_t n, double* __restrict__ out)
@@ -73,7 +57,7 @@ kl_shift_dot(double* __restrict__ w, const double* __restrict__ sw, const double
         w[i] = x;
         acc += p[i] * x;
     }
-    kl_block_sum(acc, part, 0, 1);
+    block_sum_slot(acc, part, 0);
 }
 
 // c += alpha p, r -= alpha w; part = r . r
@@ -88,7 +72,7 @@ kl_cg_update(double* __restrict__ c, double* __restrict__ r, const double* __res
         r[i] = x;
         acc += x * x;
     }
-    kl_block_sum(acc, part, 0, 1);
+    block_sum_slot(acc, part, 0);
 }
 
 __global__ void kl_pupdate(double* __restrict__ p, const double* __restrict__ r, double beta, int64_t n)
@@ -110,7 +94,7 @@ kl_cg_init(const double* __restrict__ rhs, int64_t n, double* __restrict__ c, do
         c[i] = 0.0;
         acc += x * x;
     }
-    kl_block_sum(acc, part, 0, 1);
+    block_sum_slot(acc, part, 0);
 }
 
 // d = (b - sw c) / lam; part slots: 0 = d . f, 1 = a . f
@@ -126,8 +110,8 @@ kl_direction(const double* __restrict__ b, const double* __restrict__ sw, const 
         df += x * f[i];
         af += a[i] * f[i];
     }
-    kl_block_sum(df, part, 0, 2);
-    kl_block_sum(af, part, 1, 2);
+    block_sum_slot(df, part, 0);
+    block_sum_slot(af, part, 1);
 }
 
 // part slots: 0 = d . Kd, 1 = sum log(1 + exp(-y (f + t Kd)))
@@ -141,8 +125,8 @@ kl_line(const double* __restrict__ f, const double* __restrict__ Kd, const doubl
         const double z = -y[i] * (f[i] + t * Kd[i]);
         loss += z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
     }
-    kl_block_sum(dkd, part, 0, 2);
-    kl_block_sum(loss, part, 1, 2);
+    block_sum_slot(dkd, part, 0);
+    block_sum_slot(loss, part, 1);
 }
 
 __global__ void kl_step(double* __restrict__ a, double* __restrict__ f, const double* __restrict__ d,
@@ -154,17 +138,9 @@ __global__ void kl_step(double* __restrict__ a, double* __restrict__ f, const do
     }
 }
 
-// fixed-order host sums of `slots` partial arrays
 gvt_status kl_sums(const double* part_dev, int slots, std::vector<double>& host, double* out, cudaStream_t s)
 {
-    GVT_CUDA(cudaMemcpyAsync(host.data(), part_dev, sizeof(double) * kKlBlocks * slots, cudaMemcpyDeviceToHost, s));
-    GVT_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < slots; ++k) {
-        double t = 0.0;
-        for (int b = 0; b < kKlBlocks; ++b) t += host[(size_t)k * kKlBlocks + b];
-        out[k] = t;
-    }
-    return GVT_OK;
+    return host_reduce(part_dev, slots, host, out, s);
 }
 
 }  // namespace

@@ -16,22 +16,8 @@
 namespace gvt {
 namespace {
 
-constexpr int kMrBlocks = 512;
-constexpr int kMrThreads = 256;
-
-__device__ __forceinline__ void block_sum_to(double v, double* __restrict__ part)
-{
-    __shared__ double sh[kMrThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kMrThreads / 32; ++i) t += sh[i];
-        part[blockIdx.x] = t;
-    }
-}
+constexpr int kMrBlocks = kRedGrid;
+constexpr int kMrThreads = kRedBlock;
 
 // w = w + lambda v - beta v_prev; part = block sums of v . w
 __global__ void __launch_bounds__(kMrThreads)
@@ -44,7 +30,7 @@ mr_shift_dot(double* __restrict__ w, const double* __restrict__ v, const double*
         w[i] = x;
         acc += v[i] * x;
     }
-    block_sum_to(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 // w -= alpha v; part = block sums of w . w
@@ -58,7 +44,7 @@ mr_axpy_norm(double* __restrict__ w, const double* __restrict__ v, double alpha,
         w[i] = x;
         acc += x * x;
     }
-    block_sum_to(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 // d_k = (v - delta d1 - eps d2) / gamma into d2; a += tau d_k; w *= 1 / beta_next (v_{k+1})
@@ -85,7 +71,7 @@ mr_residual(const double* __restrict__ y, const double* __restrict__ w, const do
         const double r = y[i] - w[i] - lam * a[i];
         acc += r * r;
     }
-    block_sum_to(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 __global__ void mr_scale(const double* __restrict__ x, double s, int64_t n, double* __restrict__ out)
@@ -99,21 +85,29 @@ __global__ void mr_dot(const double* __restrict__ x, int64_t n, double* __restri
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         acc += x[i] * x[i];
-    block_sum_to(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
-// fixed-order host sum of the block partials
 gvt_status host_sum(const double* part_dev, std::vector<double>& part_host, double* out, cudaStream_t s)
 {
-    GVT_CUDA(cudaMemcpyAsync(part_host.data(), part_dev, sizeof(double) * kMrBlocks, cudaMemcpyDeviceToHost, s));
-    GVT_CUDA(cudaStreamSynchronize(s));
-    double t = 0.0;
-    for (int b = 0; b < kMrBlocks; ++b) t += part_host[b];
-    *out = t;
-    return GVT_OK;
+    return host_reduce(part_dev, 1, part_host, out, s);
 }
 
 }  // namespace
+
+gvt_status host_reduce(const double* part_dev, int slots, std::vector<double>& host, double* out, cudaStream_t s)
+{
+    if (host.size() < (size_t)kRedGrid * slots) host.resize((size_t)kRedGrid * slots);
+    GVT_CUDA(cudaMemcpyAsync(host.data(), part_dev, sizeof(double) * kRedGrid * slots, cudaMemcpyDeviceToHost, s));
+    GVT_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < slots; ++k) {
+        double t = 0.0;
+        for (int b = 0; b < kRedGrid; ++b) t += host[(size_t)k * kRedGrid + b];
+        out[k] = t;
+    }
+    return GVT_OK;
+}
+
 }  // namespace gvt
 
 using namespace gvt;

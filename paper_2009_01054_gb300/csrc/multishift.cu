@@ -19,8 +19,8 @@
 namespace gvt {
 namespace {
 
-constexpr int kMsBlocks = 512;
-constexpr int kMsThreads = 256;
+constexpr int kMsBlocks = kRedGrid;
+constexpr int kMsThreads = kRedBlock;
 constexpr int kMaxShifts = 32;
 
 struct ShiftCoefs {
@@ -31,27 +31,13 @@ struct ShiftCoefs {
     int count;
 };
 
-__device__ __forceinline__ void ms_block_sum(double v, double* __restrict__ part)
-{
-    __shared__ double sh[kMsThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kMsThreads / 32; ++i) t += sh[i];
-        part[blockIdx.x] = t;
-    }
-}
-
 __global__ void __launch_bounds__(kMsThreads)
 ms_dot(const double* __restrict__ x, int64_t n, double* __restrict__ part)
 {
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         acc += x[i] * x[i];
-    ms_block_sum(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 // w += lambda_0 p; part = block sums of p . w
@@ -64,7 +50,7 @@ ms_shift_dot(double* __restrict__ w, const double* __restrict__ p, double lam0, 
         w[i] = x;
         acc += p[i] * x;
     }
-    ms_block_sum(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 // r -= alpha w; part = block sums of r . r
@@ -78,7 +64,7 @@ ms_residual_update(double* __restrict__ r, const double* __restrict__ w, double 
         r[i] = x;
         acc += x * x;
     }
-    ms_block_sum(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 // every active shift: a_s += alpha_s p_s, p_s = zeta_s r + beta_s p_s; base p = r + beta p
@@ -123,17 +109,12 @@ ms_true_residual(const double* __restrict__ y, const double* __restrict__ w, con
         const double e = y[i] - w[i] - lam * a[i];
         acc += e * e;
     }
-    ms_block_sum(acc, part);
+    block_sum_slot(acc, part, 0);
 }
 
 gvt_status ms_sum(const double* part_dev, std::vector<double>& host, double* out, cudaStream_t s)
 {
-    GVT_CUDA(cudaMemcpyAsync(host.data(), part_dev, sizeof(double) * kMsBlocks, cudaMemcpyDeviceToHost, s));
-    GVT_CUDA(cudaStreamSynchronize(s));
-    double t = 0.0;
-    for (int b = 0; b < kMsBlocks; ++b) t += host[b];
-    *out = t;
-    return GVT_OK;
+    return host_reduce(part_dev, 1, host, out, s);
 }
 
 }  // namespace
