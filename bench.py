@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--streams", type=int, default=3,
                     help="streams (each with its own handle and plan) over which the nine independent "
                          "products of a step are spread")
+    ap.add_argument("--tc-pairs", default="auto", choices=["auto", "off", "on"],
+                    help="tile form of the tensor-core GEMM: auto = the library's choice (one SM per tile); "
+                         "off = one SM per 128-row tile; on = SM pairs (256-row tiles, tcgen05 cta_group::2)")
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=256)
@@ -290,6 +293,10 @@ def run_gvt(args, ws, rank, local):
         for h in handles:
             gvt.gvt_set_stage1_engine(h.h, code)
 
+    pair_code = {"auto": gvt.GVT_TC_PAIRS_AUTO, "off": gvt.GVT_TC_PAIRS_OFF, "on": gvt.GVT_TC_PAIRS_ON}
+    for h in handles:
+        gvt.gvt_set_tc_pairs(h.h, pair_code[args.tc_pairs])
+
     set_engine(engine_code)
 
     def step(nstreams=S, after=None):
@@ -478,7 +485,7 @@ def run_gvt(args, ws, rank, local):
                           "kernels": KINDS, "kronecker_terms": sum(TERMS.values()),
                           "pair_terms_per_step": pts,
                           "l2": "flushed (512 MB write) before every timed step, outside the events",
-                          "streams": S,
+                          "streams": S, "tc_pairs": args.tc_pairs,
                           "roofline_timing": "per-stage CUDA events of the library, over a second pass of the same "
                                              "K steps (the timed pass runs without them)",
                           "parallelism": "replicas: independent problems per rank (seed = rank)"},

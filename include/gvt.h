@@ -268,11 +268,30 @@ gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine);
 gvt_status gvt_check_device_errors(gvt_handle* h, void* stream);
 
 /*
+ * Tile form of the tensor-core GEMM of the dense engines.  Both forms compute
+ * the same chunked FP32 sums; they agree to FP32 rounding.
+ *  GVT_TC_PAIRS_AUTO : the library's choice (default); currently one SM per
+ *                      tile, which measured as fast as SM pairs on GB300
+ *  GVT_TC_PAIRS_OFF  : one SM per 128-row output tile (tcgen05.mma cta_group::1)
+ *  GVT_TC_PAIRS_ON   : a cluster of two SMs per 256-row output tile
+ *                      (tcgen05.mma cta_group::2), also for 128 rows or fewer
+ * Returns GVT_ERR_INVALID_ARG for any other value.
+ */
+typedef enum gvt_tc_pairs {
+    GVT_TC_PAIRS_AUTO = 0,
+    GVT_TC_PAIRS_OFF = 1,
+    GVT_TC_PAIRS_ON = 2
+} gvt_tc_pairs;
+
+gvt_status gvt_set_tc_pairs(gvt_handle* h, int32_t mode);
+
+/*
  * The tensor-core GEMM behind GVT_STAGE1_TC_BF16X3, exposed for testing:
  * C[M x N] = A[M x K] B[N x K]^T with A, B BF16 row-major (K innermost,
  * K a multiple of 64, lda and ldb multiples of 8, 16-byte aligned), C FP32
- * row-major with leading dimension ldc >= N.  Asynchronous; device-side
- * timeouts are reported by gvt_check_device_errors.
+ * row-major with leading dimension ldc >= N.  The tile form is the handle's
+ * (gvt_set_tc_pairs).  Asynchronous; device-side timeouts are reported by
+ * gvt_check_device_errors.
  */
 gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
                             int64_t ldc, int64_t M, int64_t N, int64_t K, void* stream);

@@ -499,6 +499,16 @@ gvt_status gvt_tanimoto_kernel(gvt_handle* h, const uint32_t* X, int64_t rows_x,
     return tanimoto_kernel(X, rows_x, Y, rows_y, words, K, ldk, out_dtype, as_stream(stream));
 }
 
+gvt_status gvt_set_tc_pairs(gvt_handle* h, int32_t mode)
+{
+    if (!h || mode < GVT_TC_PAIRS_AUTO || mode > GVT_TC_PAIRS_ON) {
+        set_error("gvt_set_tc_pairs: bad handle or mode");
+        return GVT_ERR_INVALID_ARG;
+    }
+    h->tc_pairs = mode;
+    return GVT_OK;
+}
+
 gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine)
 {
     if (!h || engine < GVT_STAGE1_SIMT || engine > GVT_STAGES_AUTO) {
@@ -535,7 +545,7 @@ gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const voi
         set_error("gvt_tc_gemm_bf16: NULL argument");
         return GVT_ERR_INVALID_ARG;
     }
-    return tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, handle_err_word(h), as_stream(stream));
+    return tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, handle_err_word(h), as_stream(stream), h->tc_pairs);
 }
 
 gvt_status gvt_convert(const void* src, int32_t src_dtype, void* dst, int32_t dst_dtype, int64_t n,

@@ -319,14 +319,14 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
 }
 
 gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
-                      cudaStream_t s)
+                      cudaStream_t s, int pair_mode)
 {
     if (a.kp != b.kp) {
         set_error("dense stage: operand widths differ");
         return GVT_ERR_INVALID_ARG;
     }
     return tc_gemm(a.data, 3 * a.kp, b.data, 3 * b.kp, C, ldc, a.rows, b.rows, 3 * a.kp, f16,
-                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s);
+                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s, pair_mode);
 }
 
 gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s)

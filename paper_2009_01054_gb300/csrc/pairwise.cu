@@ -46,12 +46,12 @@ struct Compiled {
 // Engine choice of GVT_STAGES_AUTO for one stage: the dense FP16x3 GEMM (rows x cols
 // outputs, inner length K) against the sparse SIMT stage doing simt_flops useful flops.
 // Rates measured on GB300 at the homogeneous m = q = 2000 workload: SIMT stages about
-// 4.5e12 useful flop/s, the split GEMM about 0.9e15 flop/s, the split and densify passes
+// 4.5e12 useful flop/s, the split GEMM about 1.2e15 flop/s, the split and densify passes
 // about 3e12 B/s, and about 15 us of fixed cost per dense stage.
 bool dense_pays(int64_t rows, int64_t cols, int64_t K, double simt_flops)
 {
     const double kp = (double)dense_kp(K);
-    const double t_dense = 6.0 * rows * cols * kp / 0.9e15 +
+    const double t_dense = 6.0 * rows * cols * kp / 1.2e15 +
                            (6.0 * (double)(rows + cols) * kp + 4.0 * (double)rows * cols) / 3e12 + 15e-6;
     return t_dense < simt_flops / 4.5e12;
 }
@@ -387,7 +387,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             {
                 StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * X * 3.0 * kp,
                              2.0 * 3.0 * kp * (Y + X) + 4.0 * Y * X);
-                GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s));
+                GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s, h->tc_pairs));
             }
         } else if (g.fb == GVT_FACTOR_IDENTITY) {
             GVT_CHECK(vec_zero<T>(S, Y * lds, s));
@@ -425,7 +425,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 {
                     StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * 3.0 * kp,
                                  2.0 * 3.0 * kp * (mb + Y) + 4.0 * mb * Y);
-                    GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s));
+                    GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs));
                 }
                 GVT_CHECK(dense_gather(C2, ldc2, outs, reinterpret_cast<float*>(u), s));
             } else {

@@ -23,9 +23,23 @@
 // long accumulation chain drifts systematically (about -1e-5 relative after
 // K = 4096 on positive data, measured on GB300), while chunks of 512 stay near
 // FP32 rounding (-7e-7) and the folds round to nearest.
+// SM-pair form (PAIR = true): a cluster of two CTAs on neighbouring SMs
+// computes a 256 x BN tile with tcgen05.mma.cta_group::2 (M = 256).  Each CTA
+// loads its own 128 rows of A and half of the BN rows of B, so per SM the
+// tensor core reads 128 + BN/2 operand rows from shared memory per k-block
+// instead of 128 + BN; each CTA's TMEM holds the accumulator of its own 128
+// rows.  Only the even CTA issues MMAs.  The tile loads of both CTAs
+// complete on the even CTA's ring barrier (cp.async.bulk.tensor .cta_group::2),
+// the MMA commits arrive on both CTAs' barriers (multicast), and the odd CTA's
+// folding warps release an accumulator on the even CTA's barrier.  (Having the
+// odd CTA wait for its own loads and forward their completion instead adds a
+// hop to every ring slot and measured half the speed.)
+// Epilogue: the folding warps stage the 128 x BN tile in the (then idle) ring
+// memory and store it row by row, 32 consecutive columns per warp instruction.
 // Every wait on an mbarrier is bounded by a clock budget; on expiry the
 // thread records GVT_ERR_TIMEOUT in a device error word, the kernel waits
-// (bounded) for the copies it issued, frees its TMEM and returns.
+// (bounded) for the copies it issued and for its MMAs, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -44,16 +58,18 @@ constexpr int TC_THREADS = 320;           // producer warp, MMA warp, 8 folding 
 constexpr int TC_FOLD_WARPS = 8;
 constexpr int TC_CHUNK = 8;               // k-blocks (8 x 64 = 512 of K) per accumulation chunk
 constexpr long long TC_TIMEOUT_CYCLES = 4000000000ll;   // about 2 s at 2 GHz
+constexpr long long TC_DRAIN_CYCLES = 20000000ll;       // about 10 ms
 
 struct TcShared {
     uint64_t full[TC_MAX_STAGES];
     uint64_t empty[TC_MAX_STAGES];
     uint64_t acc_full[2];    // chunk accumulated into TMEM buffer b
     uint64_t acc_empty[2];   // folding warps have read buffer b
+    uint64_t mma_done;       // every MMA this CTA issued has completed (SM-pair form)
     uint32_t tmem_base;
     int timeout;
     int issued;      // TMA stage loads issued
-    int consumed;    // stage loads the MMA thread has waited for
+    int consumed;    // stage loads the MMA thread has waited for (one-SM form)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -90,13 +106,49 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// try_wait that also acquires what other CTAs of the cluster released before arriving
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity; false on timeout.
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
+    while (!(CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)))
         if (clock64() - t0 > TC_TIMEOUT_CYCLES) return false;
     return true;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Arrive on the barrier at the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, uint32_t rank)
+{
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(bar)), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
+// Every thread of both CTAs of the cluster.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
@@ -107,42 +159,98 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+// SM-pair form: load into this CTA's shared memory, completing on the barrier at the same offset
+// in CTA `rank` of the pair.
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint64_t* bar, uint32_t rank,
+                                                 int x, int y)
 {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
-                 "r"(ncols)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_relinquish()
-{
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 x BF16 -> FP32
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate)
-{
+    uint32_t rbar;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(smem_u32(bar)), "r"(rank));
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(rbar), "r"(x), "r"(y)
         : "memory");
 }
 
-// Arrive on `bar` once every tcgen05 operation issued so far by this thread completed.
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Every tcgen05 instruction of one kernel uses the same CTA group: ::1 in the one-SM form, ::2 in
+// the SM-pair form, where the allocation is made collectively by warp 0 of both CTAs.
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+{
+    if constexpr (PAIR)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                     "r"(ncols)
+                     : "memory");
+    else
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                     "r"(ncols)
+                     : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_relinquish()
+{
+    if constexpr (PAIR)
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    else
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    if constexpr (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, 16-bit x 16-bit -> FP32
+template <bool PAIR>
+__device__ __forceinline__ void umma_f16kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate)
+{
+    if constexpr (PAIR)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
+// Arrive on `bar` once every tcgen05 operation issued so far by this thread completed: in the
+// one-SM form on this CTA's barrier, in the SM-pair form on the barrier at the same offset in
+// both CTAs of the pair.
+template <bool PAIR>
 __device__ __forceinline__ void umma_commit(uint64_t* bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+    if constexpr (PAIR)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+            ::"r"(smem_u32(bar)), "h"((uint16_t)3)
+            : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+}
+
+// SM-pair form: arrive on this CTA's barrier only.
+__device__ __forceinline__ void umma_commit_local_pair(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
 }
@@ -180,29 +288,37 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
 // A and B both BF16 (format 1 at bits 7-9 and 10-12) or both FP16 (format 0),
-// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-template <int BN, bool F16>
+// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+// (M = 128 for one SM, 256 for an SM pair).
+template <int BN, bool F16, bool PAIR>
 __host__ __device__ constexpr uint32_t idesc_f16kind_f32()
 {
     return (1u << 4) | (F16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(BN >> 3) << 17) |
-           ((uint32_t)(TC_BM >> 4) << 24);
+           ((uint32_t)((PAIR ? 2 * TC_BM : TC_BM) >> 4) << 24);
+}
+
+// B rows one CTA loads per k-block: all BN, or its half of them in the SM-pair form
+template <int BN, bool PAIR>
+__host__ __device__ constexpr int tc_b_rows()
+{
+    return PAIR ? BN / 2 : BN;
 }
 
 // ring depth: as many A + B stages as fit in shared memory beside the barriers; narrow tiles
 // keep a 4-deep ring so that two CTAs share an SM (their grids are the split-K ones)
-template <int BN>
+template <int BN, bool PAIR>
 __host__ __device__ constexpr int tc_stages()
 {
-    constexpr size_t stage = (size_t)(TC_BM + BN) * TC_BK * 2;
+    constexpr size_t stage = (size_t)(TC_BM + tc_b_rows<BN, PAIR>()) * TC_BK * 2;
     constexpr size_t n = (TC_SMEM_LIMIT - sizeof(TcShared) - 1024) / stage;
     constexpr int cap = BN <= 64 ? 4 : TC_MAX_STAGES;
     return n > (size_t)cap ? cap : (int)n;
 }
 
-template <int BN>
+template <int BN, bool PAIR>
 __host__ __device__ constexpr size_t tc_smem_bytes()
 {
-    return (size_t)tc_stages<BN>() * (TC_BM + BN) * TC_BK * 2 + sizeof(TcShared) + 1024;
+    return (size_t)tc_stages<BN, PAIR>() * (TC_BM + tc_b_rows<BN, PAIR>()) * TC_BK * 2 + sizeof(TcShared) + 1024;
 }
 
 // TMEM columns of the two accumulators, rounded up to a power of two
@@ -212,7 +328,7 @@ __host__ __device__ constexpr uint32_t tc_tmem_cols()
     return 2 * BN <= 128 ? 128u : 2 * BN <= 256 ? 256u : 512u;
 }
 
-template <int BN, bool F16>
+template <int BN, bool F16, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t ldc, int M, int N, int kb_total, int kb_per_split,
@@ -220,20 +336,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                int* __restrict__ err)
 {
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "UMMA N");
-    constexpr int TC_STAGES = tc_stages<BN>();
+    static_assert(!PAIR || BN % 16 == 0, "UMMA N for M = 256");
+    constexpr int TC_STAGES = tc_stages<BN, PAIR>();
     static_assert(TC_STAGES >= 2, "ring depth");
+    constexpr int B_ROWS = tc_b_rows<BN, PAIR>();
     constexpr int A_BYTES = TC_BM * TC_BK * 2;
-    constexpr int B_BYTES = BN * TC_BK * 2;
+    constexpr int B_BYTES = B_ROWS * TC_BK * 2;
+    static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms");
     constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     constexpr int HALF = BN / 2;            // columns one folding warp owns
     constexpr uint32_t TMEM_COLS = tc_tmem_cols<BN>();  // two accumulators
     extern __shared__ unsigned char smem_raw[];
-    // 1024-byte alignment of the shared-space offset (swizzle atoms, descriptor base offset 0)
+    // 1024-byte alignment of the shared-space offset (swizzle atoms, descriptor base offset 0);
+    // the offset is the same in both CTAs of a pair, as the leader's descriptors require
     unsigned char* tiles = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     TcShared* sh = reinterpret_cast<TcShared*>(tiles + TC_STAGES * STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    // SM pair: CTA rank 0 (the leader) holds rows 0-127 of the 256-row tile and B rows
+    // 0..BN/2-1, rank 1 the rest
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
+    const int m0 = PAIR ? (int)(blockIdx.x >> 1) * (2 * TC_BM) + (int)rank * TC_BM : (int)blockIdx.x * TC_BM;
+    const int n0 = blockIdx.y * BN;
+    const int nb0 = n0 + (int)rank * B_ROWS;   // first B row this CTA loads
     const int kb0 = blockIdx.z * kb_per_split;
     const int kb1 = min(kb_total, kb0 + kb_per_split);
     const int nkb = max(kb1 - kb0, 0);
@@ -241,24 +367,26 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < TC_STAGES; ++st) {
-            mbar_init(&sh->full[st], 1);
+            mbar_init(&sh->full[st], 1);   // SM pair: only the leader's are used
             mbar_init(&sh->empty[st], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->acc_full[b], 1);
-            mbar_init(&sh->acc_empty[b], TC_FOLD_WARPS);
+            mbar_init(&sh->acc_empty[b], PAIR ? 2 * TC_FOLD_WARPS : TC_FOLD_WARPS);
         }
+        mbar_init(&sh->mma_done, 1);
         sh->timeout = 0;
         sh->issued = 0;
         sh->consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        tmem_alloc(&sh->tmem_base, TMEM_COLS);
-        tmem_relinquish();
+        tmem_alloc<PAIR>(&sh->tmem_base, TMEM_COLS);
+        tmem_relinquish<PAIR>();
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // barriers of both CTAs initialised before any remote arrival
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
 
@@ -274,22 +402,29 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 }
                 if (*(volatile int*)&sh->timeout) break;
                 unsigned char* sa = tiles + st * STAGE_BYTES;
-                mbar_expect_tx(&sh->full[st], STAGE_BYTES);
                 const int kx = (kb0 + i) * TC_BK;
-                tma_load_2d(sa, &mapA, &sh->full[st], kx, m0);
-                tma_load_2d(sa + A_BYTES, &mapB, &sh->full[st], kx, n0);
+                if constexpr (PAIR) {
+                    // the leader's slot completes when the loads of both CTAs landed
+                    if (leader) mbar_expect_tx(&sh->full[st], 2 * STAGE_BYTES);
+                    tma_load_2d_pair(sa, &mapA, &sh->full[st], 0, kx, m0);
+                    tma_load_2d_pair(sa + A_BYTES, &mapB, &sh->full[st], 0, kx, nb0);
+                } else {
+                    mbar_expect_tx(&sh->full[st], STAGE_BYTES);
+                    tma_load_2d(sa, &mapA, &sh->full[st], kx, m0);
+                    tma_load_2d(sa + A_BYTES, &mapB, &sh->full[st], kx, nb0);
+                }
             }
             sh->issued = i;
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && (!PAIR || leader)) {
             // ---- MMA issuer: chunk c accumulates into TMEM buffer c & 1
-            constexpr uint32_t idesc = idesc_f16kind_f32<BN, F16>();
+            constexpr uint32_t idesc = idesc_f16kind_f32<BN, F16, PAIR>();
             int i = 0;
             bool ok = true;
             for (int c = 0; c < nchunks && ok; ++c) {
                 const int b = c & 1;
-                if (c >= 2 && !mbar_wait(&sh->acc_empty[b], ((c >> 1) - 1) & 1)) {
+                if (c >= 2 && !mbar_wait<PAIR>(&sh->acc_empty[b], ((c >> 1) - 1) & 1)) {
                     atomicExch(&sh->timeout, 1);
                     break;
                 }
@@ -298,7 +433,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 const int i_end = min(nkb, (c + 1) * TC_CHUNK);
                 for (; i < i_end; ++i) {
                     const int st = i % TC_STAGES;
-                    if (!mbar_wait(&sh->full[st], (i / TC_STAGES) & 1) || *(volatile int*)&sh->timeout) {
+                    if (!mbar_wait<PAIR>(&sh->full[st], (i / TC_STAGES) & 1) || *(volatile int*)&sh->timeout) {
                         atomicExch(&sh->timeout, 1);
                         ok = false;
                         break;
@@ -308,13 +443,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sa + A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 16; ++kk)   // +32 bytes along K per instruction
-                        umma_bf16(dst, da + 2 * kk, db + 2 * kk, idesc,
-                                  (i > c * TC_CHUNK || kk > 0) ? 1u : 0u);
-                    umma_commit(&sh->empty[st]);
+                        umma_f16kind<PAIR>(dst, da + 2 * kk, db + 2 * kk, idesc,
+                                           (i > c * TC_CHUNK || kk > 0) ? 1u : 0u);
+                    umma_commit<PAIR>(&sh->empty[st]);
                 }
-                if (ok) umma_commit(&sh->acc_full[b]);
+                if (ok) umma_commit<PAIR>(&sh->acc_full[b]);
             }
             sh->consumed = i;
+            if constexpr (PAIR) {
+                // the peer's shared memory and TMEM stay in use until these MMAs complete
+                umma_commit_local_pair(&sh->mma_done);
+                if (!mbar_wait(&sh->mma_done, 0)) atomicExch(&sh->timeout, 1);
+            }
         }
     } else {
         // ---- folding warps: FP32 register sums of the chunk accumulators
@@ -357,20 +497,34 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh->acc_empty[b]);
+            if (lane == 0) {
+                if (PAIR && !leader) mbar_arrive_remote(&sh->acc_empty[b], 0);
+                else mbar_arrive(&sh->acc_empty[b]);
+            }
         }
-        const int gm = m0 + row;
-        if (good && *(volatile int*)&sh->timeout == 0 && gm < M) {
-            const float rs = row_scale ? row_scale[gm] : 1.f;
-            float* crow = C + (int64_t)gm * ldc + n0 + col0;
-            const int lim = N - (n0 + col0);
+        // Stage the tile in the ring memory: once the last chunk's accumulator has arrived, every
+        // MMA, and with it every read of the ring and every tile load, has completed.  The row
+        // stride BN + 1 puts the 32 rows a warp writes at one column in 32 different banks.
+        constexpr int SLD = BN + 1;
+        static_assert((size_t)TC_BM * SLD * sizeof(float) <= (size_t)TC_STAGES * STAGE_BYTES, "staging");
+        float* stage = reinterpret_cast<float*>(tiles);
+        if (good) {
 #pragma unroll
-            for (int e = 0; e < HALF; ++e) {
-                if (e < lim) {
-                    float f = acc[e] * rs;
-                    if (col_scale) f *= col_scale[n0 + col0 + e];
-                    if (atomic_out) atomicAdd(crow + e, f);
-                    else crow[e] = f;
+            for (int e = 0; e < HALF; ++e) stage[row * SLD + col0 + e] = acc[e];
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(TC_FOLD_WARPS * 32) : "memory");   // folding warps only
+        if (nkb > 0 && *(volatile int*)&sh->timeout == 0) {
+            const int ncols = min(BN, N - n0);
+            for (int r = fw; r < TC_BM; r += TC_FOLD_WARPS) {
+                const int gm = m0 + r;
+                if (gm >= M) break;
+                const float rs = row_scale ? row_scale[gm] : 1.f;
+                float* crow = C + (int64_t)gm * ldc + n0;
+                for (int cc = lane; cc < ncols; cc += 32) {
+                    float f = stage[r * SLD + cc] * rs;
+                    if (col_scale) f *= col_scale[n0 + cc];
+                    if (atomic_out) atomicAdd(crow + cc, f);
+                    else crow[cc] = f;
                 }
             }
         }
@@ -379,15 +533,26 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     __syncthreads();
     if (threadIdx.x == 0 && sh->timeout) {
         atomicExch(err, (int)GVT_ERR_TIMEOUT);
-        // wait (bounded) for the tile copies that were issued but never consumed
-        for (int i = sh->consumed; i < sh->issued; ++i)
-            if (!mbar_wait(&sh->full[i % TC_STAGES], (i / TC_STAGES) & 1)) break;
+        if constexpr (PAIR) {
+            // the loads of both CTAs complete on the leader's barriers, whose phases need not
+            // finish after a timeout: give copies in flight a fixed time to land (they take
+            // microseconds)
+            const long long t0 = clock64();
+            while (clock64() - t0 < TC_DRAIN_CYCLES) {
+            }
+        } else {
+            // wait (bounded) for the tile copies that were issued but never consumed
+            for (int i = sh->consumed; i < sh->issued; ++i)
+                if (!mbar_wait(&sh->full[i % TC_STAGES], (i / TC_STAGES) & 1)) break;
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    // SM pair: neither CTA frees TMEM or exits while the other may still arrive on its barriers
+    if constexpr (PAIR) cluster_sync();
+    else __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, TMEM_COLS);
+        tmem_dealloc<PAIR>(tmem, TMEM_COLS);
     }
 }
 
@@ -434,11 +599,12 @@ gvt_status make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K,
     return GVT_OK;
 }
 
-template <int BN, bool F16>
+template <int BN, bool F16, bool PAIR>
 gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M, int64_t N,
                      int64_t K, const float* rs, const float* cs, int* err, cudaStream_t s)
 {
-    const int gx = (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
+    const int pairs = (int)((M + 2 * TC_BM - 1) / (2 * TC_BM));
+    const int gx = PAIR ? 2 * pairs : (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
     const int kb_total = (int)(K / TC_BK);
     const int tiles = gx * gy;
     // split K only when the output tiles alone leave most SMs idle
@@ -451,20 +617,42 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
         zero_rows_kernel<<<152 * 4, 256, 0, s>>>(C, ldc, M, N);
         GVT_LAUNCH_CHECK("tc zero");
     }
-    const size_t smem = tc_smem_bytes<BN>();
-    GVT_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(gx, gy, splits);
-    tc_gemm_kernel<BN, F16><<<grid, TC_THREADS, smem, s>>>(ma, mb, C, ldc, (int)M, (int)N, kb_total, kb_per,
-                                                            atomic_out, rs, cs, err);
+    const size_t smem = tc_smem_bytes<BN, PAIR>();
+    auto kern = tc_gemm_kernel<BN, F16, PAIR>;
+    GVT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(gx, gy, splits);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = PAIR ? 2 : 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = PAIR ? 1 : 0;
+    GVT_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, C, ldc, (int)M, (int)N, kb_total, kb_per, atomic_out, rs, cs,
+                                err));
     GVT_LAUNCH_CHECK("tc_gemm");
     return GVT_OK;
+}
+
+template <bool F16, bool PAIR>
+gvt_status launch_tc_bn(int BN, const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M,
+                        int64_t N, int64_t K, const float* rs, const float* cs, int* err, cudaStream_t s)
+{
+    if (BN == 64) return launch_tc<64, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    if (BN == 128) return launch_tc<128, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    if (BN == 224) return launch_tc<224, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    return launch_tc<256, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
 }
 
 }  // namespace
 
 gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                    int64_t N, int64_t K, bool f16, const float* row_scale, const float* col_scale, int* err,
-                   cudaStream_t s)
+                   cudaStream_t s, int pair_mode)
 {
     if (M <= 0 || N <= 0) return GVT_OK;
     if (K <= 0 || K % TC_BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N ||
@@ -478,6 +666,9 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
         return GVT_ERR_UNSUPPORTED;
     }
     GVT_CHECK(get_encode());
+    // SM pairs only on request: on GB300 both forms reach the same rate on these shapes (the
+    // pair form reads 30 % fewer operand bytes per SM, but the loads are not the bound)
+    const bool pair = pair_mode == GVT_TC_PAIRS_ON;
     // widest N tile that still gives >= 64 output tiles (fewer split-K partial sums to reduce);
     // 224 instead of 256 where it fills more of the 152 SMs in the same single wave
     const int64_t gx = (M + TC_BM - 1) / TC_BM;
@@ -491,25 +682,20 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
     }
     CUtensorMap ma, mb;
     GVT_CHECK(make_map(&ma, A, M, K, lda, TC_BM, f16));
-    GVT_CHECK(make_map(&mb, B, N, K, ldb, BN, f16));
+    GVT_CHECK(make_map(&mb, B, N, K, ldb, pair ? BN / 2 : BN, f16));
     const float* rs = row_scale;
     const float* cs = col_scale;
-    if (f16) {
-        if (BN == 64) return launch_tc<64, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-        if (BN == 128) return launch_tc<128, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-        if (BN == 224) return launch_tc<224, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-        return launch_tc<256, true>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    }
-    if (BN == 64) return launch_tc<64, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    if (BN == 128) return launch_tc<128, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    if (BN == 224) return launch_tc<224, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    return launch_tc<256, false>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    if (f16)
+        return pair ? launch_tc_bn<true, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s)
+                    : launch_tc_bn<true, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    return pair ? launch_tc_bn<false, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s)
+                : launch_tc_bn<false, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s);
 }
 
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
-                        int64_t N, int64_t K, int* err, cudaStream_t s)
+                        int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode)
 {
-    return tc_gemm(A, lda, B, ldb, C, ldc, M, N, K, false, nullptr, nullptr, err, s);
+    return tc_gemm(A, lda, B, ldb, C, ldc, M, N, K, false, nullptr, nullptr, err, s, pair_mode);
 }
 
 }  // namespace gvt

@@ -29,6 +29,7 @@ GVT_FACTOR_M, GVT_FACTOR_N, GVT_FACTOR_M_SQ, GVT_FACTOR_N_SQ, GVT_FACTOR_ONES, G
 GVT_FIRST, GVT_SECOND = 0, 1
 GVT_SOLVE_FP64_CG, GVT_SOLVE_MIXED_IR = 0, 1
 GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3, GVT_STAGES_TC_F16X3, GVT_STAGES_AUTO = 0, 1, 2, 3
+GVT_TC_PAIRS_AUTO, GVT_TC_PAIRS_OFF, GVT_TC_PAIRS_ON = 0, 1, 2
 GVT_MAX_TERMS = 16
 
 
@@ -113,6 +114,7 @@ SIGNATURES = [
     ("gvt_krr_cg_solve_batched", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, _P(gvt_solve_opts), c_vp,
                                          _P(gvt_solve_info), c_vp]),
     ("gvt_set_stage1_engine", c_i32, [c_vp, c_i32]),
+    ("gvt_set_tc_pairs", c_i32, [c_vp, c_i32]),
     ("gvt_precond_num_params", c_i64, []),
     ("gvt_precond_create", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
                                    _P(c_vp)]),
@@ -383,6 +385,10 @@ def cg_record_pairs(handle, plan, kind, M, N, y, lam, a_star, iters, symmetric=T
 
 def gvt_set_stage1_engine(h, engine):
     _call("gvt_set_stage1_engine", h, engine)
+
+
+def gvt_set_tc_pairs(h, mode):
+    _call("gvt_set_tc_pairs", h, mode)
 
 
 def gvt_check_device_errors(h, stream):

@@ -12,7 +12,9 @@
   homogeneous samples, training and cross-kernel prediction plans, against the
   FP64 oracle within the FP32 tolerance 1e-5;
 * a mixed-precision solve whose inner operator uses the tensor cores reaches
-  the FP64 relative residual 1e-6 checked by the oracle.
+  the FP64 relative residual 1e-6 checked by the oracle;
+* the GEMM's two tile forms (one SM per 128-row tile, an SM pair per 256-row
+  tile) on the raw GEMM and on the dense engine's products.
 """
 import numpy as np
 import pytest
@@ -38,10 +40,20 @@ def normwise(u, ref):
     return float(np.max(np.abs(u - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
 
+@pytest.fixture
+def pairs(H, request):
+    """Tile form of the tensor-core GEMM for one test; the handle goes back to the default after."""
+    gvt.gvt_set_tc_pairs(H.h, request.param)
+    yield request.param
+    gvt.gvt_set_tc_pairs(H.h, gvt.GVT_TC_PAIRS_AUTO)
+
+
+@pytest.mark.parametrize("pairs", [gvt.GVT_TC_PAIRS_OFF, gvt.GVT_TC_PAIRS_ON], indirect=True,
+                         ids=["one_sm", "sm_pair"])
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (129, 17, 64), (300, 250, 192), (2000, 250, 6144),
                                    (1000, 1000, 1024), (37, 300, 128), (4000, 100, 512), (640, 2000, 2048),
-                                   (2000, 1800, 512)])
-def test_tc_gemm_bf16(H, M, N, K):
+                                   (2000, 1800, 512), (2000, 2000, 6144)])
+def test_tc_gemm_bf16(H, pairs, M, N, K):
     g = torch.Generator(device=DEV).manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(M, K, generator=g, device=DEV).to(torch.bfloat16)
     B = torch.randn(N, K, generator=g, device=DEV).to(torch.bfloat16)
@@ -148,6 +160,39 @@ def test_f16x3_stages_meet_the_fp32_tolerance(H, engine, kind):
     err = normwise(u, ref)
     print("%s engine %d: error vs FP64 %.2e" % (kind, engine, err))
     assert err <= 1e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", ["kronecker", "symmetric", "mlpk"])
+def test_sm_pair_tiles_agree_with_single_sm_tiles(H, kind):
+    """The dense engine with 256-row SM-pair tiles and with 128-row one-SM tiles: both meet the FP32
+    tolerance against the FP64 oracle and agree with each other to FP32 rounding (ragged 430 x 430 or
+    430 x 150: two pairs, the second with a partly empty odd half)."""
+    rng = np.random.default_rng(21)
+    m, q, dim = 430, (430 if kind in gvt.HOMOGENEOUS else 150), 12
+    Xd = rng.standard_normal((m, dim))
+    Xt = Xd if kind in gvt.HOMOGENEOUS else rng.standard_normal((q, dim))
+    d, t = synth.random_pairs(rng, int(0.3 * m * q), m, q)
+    v = rng.standard_normal(len(d))
+    g = 1.0 / dim
+    M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=g, dtype=torch.float32)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=g, dtype=torch.float32)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t)
+    vv = torch.as_tensor(v, dtype=torch.float32, device=DEV)
+    ref = orc.pairwise_matvec(kind, orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g),
+                              d, t, d, t, vv.double().cpu().numpy())
+    out = {}
+    try:
+        for mode in (gvt.GVT_TC_PAIRS_OFF, gvt.GVT_TC_PAIRS_ON):
+            gvt.gvt_set_tc_pairs(H.h, mode)
+            out[mode] = _engine_product(H, gvt.GVT_STAGES_TC_F16X3, plan, kind, M, N, vv)
+    finally:
+        gvt.gvt_set_tc_pairs(H.h, gvt.GVT_TC_PAIRS_AUTO)
+    e1, e2 = normwise(out[gvt.GVT_TC_PAIRS_OFF], ref), normwise(out[gvt.GVT_TC_PAIRS_ON], ref)
+    diff = normwise(out[gvt.GVT_TC_PAIRS_ON], out[gvt.GVT_TC_PAIRS_OFF])
+    print("%s: one SM %.2e, SM pair %.2e, between them %.2e" % (kind, e1, e2, diff))
+    assert e1 <= 1e-5 and e2 <= 1e-5
+    assert diff <= 2e-6
     plan.close()
 
 
