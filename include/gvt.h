@@ -268,6 +268,23 @@ gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine);
 gvt_status gvt_check_device_errors(gvt_handle* h, void* stream);
 
 /*
+ * Keep split copies of kernel matrices across products.  Between
+ * gvt_factor_cache_begin and the matching gvt_factor_cache_end, the dense
+ * engines keep the 16-bit hi/lo split of each kernel matrix they read (up to
+ * four; the least recently used is replaced) in handle-owned device memory and
+ * reuse it in later products of this handle.  The key is the matrix pointer,
+ * leading dimension, extents and split format.  The caller guarantees that
+ * the contents of those matrices do not change until the scope ends, and that
+ * the products of the scope are ordered on the device (one stream, or events).
+ * Scopes nest.  When the outermost one ends, the copies are dropped; their
+ * memory is kept for reuse and freed by gvt_destroy.  The solvers open such a
+ * scope themselves for the duration of a solve.  gvt_factor_cache_end returns
+ * GVT_ERR_INVALID_ARG when no scope is open.  Host-only calls: no device work.
+ */
+gvt_status gvt_factor_cache_begin(gvt_handle* h);
+gvt_status gvt_factor_cache_end(gvt_handle* h);
+
+/*
  * Tile form of the tensor-core GEMM of the dense engines.  Both forms compute
  * the same chunked FP32 sums; they agree to FP32 rounding.
  *  GVT_TC_PAIRS_AUTO : the library's choice (default); currently one SM per

@@ -499,6 +499,27 @@ gvt_status gvt_tanimoto_kernel(gvt_handle* h, const uint32_t* X, int64_t rows_x,
     return tanimoto_kernel(X, rows_x, Y, rows_y, words, K, ldk, out_dtype, as_stream(stream));
 }
 
+gvt_status gvt_factor_cache_begin(gvt_handle* h)
+{
+    if (!h) {
+        set_error("gvt_factor_cache_begin: NULL handle");
+        return GVT_ERR_INVALID_ARG;
+    }
+    ++h->factor_cache_depth;
+    return GVT_OK;
+}
+
+gvt_status gvt_factor_cache_end(gvt_handle* h)
+{
+    if (!h || h->factor_cache_depth <= 0) {
+        set_error("gvt_factor_cache_end: NULL handle or no open scope");
+        return GVT_ERR_INVALID_ARG;
+    }
+    if (--h->factor_cache_depth == 0)
+        for (auto& e : h->factor_cache) e.valid = false;
+    return GVT_OK;
+}
+
 gvt_status gvt_set_tc_pairs(gvt_handle* h, int32_t mode)
 {
     if (!h || mode < GVT_TC_PAIRS_AUTO || mode > GVT_TC_PAIRS_ON) {

@@ -400,7 +400,13 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                          sz * Y * bcols + sz * Y * X + E * (8 + sz) + srcs.count * 4.0 * (X + 1));
             GVT_CHECK(stage1_dense<T>(B.Bt, B.ldbt, sq_mode(g.fb), srcs, v, S, lds, Y, X, s));
         }
-        // every group that reads this S (same B factor, out_b range and recipe)
+        // every group that reads this S (same B factor, out_b range and recipe); on the dense
+        // engine S is split once, and a group whose stage-2 GEMM equals the previous one (same
+        // A factor, square mode and rows: only the read-out positions differ) reuses its C
+        bool s_split = false;
+        const void* c_ptr = nullptr;
+        int c_sq = -1;
+        int64_t c_rows = -1;
         for (size_t gj = gi; gj < C.two.size(); ++gj) {
             const TwoSided& g2 = C.two[gj];
             if (done[gj] || g2.fb != g.fb || g2.recipe != g.recipe ||
@@ -419,13 +425,20 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 StatScope st(h, s, GVT_STAT_STAGE2, (sq_mode(g2.fa) ? 3.0 : 2.0) * X * n_out,
                              sz * ((double)mb * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
                 DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X);
-                GVT_CHECK(factor_operand(mats[base_matrix(g2.fa, homo)], sq_mode(g2.fa), mb, X, a2));
-                GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s));
+                const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
                 float* C2 = reinterpret_cast<float*>(base + off_c2);
-                {
+                if (!(c_ptr == Fa->data && c_sq == sq_mode(g2.fa) && c_rows == mb)) {
+                    GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2));
+                    if (!s_split) {
+                        GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s));
+                        s_split = true;
+                    }
                     StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * 3.0 * kp,
                                  2.0 * 3.0 * kp * (mb + Y) + 4.0 * mb * Y);
                     GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs));
+                    c_ptr = Fa->data;
+                    c_sq = sq_mode(g2.fa);
+                    c_rows = mb;
                 }
                 GVT_CHECK(dense_gather(C2, ldc2, outs, reinterpret_cast<float*>(u), s));
             } else {

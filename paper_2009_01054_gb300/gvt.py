@@ -115,6 +115,8 @@ SIGNATURES = [
                                          _P(gvt_solve_info), c_vp]),
     ("gvt_set_stage1_engine", c_i32, [c_vp, c_i32]),
     ("gvt_set_tc_pairs", c_i32, [c_vp, c_i32]),
+    ("gvt_factor_cache_begin", c_i32, [c_vp]),
+    ("gvt_factor_cache_end", c_i32, [c_vp]),
     ("gvt_precond_num_params", c_i64, []),
     ("gvt_precond_create", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
                                    _P(c_vp)]),
@@ -389,6 +391,14 @@ def gvt_set_stage1_engine(h, engine):
 
 def gvt_set_tc_pairs(h, mode):
     _call("gvt_set_tc_pairs", h, mode)
+
+
+def gvt_factor_cache_begin(h):
+    _call("gvt_factor_cache_begin", h)
+
+
+def gvt_factor_cache_end(h):
+    _call("gvt_factor_cache_end", h)
 
 
 def gvt_check_device_errors(h, stream):

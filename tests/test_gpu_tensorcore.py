@@ -329,3 +329,39 @@ def test_dense_engine_is_reproducible_without_split_k(H):
         gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     plan.close()
+
+
+def test_factor_cache_scope_reuses_splits_and_keys_by_matrix(H):
+    """Inside gvt_factor_cache_begin/end the dense engine reuses split copies of the kernel matrices
+    across products. At the benchmark shape (no K split) the products are bit-identical to those
+    made without the scope. A second matrix with another pointer, used inside the same scope, gets
+    its own split: its product matches the one made outside the scope. Ending a scope that is not
+    open is an argument error."""
+    p = synth.homogeneous(0)
+    X = torch.as_tensor(p.Xd, device=DEV)
+    M1 = gvt.gaussian_kernel(H, X, gamma=p.gamma, dtype=torch.float32)
+    M2 = gvt.gaussian_kernel(H, X, gamma=2 * p.gamma, dtype=torch.float32)
+    plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=DEV)
+    kinds = ["kronecker", "symmetric", "mlpk"]
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_TC_F16X3)
+    try:
+        ref = {(k, i): gvt.pairwise_kernel_matvec(plan, k, Mx, Mx, v).clone()
+               for k in kinds for i, Mx in enumerate((M1, M2))}
+        gvt.gvt_factor_cache_begin(H.h)
+        try:
+            got = {(k, i): gvt.pairwise_kernel_matvec(plan, k, Mx, Mx, v).clone()
+                   for k in kinds for i, Mx in enumerate((M1, M2))}
+            again = gvt.pairwise_kernel_matvec(plan, "mlpk", M1, M1, v).clone()
+        finally:
+            gvt.gvt_factor_cache_end(H.h)
+        gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    for key in ref:
+        assert torch.equal(ref[key], got[key]), key
+    assert torch.equal(again, ref[("mlpk", 0)])
+    assert not torch.equal(ref[("kronecker", 0)], ref[("kronecker", 1)])
+    with pytest.raises(gvt.GvtError):
+        gvt.gvt_factor_cache_end(H.h)
+    plan.close()
