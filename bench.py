@@ -498,7 +498,8 @@ def run_gvt(args, ws, rank, local):
                                              "K steps (the timed pass runs without them)",
                           "parallelism": "replicas: independent problems per rank (seed = rank)"},
                "roofline": roof, "stages": stage_summary, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clk, "gpu_launches": launches, "engine": args.engine, "engines": engines,
+               "clocks": clk, "gpu_launches": launches,
+               "engine": args.engine, "engines": engines,
                "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve,
                "batched": batched}
         print(json.dumps(out), flush=True)

@@ -1,6 +1,8 @@
 // C ABI entry points: handles, plans, descriptors and products.
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "gvt_internal.h"
@@ -46,6 +48,20 @@ gvt_status cuda_fail(cudaError_t e, const char* what)
 {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? GVT_ERR_ALLOC : GVT_ERR_CUDA;
+}
+
+gvt_status ensure_smem_attr(const void* func, int bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> raised;   // (kernel, device) -> limit set
+    int dev = 0;
+    GVT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    int& have = raised[{func, dev}];
+    if (have >= bytes) return GVT_OK;
+    GVT_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    have = bytes;
+    return GVT_OK;
 }
 
 gvt_status DevBuf::reserve(size_t nbytes, cudaStream_t s)

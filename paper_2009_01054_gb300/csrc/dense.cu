@@ -296,13 +296,9 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
     uint4* d = static_cast<uint4*>(dst.data);
     if (4 * kp <= kRowSmemMax) {
         const size_t smem = 4 * (size_t)kp;
-        if (smem > 48 * 1024) {   // per call: the attribute belongs to the current device's context
-            if (f16)
-                GVT_CUDA(cudaFuncSetAttribute(densify_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-            else
-                GVT_CUDA(cudaFuncSetAttribute(densify_split_kernel<false>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > 48 * 1024) {
+            if (f16) GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(densify_split_kernel<true>), (int)smem));
+            else GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(densify_split_kernel<false>), (int)smem));
         }
         if (f16) densify_split_kernel<true><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp);
         else densify_split_kernel<false><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp);

@@ -16,6 +16,9 @@ namespace gvt {
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 gvt_status cuda_fail(cudaError_t e, const char* what);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device; the
+// attribute persists, so each (kernel, device) pays the driver call once.
+gvt_status ensure_smem_attr(const void* func, int bytes);
 
 #define GVT_CUDA(call)                                                     \
     do {                                                                   \

@@ -619,7 +619,7 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     }
     const size_t smem = tc_smem_bytes<BN, PAIR>();
     auto kern = tc_gemm_kernel<BN, F16, PAIR>;
-    GVT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(kern), (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(gx, gy, splits);
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
