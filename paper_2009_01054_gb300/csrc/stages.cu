@@ -368,6 +368,71 @@ __global__ void gemv_rows_multi_kernel(const T* __restrict__ F, int64_t ldf, int
     }
 }
 
+// 16-byte vectors of T
+template <class T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int width = 4;
+    __device__ static void unpack(const float4& q, float (&o)[4])
+    {
+        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int width = 2;
+    __device__ static void unpack(const double2& q, double (&o)[2])
+    {
+        o[0] = q.x; o[1] = q.y;
+    }
+};
+
+// The same product with 16-byte loads, four in flight per lane: F and the s_g 16-byte aligned,
+// ldf and lds multiples of the vector width (the host checks).  Columns past the last whole
+// vector are read one element per lane.
+template <class T, int MODE, int G>
+__global__ void gemv_rows_multi_vec_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
+                                           const T* __restrict__ s, int64_t lds, T* __restrict__ z, int64_t ldz)
+{
+    using V = typename Vec16<T>::type;
+    constexpr int W = Vec16<T>::width;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t Xv = X / W * W;
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += nw) {
+        const T* row = F + r * ldf;
+        T acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = T(0);
+#pragma unroll 4
+        for (int64_t x = (int64_t)lane * W; x < Xv; x += 32 * W) {
+            T f[W];
+            Vec16<T>::unpack(__ldg(reinterpret_cast<const V*>(row + x)), f);
+#pragma unroll
+            for (int e = 0; e < W; ++e)
+                if (MODE == FM_SQUARE) f[e] *= f[e];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                T sv[W];
+                Vec16<T>::unpack(__ldg(reinterpret_cast<const V*>(s + g * lds + x)), sv);
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc[g] = fma(f[e], sv[e], acc[g]);
+            }
+        }
+        for (int64_t x = Xv + lane; x < X; x += 32) {
+            const T f = MODE == FM_SQUARE ? row[x] * row[x] : row[x];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = fma(f, s[g * lds + x], acc[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
+            if (lane == 0) z[g * ldz + r] = acc[g];
+        }
+    }
+}
+
 template <class T>
 struct GatherSet {
     const T* z[kMaxOneSidedShare];
@@ -626,8 +691,14 @@ gvt_status gemv_rows_multi(const T* F, int64_t ldf, int mode, int64_t R, int64_t
 {
     if (R <= 0 || count <= 0) return GVT_OK;
     const unsigned g = grid1d(R * 32, 256, 152 * 16);
+    constexpr int W = Vec16<T>::width;
+    const bool vec = ((uintptr_t)F & 15) == 0 && ((uintptr_t)svecs & 15) == 0 && ldf % W == 0 && lds % W == 0;
 #define GVT_GEMV_MULTI(G)                                                                                    \
-    if (mode == FM_SQUARE)                                                                                   \
+    if (vec && mode == FM_SQUARE)                                                                            \
+        gemv_rows_multi_vec_kernel<T, FM_SQUARE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);     \
+    else if (vec)                                                                                            \
+        gemv_rows_multi_vec_kernel<T, FM_DENSE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);      \
+    else if (mode == FM_SQUARE)                                                                              \
         gemv_rows_multi_kernel<T, FM_SQUARE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);         \
     else                                                                                                     \
         gemv_rows_multi_kernel<T, FM_DENSE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);
