@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=256)
+    ap.add_argument("--batched-sample", type=int, default=8,
+                    help="problems of the plain FP64 CG comparison run system by system (0: skip it)")
     return ap.parse_args()
 
 
@@ -474,7 +476,7 @@ def run_gvt(args, ws, rank, local):
         solve = bench_solve(H, gvt, torch, dev, [float(x) for x in args.solve_lambdas.split(",")])
     batched = None
     if not args.no_batched and rank == 0:
-        batched = bench_batched(H, gvt, torch, dev, args.batched_problems)
+        batched = bench_batched(H, gvt, torch, dev, args.batched_problems, args.batched_sample)
 
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -637,6 +639,7 @@ def bench_batched(H, gvt, torch, dev, n_probs, sample=8):
     # plain FP64 CG, one system at a time, on the first `sample` problems
     t0 = time.perf_counter()
     fp_iters, fp_worst, sample_pairs = 0, 0.0, 0
+    sample = max(0, sample)
     for b in range(min(sample, len(ps))):
         p = probs[b]
         plan = gvt.Plan(H, tuple(p["M"].shape), tuple(p["N"].shape), p["d"], p["t"])
@@ -657,9 +660,10 @@ def bench_batched(H, gvt, torch, dev, n_probs, sample=8):
             "plain_fp64_cg_sample": {"problems": min(sample, len(ps)), "systems": min(sample, len(ps)) * len(lambdas),
                                      "ms": fp_ms, "iterations": fp_iters, "max_rel_residual": fp_worst,
                                      "pairs": sample_pairs},
-            "plain_fp64_cg_estimate_ms": est_full,
+            "plain_fp64_cg_estimate_ms": est_full if sample_pairs else None,
             "estimate_note": "plain FP64 CG time for all systems scaled from the sample by pair count",
-            "speedup_vs_plain_fp64_cg_estimate": est_full / batched_ms, "data_generation_s": gen_s}
+            "speedup_vs_plain_fp64_cg_estimate": est_full / batched_ms if sample_pairs else None,
+            "data_generation_s": gen_s}
 
 
 def main():
