@@ -523,8 +523,9 @@ typedef struct gvt_problem {
  * several regularisation values at once: for every problem b and every
  * lambda_c, (R_b (M_b kron N_b) R_b^T + lambda_c I) a_bc = y_b.
  * One persistent launch per stage covers the whole batch; each loaded kernel
- * entry serves all lambda columns.  Inner CG in FP32 with FP64 dot products
- * and step lengths, one iteration captured as a CUDA graph; the outer loop
+ * entry serves all lambda columns.  Inner CG in FP32 (dot products summed in
+ * FP32 over 8 elements per thread, then in FP64; step lengths in FP64), one
+ * iteration captured as a CUDA graph; the outer loop
  * refines with FP64 residuals until every system reaches
  * ||y_b - (K_b + lambda_c I) a_bc|| / ||y_b|| <= opts->rel_tol.  The tile shape
  * of stage 1 is autotuned on the first call for a batch shape and cached in

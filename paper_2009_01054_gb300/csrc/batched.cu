@@ -9,8 +9,9 @@
 //   stage 2:  W[i, c]      = sum_x M_b[d_i, x] S_b[t_i, x, c]   (+ lambda_c V[i, c])
 // Both stages are persistent kernels that walk a work list of
 // (problem, tile) items sorted by cost, one launch for the whole batch.  The
-// FP32 CG iteration (operator, FP64 dot products, per-system step lengths,
-// updates) is captured once into a CUDA graph and replayed; the FP64 operator
+// FP32 CG iteration (operator, dot products summed in FP32 per thread and in
+// FP64 across threads, per-system FP64 step lengths, FP32 updates) is captured
+// once into a CUDA graph and replayed; the FP64 operator
 // gives the true residuals of an iterative-refinement loop around it.  The
 // stage tile shapes are chosen by timing the candidates on the first call.
 #include <algorithm>
@@ -255,6 +256,9 @@ __device__ double bsum_col(double x, double* sh, int kc)
     return r;
 }
 
+// Each thread sums its (at most kRows / (kBT / kc) = 8) products in T, the working precision
+// of the vectors (FP32 products on the GPU run at 64 times the FP64 rate), and the block adds the
+// threads' partial sums in FP64 in a fixed order.
 template <class T>
 __global__ void __launch_bounds__(kBT)
 b_dot_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs, const T* __restrict__ X,
@@ -264,25 +268,30 @@ b_dot_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs, c
     const int4 ch = chunks[blockIdx.x];
     const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    double acc = 0.0;
+    T acc = T(0);
+#pragma unroll 4
     for (int j = ch.y + jl; j < ch.z; j += nl) {
         const int64_t e = (base + j) * kc + c;
-        acc += (double)X[e] * (double)Y[e];
+        acc = fma(X[e], Y[e], acc);
     }
-    const double r = bsum_col(acc, sh, kc);
+    const double r = bsum_col((double)acc, sh, kc);
     if (threadIdx.x < kc) part[(int64_t)blockIdx.x * kc + threadIdx.x] = r;
 }
 
-// out[b * kc + c] = sum of part over problem b's chunks [cfirst[b], cfirst[b+1])
+// out[b * kc + c] = sum of part over problem b's chunks [cfirst[b], cfirst[b+1]): one warp per
+// system, lanes striding the chunks, then a shuffle tree (a fixed order)
 __global__ void b_sys_sum_kernel(const double* __restrict__ part, const int32_t* __restrict__ cfirst, int P, int kc,
                                  double* __restrict__ out)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (s >= P * kc) return;
     const int b = s / kc, c = s % kc;
     double acc = 0.0;
-    for (int q = cfirst[b]; q < cfirst[b + 1]; ++q) acc += part[(int64_t)q * kc + c];
-    out[s] = acc;
+    for (int q = cfirst[b] + lane; q < cfirst[b + 1]; q += 32) acc += part[(int64_t)q * kc + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) out[s] = acc;
 }
 
 // per-system scalars
@@ -341,16 +350,17 @@ b_update_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ probs
     const int4 ch = chunks[blockIdx.x];
     const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    const double alpha = sc[((int64_t)ch.x * kc + c) * B_N + B_ALPHA];
-    double acc = 0.0;
+    const T alpha = (T)sc[((int64_t)ch.x * kc + c) * B_N + B_ALPHA];
+    T acc = T(0);
+#pragma unroll 4
     for (int j = ch.y + jl; j < ch.z; j += nl) {
         const int64_t e = (base + j) * kc + c;
-        x[e] = (T)((double)x[e] + alpha * (double)p[e]);
-        const T ri = (T)((double)r[e] - alpha * (double)w[e]);
+        x[e] = fma(alpha, p[e], x[e]);
+        const T ri = fma(-alpha, w[e], r[e]);
         r[e] = ri;
-        acc += (double)ri * (double)ri;
+        acc = fma(ri, ri, acc);
     }
-    const double sres = bsum_col(acc, sh, kc);
+    const double sres = bsum_col((double)acc, sh, kc);
     if (threadIdx.x < kc) part[(int64_t)blockIdx.x * kc + threadIdx.x] = sres;
 }
 
@@ -363,10 +373,11 @@ b_pupdate_kernel(const int4* __restrict__ chunks, const BProb* __restrict__ prob
     const int4 ch = chunks[blockIdx.x];
     const int64_t base = probs[ch.x].n_off;
     const int c = threadIdx.x % kc, jl = threadIdx.x / kc, nl = kBT / kc;
-    const double beta = sc[((int64_t)ch.x * kc + c) * B_N + B_BETA];
+    const T beta = (T)sc[((int64_t)ch.x * kc + c) * B_N + B_BETA];
+#pragma unroll 4
     for (int j = ch.y + jl; j < ch.z; j += nl) {
         const int64_t e = (base + j) * kc + c;
-        p[e] = (T)((double)r[e] + beta * (double)p[e]);
+        p[e] = fma(beta, p[e], r[e]);
     }
 }
 
@@ -536,7 +547,8 @@ template <class T>
 void sys_dot(const Batch& B, const T* X, const T* Y, double* part, double* out, cudaStream_t s)
 {
     b_dot_kernel<T><<<B.nch, kBT, 0, s>>>(B.chunks, B.probs, X, Y, B.kc, part);
-    b_sys_sum_kernel<<<(B.P * B.kc + 255) / 256, 256, 0, s>>>(part, B.cfirst, B.P, B.kc, out);
+    b_sys_sum_kernel<<<(unsigned)(((int64_t)B.P * B.kc * 32 + 255) / 256), 256, 0, s>>>(part, B.cfirst, B.P, B.kc,
+                                                                                         out);
     count_launches(2);
 }
 
@@ -787,12 +799,13 @@ extern "C" gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem*
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     const unsigned sg = (unsigned)((nsys + 255) / 256);
+    const unsigned sgw = (unsigned)(((int64_t)nsys * 32 + 255) / 256);   // a warp per system
     auto record_iter = [&](cudaStream_t cs) -> gvt_status {
         GVT_CHECK(apply<float>(B, B.M32, B.N32, p32, S32, w32, lam, grid1, cs));
         sys_dot<float>(B, p32, w32, part, sysv, cs);
         b_alpha_kernel<<<sg, 256, 0, cs>>>(sysv, sc, nsys, flags);
         b_update_kernel<float><<<B.nch, kBT, 0, cs>>>(B.chunks, B.probs, c32, r32, p32, w32, sc, kc, part);
-        b_sys_sum_kernel<<<sg, 256, 0, cs>>>(part, B.cfirst, B.P, kc, sysv);
+        b_sys_sum_kernel<<<sgw, 256, 0, cs>>>(part, B.cfirst, B.P, kc, sysv);
         b_beta_kernel<<<sg, 256, 0, cs>>>(sysv, sc, nsys, flags + 1);
         b_pupdate_kernel<float><<<B.nch, kBT, 0, cs>>>(B.chunks, B.probs, p32, r32, sc, kc);
         GVT_LAUNCHED(5, "batched CG iteration");
