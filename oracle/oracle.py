@@ -151,6 +151,15 @@ def tanimoto_kernel(Xb, Yb=None):
     return K
 
 
+def linear_kernel(X, Y=None):
+    """Linear base kernel K[a,b] = <X_a, Y_b> (Sec. 5, the Metz data: rows of a similarity matrix
+    used as feature vectors).  A plain matrix product in FP64."""
+    X = _f64(X)
+    Y = X if Y is None else _f64(Y)
+    assert X.shape[1] == Y.shape[1]
+    return X @ Y.T
+
+
 def compensated_sum(x):
     x = _f64(x)
     return float(_load().orc_compensated_sum(_ptr(x), len(x)))

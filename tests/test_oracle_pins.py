@@ -366,6 +366,34 @@ def test_tanimoto_kernel_is_the_jaccard_index_and_psd():
     assert np.linalg.eigvalsh(K).min() >= -1e-12 * np.abs(K).max()
 
 
+def test_linear_kernel_on_similarity_rows():
+    """Linear base kernel of Sec. 5 (Metz: rows of a similarity matrix as features):
+    * entry by entry, a brute-force sum of products;
+    * on the rows of a symmetric similarity matrix S it is the matrix square S S;
+    * it ties to the Gaussian kernel through ||x - y||^2 = k(x, x) + k(y, y) - 2 k(x, y);
+    * the cross kernel of new rows against training rows is the matching block of the kernel of
+      the stacked rows;
+    * it is symmetric and positive semidefinite."""
+    rng = np.random.default_rng(33)
+    X = rng.standard_normal((9, 5))
+    K = orc.linear_kernel(X)
+    for a in range(9):
+        for b in range(9):
+            want = sum(float(X[a, i]) * float(X[b, i]) for i in range(5))
+            assert abs(K[a, b] - want) <= 1e-14 * max(1.0, abs(want))
+    A = rng.uniform(0.0, 1.0, (12, 12))
+    S = (A + A.T) / 2
+    np.fill_diagonal(S, 1.0)
+    np.testing.assert_allclose(orc.linear_kernel(S), np.linalg.matrix_power(S, 2), rtol=1e-13, atol=1e-13)
+    Y = rng.standard_normal((4, 5))
+    d2 = np.diag(K)[:, None] + np.sum(Y * Y, axis=1)[None, :] - 2 * orc.linear_kernel(X, Y)
+    np.testing.assert_allclose(np.exp(-0.3 * d2), orc.gaussian_kernel(X, Y, gamma=0.3), rtol=1e-12, atol=1e-14)
+    Kall = orc.linear_kernel(np.vstack([X, Y]))
+    np.testing.assert_allclose(orc.linear_kernel(Y, X), Kall[9:, :9], rtol=1e-14, atol=1e-14)
+    np.testing.assert_array_equal(K, K.T)
+    assert np.linalg.eigvalsh(K).min() >= -1e-12 * np.abs(K).max()
+
+
 def test_fingerprint_packing_round_trip():
     rng = np.random.default_rng(32)
     bits, packed = synth.fingerprints(rng, 9, 77, 0.4)
