@@ -223,6 +223,17 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x,
                                void* stream);
 
 /*
+ * Linear base kernel  K[a, b] = <X_a, Y_b>  (Sec. 5, the Metz data set: the rows
+ * of a drug or target similarity matrix serve as feature vectors), summed in
+ * FP64 and stored in out_dtype (GVT_F64, GVT_F32 or GVT_BF16).  X: rows_x x dim,
+ * Y: rows_y x dim, row-major FP64 device arrays; Y may equal X.  K: rows_x x
+ * rows_y, ld ldk >= rows_y.  GVT_ERR_INVALID_ARG on NULL or negative sizes.
+ */
+gvt_status gvt_linear_kernel(gvt_handle* h, const double* X, int64_t rows_x,
+                             const double* Y, int64_t rows_y, int64_t dim,
+                             void* K, int64_t ldk, int32_t out_dtype, void* stream);
+
+/*
  * Tanimoto (MinMax) base kernel of binary fingerprints (Sec. 5):
  *     K[a, b] = sum_i min(x_ai, y_bi) / sum_i max(x_ai, y_bi) = |x_a AND y_b| / |x_a OR y_b|,
  * with K[a, b] = 1 when both fingerprints are empty.  X: rows_x x words, Y: rows_y x

@@ -499,6 +499,21 @@ gvt_status gvt_gaussian_kernel(gvt_handle* h, const double* X, int64_t rows_x, c
     return gaussian_kernel(X, rows_x, Y, rows_y, dim, gamma, K, ldk, out_dtype, as_stream(stream));
 }
 
+gvt_status gvt_linear_kernel(gvt_handle* h, const double* X, int64_t rows_x, const double* Y, int64_t rows_y,
+                             int64_t dim, void* K, int64_t ldk, int32_t out_dtype, void* stream)
+{
+    if (!h || (rows_x > 0 && (!X || !K)) || (rows_y > 0 && !Y) || rows_x < 0 || rows_y < 0 || dim < 0 ||
+        ldk < rows_y) {
+        set_error("gvt_linear_kernel: bad argument");
+        return GVT_ERR_INVALID_ARG;
+    }
+    if ((rows_x + 31) / 32 > 65535) {
+        set_error("gvt_linear_kernel: too many rows");
+        return GVT_ERR_UNSUPPORTED;
+    }
+    return linear_kernel(X, rows_x, Y, rows_y, dim, K, ldk, out_dtype, as_stream(stream));
+}
+
 gvt_status gvt_tanimoto_kernel(gvt_handle* h, const uint32_t* X, int64_t rows_x, const uint32_t* Y,
                                int64_t rows_y, int64_t words, void* K, int64_t ldk, int32_t out_dtype,
                                void* stream)

@@ -250,6 +250,8 @@ gvt_status transpose(const T* B, int64_t ldb, int64_t rows, int64_t cols, T* Bt,
                      cudaStream_t s);
 
 gvt_status convert(const void* src, int sdt, void* dst, int ddt, int64_t n, cudaStream_t s);
+gvt_status linear_kernel(const double* X, int64_t rx, const double* Y, int64_t ry, int64_t dim, void* K,
+                         int64_t ldk, int dtype, cudaStream_t s);
 gvt_status tanimoto_kernel(const uint32_t* X, int64_t rx, const uint32_t* Y, int64_t ry, int64_t words, void* K,
                            int64_t ldk, int dtype, cudaStream_t s);
 gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t ry, int64_t dim,

@@ -541,6 +541,39 @@ __global__ void gaussian_kernel_kernel(const double* __restrict__ X, int64_t rx,
     }
 }
 
+// Linear kernel K[a, b] = <X_a, Y_b> (Sec. 5: rows of a similarity matrix as feature vectors),
+// FP64 sums over 32-wide feature tiles staged in shared memory; 32 x 32 output tile per block.
+template <class D>
+__global__ void linear_kernel_kernel(const double* __restrict__ X, int64_t rx, const double* __restrict__ Y,
+                                     int64_t ry, int64_t dim, D* __restrict__ K, int64_t ldk)
+{
+    __shared__ double xs[32][33];
+    __shared__ double ys[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int64_t a0 = (int64_t)blockIdx.y * 32, b0 = (int64_t)blockIdx.x * 32;
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t k0 = 0; k0 < dim; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t a = a0 + r, b = b0 + r, k = k0 + tx;
+            xs[r][tx] = (a < rx && k < dim) ? X[a * dim + k] : 0.0;
+            ys[r][tx] = (b < ry && k < dim) ? Y[b * dim + k] : 0.0;
+        }
+        __syncthreads();
+        const int kmax = (dim - k0 < 32) ? (int)(dim - k0) : 32;
+        for (int kk = 0; kk < kmax; ++kk) {
+            const double yv = ys[tx][kk];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(xs[ty + 8 * i][kk], yv, acc[i]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t a = a0 + ty + 8 * i, b = b0 + tx;
+        if (a < rx && b < ry) K[a * ldk + b] = cvt<double, D>(acc[i]);
+    }
+}
+
 // Tanimoto (MinMax) kernel of binary fingerprints, Sec. 5:
 //   K[a, b] = |x_a AND y_b| / |x_a OR y_b|   (popcounts over `words` 32-bit words)
 // with K = 1 when both fingerprints are empty.  32 x 32 output tile per block.
@@ -804,6 +837,30 @@ gvt_status gaussian_kernel(const double* X, int64_t rx, const double* Y, int64_t
         return GVT_ERR_INVALID_ARG;
     }
     GVT_LAUNCH_CHECK("gaussian_kernel");
+    return GVT_OK;
+}
+
+gvt_status linear_kernel(const double* X, int64_t rx, const double* Y, int64_t ry, int64_t dim, void* K,
+                         int64_t ldk, int dtype, cudaStream_t s)
+{
+    if (rx <= 0 || ry <= 0) return GVT_OK;
+    dim3 grid((unsigned)((ry + 31) / 32), (unsigned)((rx + 31) / 32));
+    dim3 block(32, 8);
+    switch (dtype) {
+    case GVT_F64:
+        linear_kernel_kernel<double><<<grid, block, 0, s>>>(X, rx, Y, ry, dim, (double*)K, ldk);
+        break;
+    case GVT_F32:
+        linear_kernel_kernel<float><<<grid, block, 0, s>>>(X, rx, Y, ry, dim, (float*)K, ldk);
+        break;
+    case GVT_BF16:
+        linear_kernel_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(X, rx, Y, ry, dim, (__nv_bfloat16*)K, ldk);
+        break;
+    default:
+        set_error("linear_kernel: bad dtype");
+        return GVT_ERR_INVALID_ARG;
+    }
+    GVT_LAUNCH_CHECK("linear_kernel");
     return GVT_OK;
 }
 

@@ -103,6 +103,7 @@ SIGNATURES = [
     ("gvt_stats_read", c_i32, [c_vp, c_vp]),
     ("gvt_launch_count", c_i64, []),
     ("gvt_tanimoto_kernel", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_i64, c_i32, c_vp]),
+    ("gvt_linear_kernel", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_i64, c_i32, c_vp]),
     ("gvt_krr_cg_solve_multishift", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
                                             c_i32, c_vp, c_dbl, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_klr_newton_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl, c_vp,
@@ -555,6 +556,17 @@ def gaussian_kernel(handle, X, Y=None, gamma=1.0, dtype=None, stream=None):
     out = torch.empty((X.shape[0], Y.shape[0]), dtype=dtype or torch.float64, device=X.device)
     gvt_gaussian_kernel(handle.h, ptr(X), X.shape[0], ptr(Y), Y.shape[0], X.shape[1], float(gamma),
                         ptr(out), out.stride(0), dtype_code(out), stream_ptr(stream))
+    return out
+
+
+def linear_kernel(handle, X, Y=None, dtype=None, stream=None):
+    """Linear base kernel <X_a, Y_b> (rows of a similarity matrix as features), summed in FP64."""
+    torch = _torch()
+    X = X.to(torch.float64).contiguous()
+    Y = X if Y is None else Y.to(torch.float64).contiguous()
+    out = torch.empty((X.shape[0], Y.shape[0]), dtype=dtype or torch.float64, device=X.device)
+    _call("gvt_linear_kernel", handle.h, ptr(X), X.shape[0], ptr(Y), Y.shape[0], X.shape[1], ptr(out),
+          out.stride(0), dtype_code(out), stream_ptr(stream))
     return out
 
 

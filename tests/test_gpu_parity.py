@@ -339,3 +339,37 @@ def test_tanimoto_base_kernel_and_product(H):
     u = run(H, "kronecker", Mt, N, d, t, v, do, to)
     ref = orc.pairwise_matvec("kronecker", Mo, No, do, to, d, t, v)
     assert normwise(u, ref) <= 1e-10
+
+
+def test_linear_base_kernel_on_similarity_rows_and_product(H):
+    """Linear kernel on the rows of a symmetric similarity matrix (Sec. 5, Metz) against the oracle:
+    FP64 within 1e-13 of max |K| (the GPU sums in another order), FP32 and BF16 the rounded values;
+    ragged (131 rows, 131-d) and rectangular (new rows against training rows); then a Kronecker
+    product with a linear drug kernel and a linear target kernel against the oracle."""
+    rng = np.random.default_rng(43)
+    A = rng.uniform(0.0, 1.0, (131, 131))
+    Sd = (A + A.T) / 2
+    np.fill_diagonal(Sd, 1.0)
+    X = torch.as_tensor(Sd, device=DEV)
+    K = gvt.linear_kernel(H, X).cpu().numpy()
+    Ko = orc.linear_kernel(Sd)
+    assert np.max(np.abs(K - Ko)) <= 1e-13 * np.max(np.abs(Ko))
+    Xn = rng.uniform(0.0, 1.0, (37, 131))
+    Kx = gvt.linear_kernel(H, torch.as_tensor(Xn, device=DEV), X).cpu().numpy()
+    Kxo = orc.linear_kernel(Xn, Sd)
+    assert Kx.shape == (37, 131) and np.max(np.abs(Kx - Kxo)) <= 1e-13 * np.max(np.abs(Kxo))
+    K32 = gvt.linear_kernel(H, X, dtype=torch.float32).cpu().numpy()
+    assert np.max(np.abs(K32 - Ko) / np.abs(Ko)) <= 2 ** -24 * 1.0001   # one rounding of the FP64 sum
+    K16 = gvt.linear_kernel(H, X, dtype=torch.bfloat16).float().cpu().numpy()
+    assert np.max(np.abs(K16 - Ko) / np.abs(Ko)) <= 2 ** -8 * 1.0001
+    B = rng.uniform(0.0, 1.0, (45, 45))
+    St = (B + B.T) / 2
+    Mg = gvt.linear_kernel(H, X)
+    Ng = gvt.linear_kernel(H, torch.as_tensor(St, device=DEV))
+    d, t = synth.random_pairs(rng, 2500, 131, 45)
+    v = rng.standard_normal(2500)
+    u = run(H, "kronecker", Mg, Ng, d, t, v, d, t)
+    ref = orc.pairwise_matvec("kronecker", Ko, orc.linear_kernel(St), d, t, d, t, v)
+    assert normwise(u, ref) <= 1e-10
+    E = gvt.linear_kernel(H, X[:0], X)
+    assert E.shape == (0, 131)
