@@ -151,6 +151,27 @@ def tanimoto_kernel(Xb, Yb=None):
     return K
 
 
+def auc(scores, labels):
+    """Area under the ROC curve, the paper's evaluation measure (Sec. 6): the fraction of
+    (positive, negative) pairs whose positive scores higher, ties counting one half.  Computed
+    from average ranks (the Mann-Whitney statistic)."""
+    s = np.asarray(scores, dtype=np.float64)
+    yb = np.asarray(labels).astype(bool)
+    n_pos, n_neg = int(yb.sum()), int((~yb).sum())
+    assert n_pos > 0 and n_neg > 0
+    order = np.argsort(s, kind="mergesort")
+    ranks = np.empty(len(s))
+    ss = s[order]
+    i = 0
+    while i < len(s):          # average rank (1-based) over each run of equal scores
+        j = i
+        while j + 1 < len(s) and ss[j + 1] == ss[i]:
+            j += 1
+        ranks[order[i:j + 1]] = 0.5 * (i + j) + 1.0
+        i = j + 1
+    return float((ranks[yb].sum() - n_pos * (n_pos + 1) / 2.0) / (n_pos * n_neg))
+
+
 def linear_kernel(X, Y=None):
     """Linear base kernel K[a,b] = <X_a, Y_b> (Sec. 5, the Metz data: rows of a similarity matrix
     used as feature vectors).  A plain matrix product in FP64."""

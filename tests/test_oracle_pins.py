@@ -394,6 +394,23 @@ def test_linear_kernel_on_similarity_rows():
     assert np.linalg.eigvalsh(K).min() >= -1e-12 * np.abs(K).max()
 
 
+def test_auc_is_the_pairwise_ranking_probability():
+    """AUC (the paper's measure): equal to the brute-force fraction of correctly ordered
+    (positive, negative) pairs with ties counting 1/2; 1 for a perfect ranking, 0 for the
+    reversed one, 1/2 when every score ties; unchanged by a strictly increasing transform."""
+    rng = np.random.default_rng(34)
+    s = np.round(rng.standard_normal(60), 1)          # rounding creates ties
+    y = rng.random(60) < 0.3
+    pos, neg = s[y], s[~y]
+    want = sum((p > q) + 0.5 * (p == q) for p in pos for q in neg) / (len(pos) * len(neg))
+    assert abs(orc.auc(s, y) - want) <= 1e-15
+    lab = np.array([0, 0, 1, 1, 0, 1])
+    sc = np.array([0.1, 0.2, 0.8, 0.9, 0.3, 0.7])
+    assert orc.auc(sc, lab) == 1.0 and orc.auc(-sc, lab) == 0.0
+    assert orc.auc(np.zeros(6), lab) == 0.5
+    assert abs(orc.auc(np.exp(3 * s) + 2, y) - orc.auc(s, y)) <= 1e-15
+
+
 def test_fingerprint_packing_round_trip():
     rng = np.random.default_rng(32)
     bits, packed = synth.fingerprints(rng, 9, 77, 0.4)
