@@ -425,6 +425,27 @@ gvt_status gvt_klr_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* d
                                 void* stream);
 
 /*
+ * Support vector machine with the squared hinge loss and a pairwise kernel (Sec. 7 names
+ * support vector machines among the kernel methods the product speeds up), trained in the
+ * primal by Newton's method over active sets (Chapelle 2007):
+ *     J(a) = lambda a^T K a + sum_i max(0, 1 - y_i f_i)^2,   f = K a,  y_i = +-1.
+ * With S = {i : y_i f_i < 1}, each Newton point solves (K_SS + lambda I) a_S = y_S with a = 0
+ * outside S: kernel ridge regression (Eq. 1) on the active pairs, by FP64 CG to relative
+ * residual cg_tol (at most max_cg_iter iterations) on a plan of those pairs.  A backtracking
+ * line search halves the step toward it until J does not increase.  Stops when a full step
+ * leaves S unchanged (the optimum) or after newton_iters steps.  FP64 products; M, N FP64 and
+ * symmetric; a training plan.  y, a: device FP64 (a out; starts from zero).  info (may be
+ * NULL): refinements = Newton steps, iterations = CG iterations in total, rel_residual =
+ * ||lambda a + [y f < 1](f - y)|| / ||y|| (the gradient of J is 2 K times that vector).
+ * Returns GVT_ERR_NOT_CONVERGED when newton_iters (or an inner max_cg_iter) ends the run,
+ * with a holding the last iterate.
+ */
+gvt_status gvt_svm_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
+                                const gvt_matrix* M, const gvt_matrix* N, const double* y,
+                                double lambda, double* a, int32_t newton_iters, double cg_tol,
+                                int64_t max_cg_iter, gvt_solve_info* info, void* stream);
+
+/*
  * MINRES on the same system (the solver of Sec. 6, which stops it early):
  * Lanczos on K + lambda I from y with Givens rotations, so that the k-th iterate
  * minimises ||y - (K + lambda I) a|| over span{y, A y, ..., A^{k-1} y}.  One FP64

@@ -108,6 +108,8 @@ SIGNATURES = [
                                             c_i32, c_vp, c_dbl, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_klr_newton_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl, c_vp,
                                      c_i32, c_dbl, c_dbl, c_i64, _P(gvt_solve_info), c_vp]),
+    ("gvt_svm_newton_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl, c_vp,
+                                     c_i32, c_dbl, c_i64, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_minres_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
                                      c_vp, c_dbl, c_i64, c_i64, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
@@ -612,6 +614,21 @@ def klr_newton_solve(handle, plan, kind, M, N, y, lam, newton_iters=30, cg_tol=1
                                      int(max_cg_iter), ctypes.byref(info), stream_ptr(stream))
     if st not in (GVT_OK, 6, 7):
         raise GvtError(st, "gvt_klr_newton_solve", last_error())
+    return a, st, info
+
+
+def svm_newton_solve(handle, plan, kind, M, N, y, lam, newton_iters=50, cg_tol=1e-12, max_cg_iter=100000,
+                     symmetric=True, stream=None):
+    """Squared-hinge SVM (labels +-1) by Newton's method over active sets; returns (a, status, info)."""
+    torch = _torch()
+    a = torch.zeros_like(y)
+    info = gvt_solve_info()
+    st = load().gvt_svm_newton_solve(handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
+                                     ctypes.byref(matrix(N, symmetric)) if N is not None else None, ptr(y),
+                                     float(lam), ptr(a), int(newton_iters), float(cg_tol), int(max_cg_iter),
+                                     ctypes.byref(info), stream_ptr(stream))
+    if st not in (GVT_OK, GVT_ERR_BREAKDOWN, GVT_ERR_NOT_CONVERGED):
+        raise GvtError(st, "gvt_svm_newton_solve", last_error())
     return a, st, info
 
 
