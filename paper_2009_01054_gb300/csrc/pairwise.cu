@@ -45,14 +45,15 @@ struct Compiled {
 
 // Engine choice of GVT_STAGES_AUTO for one stage: the dense FP16x3 GEMM (rows x cols
 // outputs, inner length K) against the sparse SIMT stage doing simt_flops useful flops.
-// Rates measured on GB300 at the homogeneous m = q = 2000 workload: SIMT stages about
-// 4.5e12 useful flop/s, the split GEMM about 1.2e15 flop/s, the split and densify passes
-// about 3e12 B/s, and about 15 us of fixed cost per dense stage.
+// Rates measured on GB300 at m = q = 2000 over pair densities 0.2 % to 20 %: SIMT stages about
+// 4.5e12 useful flop/s, the split GEMM about 1.2e15 flop/s, the split and densify passes about
+// 4e12 B/s, and about 8 us of fixed cost per dense stage (a dense stage measured 66 us there,
+// the SIMT stage 74 us at 2 % density; for one Kronecker term the model switches at 1.8 %).
 bool dense_pays(int64_t rows, int64_t cols, int64_t K, double simt_flops)
 {
     const double kp = (double)dense_kp(K);
     const double t_dense = 6.0 * rows * cols * kp / 1.2e15 +
-                           (6.0 * (double)(rows + cols) * kp + 4.0 * (double)rows * cols) / 3e12 + 15e-6;
+                           (6.0 * (double)(rows + cols) * kp + 4.0 * (double)rows * cols) / 4e12 + 8e-6;
     return t_dense < simt_flops / 4.5e12;
 }
 
