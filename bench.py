@@ -579,7 +579,7 @@ def bench_solve(H, gvt, torch, dev, lambdas):
             gvt.gvt_set_stage1_engine(H.h, engine)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=10,
+            a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=2,
                                            max_iter=20000, inner_dtype=inner)
             torch.cuda.synchronize()
             wall = (time.perf_counter() - t0) * 1e3
@@ -645,7 +645,7 @@ def bench_batched(H, gvt, torch, dev, n_probs, sample=8):
         plan = gvt.Plan(H, tuple(p["M"].shape), tuple(p["N"].shape), p["d"], p["t"])
         for lam in lambdas:
             a, st2, inf2 = gvt.krr_cg_solve(H, plan, "kronecker", p["M"], p["N"], p["y"], lam, max_iter=50000,
-                                            check_every=10)
+                                            check_every=2)
             fp_iters += inf2.iterations
             fp_worst = max(fp_worst, inf2.rel_residual)
         sample_pairs += ps[b].n

@@ -343,7 +343,10 @@ typedef struct gvt_solve_opts {
                                 GVT_BF16 (FP32 CG with the GVT_STAGE1_TC_BF16X3 stage 1) */
     double inner_tol;        /* MIXED_IR inner relative tolerance (default 1e-3) */
     int32_t max_refine;      /* MIXED_IR outer steps (default 30) */
-    int32_t check_every;     /* CG iterations between host convergence checks (default 1) */
+    int32_t check_every;     /* CG iterations between convergence checks (default 1).  The host
+                                reads each check one check late, without stalling the GPU, so a
+                                run may go up to check_every iterations past the one that met
+                                the tolerance (they continue the same CG) */
     int32_t precond_budget;  /* flexible-CG iterations allowed (per inner solve in MIXED_IR) before
                                 the solve falls back to plain CG from the current iterate;
                                 0 (default): max_iter / 2 */

@@ -73,9 +73,9 @@ finalize_kernel(const double* __restrict__ part, int nb, double* __restrict__ sc
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
     acc = block_sum(acc);
     if (threadIdx.x != 0) return;
-    if (what == 0) {            // alpha = rr / pw
+    if (what == 0) {            // alpha = rr / pw; after a breakdown the iteration stays frozen
         sc[SC_PW] = acc;
-        if (!(acc > 0.0) || !isfinite(acc)) {
+        if (sc[SC_FLAG] != 0.0 || !(acc > 0.0) || !isfinite(acc)) {
             sc[SC_FLAG] = 1.0;
             sc[SC_ALPHA] = 0.0;
         } else {
@@ -95,9 +95,9 @@ finalize_kernel(const double* __restrict__ part, int nb, double* __restrict__ sc
     } else if (what == 4) {     // flexible CG start: rz = r.z
         sc[SC_RZ] = acc;
         if (!isfinite(acc) || !(acc > 0.0)) sc[SC_FLAG] = 1.0;
-    } else if (what == 5) {     // flexible CG: alpha = rz / pw
+    } else if (what == 5) {     // flexible CG: alpha = rz / pw (frozen after a breakdown)
         sc[SC_PW] = acc;
-        if (!(acc > 0.0) || !isfinite(acc)) {
+        if (sc[SC_FLAG] != 0.0 || !(acc > 0.0) || !isfinite(acc)) {
             sc[SC_FLAG] = 1.0;
             sc[SC_ALPHA] = 0.0;
         } else {
@@ -222,6 +222,33 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
         GVT_LAUNCH_CHECK("cg init");
     }
     if (check_every < 1) check_every = 1;
+    // The convergence checks lag one check behind, so that the GPU never idles waiting for the
+    // host: each check copies the scalars asynchronously into one of two pinned slots and records
+    // an event; the host reads a check only after the next check's iterations are queued.  At most
+    // check_every iterations run past the one that met the tolerance (a breakdown in them leaves
+    // x unchanged: alpha is set to zero).
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard()
+        {
+            for (int i = 0; i < 2; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } ev_guard{ev};
+    for (auto& e : ev) GVT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    double* ring[2] = {hsc + 16, hsc + 32};   // SC_COUNT doubles each, clear of hsc[0, SC_COUNT)
+    int pending = -1, next_slot = 0;
+    // 1 = stop with GVT_OK, 2 = stop with a breakdown, 0 = go on
+    auto read_check = [&](int slot) -> int {
+        const double* h = ring[slot];
+        if (h[SC_FLAG] != 0.0) {
+            *rel = std::sqrt(std::fabs(h[SC_RR])) / bnorm;
+            return 2;
+        }
+        *rel = std::sqrt(h[SC_RR]) / bnorm;
+        return *rel <= tol ? 1 : 0;
+    };
     int64_t it = 0;
     while (it < max_iter) {
         GVT_CHECK(pairwise_apply<T>(plan, desc, M, N, p, w, s));
@@ -247,19 +274,47 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
         }
         ++it;
         if (it % check_every == 0 || it == max_iter) {
-            GVT_CUDA(cudaMemcpyAsync(hsc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-            GVT_CUDA(cudaStreamSynchronize(s));
-            *iters = it;
-            if (hsc[SC_FLAG] != 0.0) {
-                *rel = std::sqrt(std::fabs(hsc[SC_RR])) / bnorm;
-                set_error("CG breakdown: p^T (K + lambda I) p <= 0 or not finite");
-                return GVT_ERR_BREAKDOWN;
+            const int slot = next_slot;
+            next_slot ^= 1;
+            GVT_CUDA(cudaMemcpyAsync(ring[slot], sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+            GVT_CUDA(cudaEventRecord(ev[slot], s));
+            if (pending >= 0) {
+                GVT_CUDA(cudaEventSynchronize(ev[pending]));
+                const int verdict = read_check(pending);
+                pending = -1;
+                if (verdict == 2) {
+                    GVT_CUDA(cudaStreamSynchronize(s));
+                    *iters = it;
+                    set_error("CG breakdown: p^T (K + lambda I) p <= 0 or not finite");
+                    return GVT_ERR_BREAKDOWN;
+                }
+                if (verdict == 1) {
+                    // the returned x is the latest iterate: accept it if it meets the tolerance too
+                    // (a breakdown after convergence left x as it was); CG residuals need not
+                    // decrease monotonically, so otherwise iterate on
+                    GVT_CUDA(cudaStreamSynchronize(s));
+                    const double kept = *rel;
+                    const int latest = read_check(slot);
+                    if (latest != 0) {
+                        if (latest == 2) *rel = kept;
+                        *iters = it;
+                        return GVT_OK;
+                    }
+                }
             }
-            *rel = std::sqrt(hsc[SC_RR]) / bnorm;
-            if (*rel <= tol) return GVT_OK;
+            pending = slot;
         }
     }
     *iters = it;
+    if (pending >= 0) {
+        GVT_CUDA(cudaEventSynchronize(ev[pending]));
+        const int verdict = read_check(pending);
+        if (verdict == 2) {
+            set_error("CG breakdown: p^T (K + lambda I) p <= 0 or not finite");
+            return GVT_ERR_BREAKDOWN;
+        }
+        if (verdict == 1) return GVT_OK;
+    }
     return GVT_ERR_NOT_CONVERGED;
 }
 
