@@ -205,8 +205,9 @@ gvt_status gvt_svm_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* d
     for (;; ++it) {
         sv_flags<<<g, 256, 0, s>>>(f, y, n, flag);
         GVT_LAUNCHED(1, "svm active set");
-        GVT_CUDA(cudaMemcpyAsync(S.data(), flag, (size_t)n, cudaMemcpyDeviceToHost, s));
-        GVT_CUDA(cudaStreamSynchronize(s));
+        if (cudaMemcpyAsync(S.data(), flag, (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return ret(cuda_fail(cudaGetLastError(), "svm active set"));
         if (!S_prev.empty() && full_prev && S == S_prev) {
             converged = true;
             break;
@@ -219,7 +220,8 @@ gvt_status gvt_svm_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* d
         sv_zero<<<g, 256, 0, s>>>(ap, n);
         GVT_LAUNCHED(1, "svm newton point");
         if (ns > 0) {
-            GVT_CUDA(cudaMemcpyAsync(idx, hidx.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, s));
+            if (cudaMemcpyAsync(idx, hidx.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return ret(cuda_fail(cudaGetLastError(), "svm active pairs"));
             sv_gather<<<sv_grid(ns), 256, 0, s>>>(idx, ns, plan->d_in, plan->t_in, y, dS, tS, yS, bS);
             GVT_LAUNCHED(1, "svm active pairs");
             // the Newton point: kernel ridge regression on the active pairs
