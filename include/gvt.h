@@ -14,7 +14,7 @@
  * gathers u_i = <M[dhat_i, :], S[that_i, :]>.  Every pairwise kernel of
  * Table 4b is a sum of such Kronecker terms with permuted index sequences
  * (Corollary 1); the kernel ridge regression system (K + lambda I) a = y
- * (Eq. linsystem, Eq. 1) is solved with conjugate gradients on top.
+ * (Eq. 1) is solved with conjugate gradients on top.
  *
  * Conventions shared by every entry point:
  *  - Every data pointer is DEVICE memory owned by the caller unless stated;
@@ -371,7 +371,7 @@ typedef struct gvt_precond gvt_precond;
 gvt_status gvt_solve_opts_default(gvt_solve_opts* o);
 
 /*
- * Kernel ridge regression (Eq. linsystem / Eq. 1): solve
+ * Kernel ridge regression (Eq. 1): solve
  *     (R K_desc R^T + lambda I) a = y
  * over the plan's input pairs (the plan must be a training plan: output
  * pairs = input pairs).  M, N: FP64 kernel matrices.  y: n FP64.
@@ -554,7 +554,7 @@ typedef struct gvt_problem {
 } gvt_problem;
 
 /*
- * Kernel ridge regression (Eq. linsystem) for many independent problems and
+ * Kernel ridge regression (Eq. 1) for many independent problems and
  * several regularisation values at once: for every problem b and every
  * lambda_c, (R_b (M_b kron N_b) R_b^T + lambda_c I) a_bc = y_b.
  * One persistent launch per stage covers the whole batch; each loaded kernel

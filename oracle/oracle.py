@@ -10,7 +10,7 @@ Contents (each function cites the passage it follows):
   * Gaussian base kernel (C), Sec. 5.2 with the squared norm;
   * explicit operators of Definition 1 (commutation P, unification Q, PQ) and
     the sampling operator R of Sec. 3, as dense 0/1 matrices;
-  * kernel ridge regression, Eq. (linsystem): dense Cholesky solve and plain CG;
+  * kernel ridge regression, Eq. 1: dense Cholesky solve and plain CG;
   * the complete-data closed form through eigendecompositions (Sec. 1).
 
 Every function here is pinned by ``tests/test_oracle_pins.py`` against values
@@ -218,7 +218,7 @@ def sampling_R(d, t, nD, nT):
 
 
 # --------------------------------------------------------------------------
-# Kernel ridge regression, Eq. (linsystem): (K + lambda I) a = y.
+# Kernel ridge regression, Eq. 1: (K + lambda I) a = y.
 # --------------------------------------------------------------------------
 
 def krr_solve_dense(K, y, lam):

@@ -1,5 +1,5 @@
 // Batched kernel ridge regression: many independent problems, each with
-// several regularisation values lambda_c, solved together (Eq. linsystem for
+// several regularisation values lambda_c, solved together (Eq. 1 for
 // every (problem, lambda) system).
 //
 // All problems live in packed device buffers.  The Kronecker operator of

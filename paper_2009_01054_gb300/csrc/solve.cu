@@ -1,4 +1,4 @@
-// Kernel ridge regression (Eq. linsystem / Eq. 1) by conjugate gradients on
+// Kernel ridge regression (Eq. 1) by conjugate gradients on
 // top of the GVT products: plain FP64 CG, and mixed-precision iterative
 // refinement (FP64 residual and correction, FP32 operator and vectors inside,
 // FP64 dot products and step lengths everywhere).
