@@ -17,6 +17,7 @@ c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, cty
 
 # ---------------------------------------------------------------- enums (gvt.h)
 GVT_OK = 0
+GVT_ERR_INVALID_ARG, GVT_ERR_INDEX_OOB, GVT_ERR_UNSUPPORTED, GVT_ERR_ALLOC, GVT_ERR_CUDA = 1, 2, 3, 4, 5
 GVT_ERR_BREAKDOWN, GVT_ERR_NOT_CONVERGED, GVT_ERR_TIMEOUT = 6, 7, 8
 STATUS_NAMES = {0: "GVT_OK", 1: "GVT_ERR_INVALID_ARG", 2: "GVT_ERR_INDEX_OOB",
                 3: "GVT_ERR_UNSUPPORTED", 4: "GVT_ERR_ALLOC", 5: "GVT_ERR_CUDA",

@@ -142,6 +142,25 @@ def test_argument_errors_return_status_and_message(lib):
     assert lib.gvt_destroy(None) == 0 and lib.gvt_plan_destroy(None) == 0
 
 
+def test_null_handle_arguments_are_rejected_without_device_work(lib):
+    """Entry points added for engine control, the factor cache, the base kernels and the other
+    losses check their arguments before touching the device: a NULL handle or plan is
+    GVT_ERR_INVALID_ARG with a message, on a machine without a GPU."""
+    for mode in (0, 1, 2, 3, -1):
+        assert lib.gvt_set_tc_pairs(None, mode) == gvt.GVT_ERR_INVALID_ARG
+    assert "gvt_set_tc_pairs" in gvt.last_error()
+    assert lib.gvt_factor_cache_begin(None) == gvt.GVT_ERR_INVALID_ARG
+    assert lib.gvt_factor_cache_end(None) == gvt.GVT_ERR_INVALID_ARG
+    assert "gvt_factor_cache_end" in gvt.last_error()
+    assert lib.gvt_linear_kernel(None, None, 4, None, 4, 3, None, 4, gvt.GVT_F64, None) == gvt.GVT_ERR_INVALID_ARG
+    assert "gvt_linear_kernel" in gvt.last_error()
+    info = gvt.gvt_solve_info()
+    st = lib.gvt_svm_newton_solve(None, None, None, None, None, None, 0.1, None, 10, 1e-10, 100,
+                                  ctypes.byref(info), None)
+    assert st == gvt.GVT_ERR_INVALID_ARG and info.status == gvt.GVT_ERR_INVALID_ARG
+    assert "gvt_svm_newton_solve" in gvt.last_error()
+
+
 def test_solve_defaults(lib):
     o = gvt.gvt_solve_opts_default()
     assert o.rel_tol == 1e-6 and o.mode == gvt.GVT_SOLVE_FP64_CG and o.inner_tol == 1e-3
