@@ -420,6 +420,28 @@ def svm_newton(matvec, y, lam, newton_iters=50, cg_tol=1e-12):
     return a, newton_iters, cg_total, False
 
 
+def hinge_svm_objective(f, a, y, lam):
+    """J = (lam / 2) a^T f + (1 / n) sum_i max(0, 1 - y_i f_i) with f = K a: the hinge-loss SVM in
+    the coefficients of the representer theorem."""
+    return float(0.5 * lam * float(a @ f) + np.mean(np.maximum(0.0, 1.0 - y * f)))
+
+
+def hinge_svm_subgradient(matvec, y, lam, iters):
+    """Hinge-loss SVM by the stochastic-free kernelised sub-gradient method of Pegasos
+    (Shalev-Shwartz et al., 2011): with step 1 / (lam t), the sub-gradient step in the RKHS is
+        a <- (1 - 1/t) a + (1 / (lam t n)) y * [y f < 1],   f = K a,   t = 1, 2, ...
+    Returns (a, f, the objective at the returned a)."""
+    y = np.asarray(y, dtype=np.float64)
+    n = len(y)
+    a = np.zeros(n)
+    f = np.zeros(n)
+    for t in range(1, iters + 1):
+        act = (y * f < 1.0).astype(np.float64)
+        a = (1.0 - 1.0 / t) * a + (1.0 / (lam * t * n)) * y * act
+        f = matvec(a)
+    return a, f, hinge_svm_objective(f, a, y, lam)
+
+
 def minres_solve(matvec, y, lam, tol=1e-6, max_iter=10000, record_every=0):
     """MINRES (Paige and Saunders) for (K + lam I) a = y, the solver of Sec. 6.
 

@@ -8,6 +8,10 @@
   (K + lam I)^-1 y of Eq. 1;
 * flipping every label flips the solution (y -> -y gives a -> -a), and the objective never
   increases from one Newton iterate to the next.
+
+The hinge-loss SVM by sub-gradients (Pegasos in the coefficients): its first step is y / (lam n)
+in closed form, it flips with the labels, and its objective approaches, from above, the optimum
+computed independently from the dual quadratic program (scipy's bounded L-BFGS).
 """
 import numpy as np
 import pytest
@@ -83,3 +87,44 @@ def test_label_flip_and_monotone_objective():
         Jk = orc.svm_objective(K @ ak, ak, y, lam)
         assert Jk <= prev + 1e-12
         prev = Jk
+
+
+# ---------------------------------------------------------------- hinge loss, sub-gradients
+def _dual_optimum(K, y, lam):
+    """The hinge SVM optimum from its dual, a box-constrained QP solved by scipy's L-BFGS-B:
+    max_alpha sum(alpha) / n - (1 / (2 lam n^2)) alpha^T (yy^T o K) alpha, 0 <= alpha <= 1, and
+    a* = alpha * y / (lam n)."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    n = len(y)
+    Q = (y[:, None] * y[None, :]) * K / (lam * n * n)
+    fun = lambda al: 0.5 * al @ Q @ al - al.sum() / n
+    jac = lambda al: Q @ al - 1.0 / n
+    res = scipy_opt.minimize(fun, np.full(n, 0.5), jac=jac, method="L-BFGS-B", bounds=[(0.0, 1.0)] * n,
+                             options={"maxiter": 50000, "gtol": 1e-14, "ftol": 1e-16})
+    return res.x * y / (lam * n)
+
+
+def test_hinge_subgradient_first_step_and_label_flip():
+    K, y = _problem(n=30, seed=4)
+    lam = 0.1
+    mv = lambda x: K @ x
+    a1, f1, _ = orc.hinge_svm_subgradient(mv, y, lam, 1)
+    np.testing.assert_allclose(a1, y / (lam * len(y)), rtol=0, atol=0)   # f = 0: every pair active
+    np.testing.assert_allclose(f1, K @ a1, rtol=1e-14, atol=1e-15)
+    a, _, _ = orc.hinge_svm_subgradient(mv, y, lam, 50)
+    b, _, _ = orc.hinge_svm_subgradient(mv, -y, lam, 50)
+    np.testing.assert_allclose(b, -a, rtol=0, atol=1e-15)
+
+
+def test_hinge_subgradient_approaches_the_dual_optimum():
+    K, y = _problem(n=40, seed=5)
+    lam = 0.1
+    mv = lambda x: K @ x
+    a_star = _dual_optimum(K, y, lam)
+    J_star = orc.hinge_svm_objective(K @ a_star, a_star, y, lam)
+    gaps = []
+    for T in (100, 1000, 10000):
+        a, f, J = orc.hinge_svm_subgradient(mv, y, lam, T)
+        assert J >= J_star - 1e-9                       # the dual optimum is a lower bound
+        gaps.append(J - J_star)
+    assert gaps[2] < gaps[0] and gaps[2] <= 2e-3 * J_star
