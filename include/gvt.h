@@ -449,6 +449,22 @@ gvt_status gvt_svm_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* d
                                 int64_t max_cg_iter, gvt_solve_info* info, void* stream);
 
 /*
+ * Support vector machine with the hinge loss by sub-gradient steps (Sec. 7 names
+ * sub-gradient computations for support vector machines among the uses of the product):
+ *     J(a) = (lambda / 2) a^T K a + (1 / n) sum_i max(0, 1 - y_i f_i),   f = K a,  y_i = +-1,
+ * minimised by the kernelised Pegasos update (Shalev-Shwartz et al. 2011, every pair in every
+ * step):  a <- (1 - 1/t) a + (1 / (lambda t n)) y [y f < 1],  then f = K a,  t = 1 .. iters.
+ * One FP64 product per step.  M, N FP64 and symmetric; a training plan.  y, a: device FP64
+ * (a out; starts from zero).  objective (host, may be NULL) receives J at the returned a.
+ * info (may be NULL): iterations = iters.  The step count is the caller's choice: the
+ * method converges as O(log t / (lambda t)) in J and has no exact stopping rule.
+ */
+gvt_status gvt_svm_subgradient_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
+                                     const gvt_matrix* M, const gvt_matrix* N, const double* y,
+                                     double lambda, double* a, int64_t iters, double* objective,
+                                     gvt_solve_info* info, void* stream);
+
+/*
  * MINRES on the same system (the solver of Sec. 6, which stops it early):
  * Lanczos on K + lambda I from y with Givens rotations, so that the k-th iterate
  * minimises ||y - (K + lambda I) a|| over span{y, A y, ..., A^{k-1} y}.  One FP64

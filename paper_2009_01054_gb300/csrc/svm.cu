@@ -9,6 +9,12 @@
 // pairs.  A backtracking line search halves the step from a toward a+ until J does not increase
 // (along the step f moves linearly, so J needs only dot products).  The solution is reached when
 // a full step leaves S unchanged.
+//
+// The hinge loss is served by sub-gradient steps instead (the kernelised Pegasos update of
+// Shalev-Shwartz et al., 2011, without sampling):
+//   J(a) = (lambda / 2) a^T K a + (1 / n) sum_i max(0, 1 - y_i f_i),
+//   a <- (1 - 1/t) a + (1 / (lambda t n)) y [y f < 1],   f = K a,   t = 1, 2, ...
+// one product per step.
 #include <chrono>
 #include <cmath>
 #include <cstdint>
@@ -120,6 +126,28 @@ sv_grad(const double* __restrict__ a, const double* __restrict__ f, const double
     }
     block_sum_slot(acc, part, 0);
     block_sum_slot(yy, part, 1);
+}
+
+// one sub-gradient step of the hinge SVM: a = (1 - 1/t) a + c y [y f < 1], c = 1 / (lambda t n)
+__global__ void sg_step(double* __restrict__ a, const double* __restrict__ f, const double* __restrict__ y,
+                        double keep, double c, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = keep * a[i] + (y[i] * f[i] < 1.0 ? c * y[i] : 0.0);
+}
+
+// slot 0 = a . f, slot 1 = sum_i max(0, 1 - y_i f_i)
+__global__ void __launch_bounds__(kSvThreads)
+sg_objective(const double* __restrict__ a, const double* __restrict__ f, const double* __restrict__ y, int64_t n,
+             double* __restrict__ part)
+{
+    double af = 0.0, loss = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        af += a[i] * f[i];
+        loss += fmax(0.0, 1.0 - y[i] * f[i]);
+    }
+    block_sum_slot(af, part, 0);
+    block_sum_slot(loss, part, 1);
 }
 
 }  // namespace
@@ -273,6 +301,65 @@ gvt_status gvt_svm_newton_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* d
         result = GVT_ERR_NOT_CONVERGED;
     }
     return ret(result);
+}
+
+gvt_status gvt_svm_subgradient_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                                     const gvt_matrix* N, const double* y, double lambda, double* a, int64_t iters,
+                                     double* objective, gvt_solve_info* info_out, void* stream)
+{
+    gvt_solve_info local{};
+    gvt_solve_info* info = info_out ? info_out : &local;
+    *info = gvt_solve_info{};
+    const auto t0 = std::chrono::steady_clock::now();
+    auto ret = [&](gvt_status st) {
+        info->status = st;
+        info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return st;
+    };
+    if (!h || !plan || !desc || !M || !M->data || (!desc->homogeneous && (!N || !N->data))) {
+        set_error("gvt_svm_subgradient_solve: NULL argument");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (!plan->out_is_in || !(lambda > 0.0) || iters < 0) {
+        set_error("gvt_svm_subgradient_solve: training plan, lambda > 0 and iters >= 0 are required");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (M->dtype != GVT_F64 || (!desc->homogeneous && N->dtype != GVT_F64)) {
+        set_error("gvt_svm_subgradient_solve: M and N must be FP64");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    const int64_t n = plan->n_in;
+    if (n > 0 && (!y || !a)) {
+        set_error("gvt_svm_subgradient_solve: y or a is NULL");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    if (objective) *objective = 0.0;
+    if (n == 0) return ret(GVT_OK);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const gvt_matrix* Nn = desc->homogeneous ? M : N;
+    DevBuf bf, bpart;
+    gvt_status st;
+    if ((st = bf.reserve(8 * (size_t)n, s)) != GVT_OK || (st = bpart.reserve(8 * (size_t)kSvBlocks * 2, s)) != GVT_OK)
+        return ret(st);
+    double* f = static_cast<double*>(bf.ptr);
+    double* part = static_cast<double*>(bpart.ptr);
+    const unsigned g = sv_grid(n);
+    sv_zero<<<g, 256, 0, s>>>(a, n);
+    sv_zero<<<g, 256, 0, s>>>(f, n);
+    GVT_LAUNCHED(2, "hinge svm init");
+    for (int64_t t = 1; t <= iters; ++t) {
+        sg_step<<<g, 256, 0, s>>>(a, f, y, 1.0 - 1.0 / (double)t, 1.0 / (lambda * (double)t * (double)n), n);
+        GVT_LAUNCHED(1, "hinge svm step");
+        if ((st = pairwise_apply<double>(plan, desc, M, Nn, a, f, s)) != GVT_OK) return ret(st);
+    }
+    sg_objective<<<kSvBlocks, kSvThreads, 0, s>>>(a, f, y, n, part);
+    GVT_LAUNCHED(1, "hinge svm objective");
+    std::vector<double> ph((size_t)kSvBlocks * 2);
+    double sums[2];
+    if ((st = host_reduce(part, 2, ph, sums, s)) != GVT_OK) return ret(st);
+    if (objective) *objective = 0.5 * lambda * sums[0] + sums[1] / (double)n;
+    info->iterations = iters;
+    return ret(GVT_OK);
 }
 
 }  // extern "C"

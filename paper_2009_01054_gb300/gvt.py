@@ -111,6 +111,8 @@ SIGNATURES = [
                                      c_i32, c_dbl, c_dbl, c_i64, _P(gvt_solve_info), c_vp]),
     ("gvt_svm_newton_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl, c_vp,
                                      c_i32, c_dbl, c_i64, _P(gvt_solve_info), c_vp]),
+    ("gvt_svm_subgradient_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
+                                          c_vp, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_minres_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
                                      c_vp, c_dbl, c_i64, c_i64, c_i64, c_vp, _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix),
@@ -631,6 +633,18 @@ def svm_newton_solve(handle, plan, kind, M, N, y, lam, newton_iters=50, cg_tol=1
     if st not in (GVT_OK, GVT_ERR_BREAKDOWN, GVT_ERR_NOT_CONVERGED):
         raise GvtError(st, "gvt_svm_newton_solve", last_error())
     return a, st, info
+
+
+def svm_subgradient_solve(handle, plan, kind, M, N, y, lam, iters, symmetric=True, stream=None):
+    """Hinge-loss SVM (labels +-1) by kernelised sub-gradient steps; returns (a, objective, info)."""
+    torch = _torch()
+    a = torch.zeros_like(y)
+    info = gvt_solve_info()
+    obj = c_dbl(0.0)
+    _call("gvt_svm_subgradient_solve", handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
+          ctypes.byref(matrix(N, symmetric)) if N is not None else None, ptr(y), float(lam), ptr(a), int(iters),
+          ctypes.byref(obj), ctypes.byref(info), stream_ptr(stream))
+    return a, obj.value, info
 
 
 def krr_minres_solve(handle, plan, kind, M, N, y, lam, rel_tol=1e-6, max_iter=10000, record_every=0,

@@ -86,3 +86,21 @@ def test_svm_arguments_and_iteration_cap(H):
     ref, _, _, _ = orc.svm_newton(mv, y, 0.05, newton_iters=1)
     assert np.max(np.abs(a.cpu().numpy() - ref)) <= 1e-7 * max(1.0, np.max(np.abs(ref)))
     plan.close()
+
+
+@pytest.mark.parametrize("kind", ["kronecker", "mlpk"])
+def test_hinge_svm_subgradient_matches_the_oracle(H, kind):
+    """The hinge-loss SVM by kernelised sub-gradient steps: after 200 steps the GPU coefficients
+    and objective equal the oracle's (the same deterministic sequence, FP64 products), and the
+    objective lies above the optimum of the dual quadratic program."""
+    p, M, N, plan, y, mv, K = _setup(H, kind)
+    lam = 0.05
+    a, J, info = gvt.svm_subgradient_solve(H, plan, kind, M, N, torch.as_tensor(y, device=DEV), lam, 200)
+    ref, fref, Jref = orc.hinge_svm_subgradient(mv, y, lam, 200)
+    an = a.cpu().numpy()
+    print("%s: hinge objective %.6f (oracle %.6f)" % (kind, J, Jref))
+    assert info.iterations == 200
+    assert np.max(np.abs(an - ref)) <= 1e-9 * np.max(np.abs(ref))
+    assert abs(J - Jref) <= 1e-10 * abs(Jref)
+    assert abs(J - orc.hinge_svm_objective(K @ an, an, y, lam)) <= 1e-10 * abs(J)
+    plan.close()
