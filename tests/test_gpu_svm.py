@@ -104,5 +104,6 @@ def test_hinge_svm_subgradient_matches_the_oracle(H, kind):
     assert np.max(np.abs(an - ref)) <= 1e-9 * np.max(np.abs(ref))
     assert abs(J - Jref) <= 1e-10 * abs(Jref)
     assert abs(J - orc.hinge_svm_objective(K @ an, an, y, lam)) <= 1e-10 * abs(J)
-    assert np.sum(y * (K @ an) >= 1.0) > 100          # the active set moved
+    # pairs left the margin during the run: the iterate is not the all-active fixed point y / (lam n)
+    assert np.max(np.abs(an - y / (lam * p.n))) > 0.1 / (lam * p.n)
     plan.close()
