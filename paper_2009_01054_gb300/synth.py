@@ -86,9 +86,15 @@ def homogeneous(seed=0, m=2000, dim=64, n=200_000):
                        lambdas=[1e-2], homogeneous=True)
 
 
-def _bilinear_labels(rng, Xd, Xt, d, t, noise=0.1):
+def _bilinear_labels(rng, Xd, Xt, d, t, noise=0.1, chunk=1 << 18):
+    """y = x_d^T B x_t / sqrt(dim_d dim_t) + noise, B ~ N(0, 1): the drug projections x_d^T B
+    once, then the pair products in chunks (10M pairs never materialise their features)."""
     B = rng.standard_normal((Xd.shape[1], Xt.shape[1]))
-    sig = np.einsum("ij,jk,ik->i", Xd[d], B, Xt[t]) / np.sqrt(Xd.shape[1] * Xt.shape[1])
+    P = Xd @ B
+    sig = np.empty(len(d))
+    for k in range(0, len(d), chunk):
+        sig[k:k + chunk] = np.einsum("ij,ij->i", P[d[k:k + chunk]], Xt[t[k:k + chunk]])
+    sig /= np.sqrt(Xd.shape[1] * Xt.shape[1])
     return sig + noise * rng.standard_normal(len(d))
 
 
