@@ -189,17 +189,41 @@ DTYPE_OF_ENGINE = {"simt": "f32", "tc": "bf16x3 stage 1 + f32 stage 2", "tc16": 
                    "auto": "f16x3 (f32 accumulate) where dense, else f32"}
 
 KERNEL_SOURCE = {"stage1_dense_kernel": "stages.cu", "stage2_dense_kernel": "stages.cu",
-                 "gemv_rows_kernel": "stages.cu", "tc_gemm_kernel": "tc_gemm.cu"}
+                 "tc_gemm_kernel": "tc_gemm.cu"}
+
+
+def kernel_text(kernel_name):
+    """Source text of a __global__ kernel definition: from its template line (if any) to the brace
+    that closes its body.  None if it is not found."""
+    src = open(os.path.join(ROOT, "paper_2009_01054_gb300", "csrc", KERNEL_SOURCE[kernel_name])).read()
+    pos = 0
+    while True:
+        i = src.find(kernel_name + "(", pos)
+        if i < 0:
+            return None
+        g = src.rfind("__global__", 0, i)
+        if g >= 0 and i - g < 200 and ";" not in src[g:i]:
+            break
+        pos = i + 1
+    start = src.rfind("\ntemplate", 0, g)
+    start = start + 1 if start >= 0 and g - start < 200 else src.rfind("\n", 0, g) + 1
+    depth, k = 0, src.find("{", i)
+    for j in range(k, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[j], 0)
+        if depth == 0:
+            return src[start:j + 1]
+    return None
 
 
 def traffic_for(kernel_name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the kernel as its source
+    reads now (the record keeps the sha256 of the kernel's definition)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get("kernels", {}).get(kernel_name)
-        src = open(os.path.join(ROOT, "paper_2009_01054_gb300", "csrc", KERNEL_SOURCE[kernel_name]), "rb").read()
-        if not rec or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        text = kernel_text(kernel_name)
+        if not rec or text is None or rec.get("kernel_sha256") != hashlib.sha256(text.encode()).hexdigest():
             return None
         return rec.get("dram_bytes_per_launch")
     except Exception:
