@@ -227,13 +227,6 @@ gvt_status stage2_identity(const T* S, int64_t lds, int64_t X, const S2Outputs& 
 template <class T>
 gvt_status segment_sums(const int32_t* seg, const int32_t* perm, int64_t K, const T* v, double coef,
                         T* s_out, cudaStream_t s);
-// z[r] = sum_{x < X} F[r, x] * s[x]  for r < R  (mode squares F)
-template <class T>
-gvt_status gemv_rows(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svec, T* z,
-                     cudaStream_t s);
-// u[i] += z[idx[i]]  for i < n
-template <class T>
-gvt_status gather_add(const T* z, const int32_t* idx, int64_t n, T* u, cudaStream_t s);
 // One-sided groups on the same factor share one pass over it (up to kMaxOneSidedShare):
 // z[g*ldz + r] = sum_{x < X} F[r, x] * svecs[g*lds + x], and u[i] += sum_g z_g[idx_g[i]].
 constexpr int kMaxOneSidedShare = 4;

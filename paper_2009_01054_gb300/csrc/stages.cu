@@ -323,25 +323,6 @@ __global__ void segment_sums_kernel(const int32_t* __restrict__ seg, const int32
     }
 }
 
-template <class T, int MODE>
-__global__ void gemv_rows_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
-                                 const T* __restrict__ s, T* __restrict__ z)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += nw) {
-        const T* row = F + r * ldf;
-        T acc = T(0);
-        for (int64_t x = lane; x < X; x += 32) {
-            const T f = MODE == FM_SQUARE ? row[x] * row[x] : row[x];
-            acc = fma(f, s[x], acc);
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) z[r] = acc;
-    }
-}
-
 // z_g[r] = sum_x F[r, x] s_g[x] for G vectors s_g = s + g lds in one pass over F
 template <class T, int MODE, int G>
 __global__ void gemv_rows_multi_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
@@ -452,15 +433,6 @@ __global__ void gather_add_multi_kernel(GatherSet<T> gs, int64_t n, T* __restric
             if (g < gs.count) acc += gs.z[g][gs.idx[g][i]];
         u[i] += acc;
     }
-}
-
-template <class T>
-__global__ void gather_add_kernel(const T* __restrict__ z, const int32_t* __restrict__ idx, int64_t n,
-                                  T* __restrict__ u)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        u[i] += z[idx[i]];
 }
 
 template <class T>
@@ -705,20 +677,6 @@ gvt_status segment_sums(const int32_t* seg, const int32_t* perm, int64_t K, cons
 }
 
 template <class T>
-gvt_status gemv_rows(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svec, T* z,
-                     cudaStream_t s)
-{
-    if (R <= 0) return GVT_OK;
-    const unsigned g = grid1d(R * 32, 256, 152 * 16);
-    if (mode == FM_SQUARE)
-        gemv_rows_kernel<T, FM_SQUARE><<<g, 256, 0, s>>>(F, ldf, R, X, svec, z);
-    else
-        gemv_rows_kernel<T, FM_DENSE><<<g, 256, 0, s>>>(F, ldf, R, X, svec, z);
-    GVT_LAUNCH_CHECK("gemv_rows");
-    return GVT_OK;
-}
-
-template <class T>
 gvt_status gemv_rows_multi(const T* F, int64_t ldf, int mode, int64_t R, int64_t X, const T* svecs, int64_t lds,
                            int count, T* z, int64_t ldz, cudaStream_t s)
 {
@@ -759,15 +717,6 @@ gvt_status gather_add_multi(const T* const* z, const int32_t* const* idx, int co
     }
     gather_add_multi_kernel<T><<<grid1d(n, 256), 256, 0, s>>>(gs, n, u);
     GVT_LAUNCH_CHECK("gather_add_multi");
-    return GVT_OK;
-}
-
-template <class T>
-gvt_status gather_add(const T* z, const int32_t* idx, int64_t n, T* u, cudaStream_t s)
-{
-    if (n <= 0) return GVT_OK;
-    gather_add_kernel<T><<<grid1d(n, 256), 256, 0, s>>>(z, idx, n, u);
-    GVT_LAUNCH_CHECK("gather_add");
     return GVT_OK;
 }
 
@@ -899,9 +848,6 @@ gvt_status tanimoto_kernel(const uint32_t* X, int64_t rx, const uint32_t* Y, int
                                            cudaStream_t);                                           \
     template gvt_status segment_sums<T>(const int32_t*, const int32_t*, int64_t, const T*, double,  \
                                         T*, cudaStream_t);                                          \
-    template gvt_status gemv_rows<T>(const T*, int64_t, int, int64_t, int64_t, const T*, T*,         \
-                                     cudaStream_t);                                                 \
-    template gvt_status gather_add<T>(const T*, const int32_t*, int64_t, T*, cudaStream_t);         \
     template gvt_status gemv_rows_multi<T>(const T*, int64_t, int, int64_t, int64_t, const T*, int64_t, int, \
                                            T*, int64_t, cudaStream_t);                                   \
     template gvt_status gather_add_multi<T>(const T* const*, const int32_t* const*, int, int64_t, T*,     \
