@@ -368,25 +368,30 @@ template <> struct Vec16<double> {
     }
 };
 
-// The same product with 16-byte loads, four in flight per lane: F and the s_g 16-byte aligned,
-// ldf and lds multiples of the vector width (the host checks).  Columns past the last whole
-// vector are read one element per lane.
+// The same product with 16-byte loads: one block of kGemvBlock threads per row, so that a row's
+// loads are all in flight at once (about four per thread for rows of 2000 FP32), then a fixed-order
+// block reduction.  F and the s_g 16-byte aligned, ldf and lds multiples of the vector width (the
+// host checks).  Columns past the last whole vector are read one element per thread.
+constexpr int kGemvBlock = 128;
+
 template <class T, int MODE, int G>
-__global__ void gemv_rows_multi_vec_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
-                                           const T* __restrict__ s, int64_t lds, T* __restrict__ z, int64_t ldz)
+__global__ void __launch_bounds__(kGemvBlock)
+gemv_rows_multi_vec_kernel(const T* __restrict__ F, int64_t ldf, int64_t R, int64_t X,
+                           const T* __restrict__ s, int64_t lds, T* __restrict__ z, int64_t ldz)
 {
     using V = typename Vec16<T>::type;
     constexpr int W = Vec16<T>::width;
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    constexpr int NWARP = kGemvBlock / 32;
+    __shared__ T red[G][NWARP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t Xv = X / W * W;
-    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += nw) {
+    for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
         const T* row = F + r * ldf;
         T acc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) acc[g] = T(0);
 #pragma unroll 4
-        for (int64_t x = (int64_t)lane * W; x < Xv; x += 32 * W) {
+        for (int64_t x = (int64_t)threadIdx.x * W; x < Xv; x += kGemvBlock * W) {
             T f[W];
             Vec16<T>::unpack(__ldg(reinterpret_cast<const V*>(row + x)), f);
 #pragma unroll
@@ -400,7 +405,7 @@ __global__ void gemv_rows_multi_vec_kernel(const T* __restrict__ F, int64_t ldf,
                 for (int e = 0; e < W; ++e) acc[g] = fma(f[e], sv[e], acc[g]);
             }
         }
-        for (int64_t x = Xv + lane; x < X; x += 32) {
+        for (int64_t x = Xv + threadIdx.x; x < X; x += kGemvBlock) {
             const T f = MODE == FM_SQUARE ? row[x] * row[x] : row[x];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[g] = fma(f, s[g * lds + x], acc[g]);
@@ -409,8 +414,16 @@ __global__ void gemv_rows_multi_vec_kernel(const T* __restrict__ F, int64_t ldf,
         for (int g = 0; g < G; ++g) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
-            if (lane == 0) z[g * ldz + r] = acc[g];
+            if (lane == 0) red[g][warp] = acc[g];
         }
+        __syncthreads();
+        if (threadIdx.x < G) {
+            T t = T(0);
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) t += red[threadIdx.x][w];
+            z[threadIdx.x * ldz + r] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -682,13 +695,14 @@ gvt_status gemv_rows_multi(const T* F, int64_t ldf, int mode, int64_t R, int64_t
 {
     if (R <= 0 || count <= 0) return GVT_OK;
     const unsigned g = grid1d(R * 32, 256, 152 * 16);
+    const unsigned gv = (unsigned)std::min<int64_t>(R, 152 * 64);   // a block per row
     constexpr int W = Vec16<T>::width;
     const bool vec = ((uintptr_t)F & 15) == 0 && ((uintptr_t)svecs & 15) == 0 && ldf % W == 0 && lds % W == 0;
 #define GVT_GEMV_MULTI(G)                                                                                    \
     if (vec && mode == FM_SQUARE)                                                                            \
-        gemv_rows_multi_vec_kernel<T, FM_SQUARE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);     \
+        gemv_rows_multi_vec_kernel<T, FM_SQUARE, G><<<gv, kGemvBlock, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz); \
     else if (vec)                                                                                            \
-        gemv_rows_multi_vec_kernel<T, FM_DENSE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);      \
+        gemv_rows_multi_vec_kernel<T, FM_DENSE, G><<<gv, kGemvBlock, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);  \
     else if (mode == FM_SQUARE)                                                                              \
         gemv_rows_multi_kernel<T, FM_SQUARE, G><<<g, 256, 0, s>>>(F, ldf, R, X, svecs, lds, z, ldz);         \
     else                                                                                                     \
