@@ -189,7 +189,7 @@ DTYPE_OF_ENGINE = {"simt": "f32", "tc": "bf16x3 stage 1 + f32 stage 2", "tc16": 
                    "auto": "f16x3 (f32 accumulate) where dense, else f32"}
 
 KERNEL_SOURCE = {"stage1_dense_kernel": "stages.cu", "stage2_dense_kernel": "stages.cu",
-                 "tc_gemm_kernel": "tc_gemm.cu"}
+                 "gemv_rows_multi_vec_kernel": "stages.cu", "tc_gemm_kernel": "tc_gemm.cu"}
 
 
 def kernel_text(kernel_name):
@@ -423,7 +423,7 @@ def run_gvt(args, ws, rank, local):
             roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "peak_source": peak_src}
         kname = {"stage1": "stage1_dense_kernel", "stage2": "stage2_dense_kernel",
-                 "one_sided": "gemv_rows_kernel"}[dom]
+                 "one_sided": "gemv_rows_multi_vec_kernel"}[dom]
         roof.update({"kernel": kname, "traffic": traffic_for(kname), "ms_per_launch": per_launch_ms,
                      "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
                      "hbm_frac": (bytes_l / (per_launch_ms / 1e3) / 1e9) / hbm})
