@@ -163,8 +163,9 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- oracle (CPU)
-def cpu_oracle_rate(p, seconds, rows_per_call=64, seed=0):
-    """FP64 oracle pair-terms/s on sampled output rows (each row against all inputs)."""
+def cpu_oracle_rate(p, seconds, rows_per_call=64, seed=0, nthreads=0):
+    """FP64 oracle pair-terms/s on sampled output rows (each row against all inputs); nthreads = 0
+    uses every host core."""
     import numpy as np
     import oracle as orc
     M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
@@ -174,13 +175,27 @@ def cpu_oracle_rate(p, seconds, rows_per_call=64, seed=0):
     while True:
         idx = rng.choice(p.n, rows_per_call, replace=False)
         for kind in KINDS:
-            orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, p.v)
+            orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, p.v, nthreads=nthreads)
         rows_done += rows_per_call
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     rate = rows_done * float(p.n) * sum(TERMS.values()) / el
-    return rate, el, rows_done, orc.num_threads()
+    return rate, el, rows_done, (orc.num_threads() if nthreads == 0 else nthreads)
+
+
+def cpu_oracle_small_solve():
+    """The oracle's plain FP64 CG (Eq. 1) on the small drug-target configuration (64 x 48 objects,
+    1000 pairs, lambda = 1e-2) to relative residual 1e-6, every product the oracle's own."""
+    import oracle as orc
+    from paper_2009_01054_gb300 import synth
+    p = synth.small(0)
+    M, N = orc.gaussian_kernel(p.Xd, gamma=p.gamma), orc.gaussian_kernel(p.Xt, gamma=p.gamma)
+    mv = lambda x: orc.pairwise_matvec("kronecker", M, N, p.d, p.t, p.d, p.t, x)
+    t0 = time.perf_counter()
+    a, it, rel = orc.cg_solve(mv, p.y, p.lambdas[0], tol=1e-6)
+    return {"ms": (time.perf_counter() - t0) * 1e3, "iterations": it, "rel_residual": rel,
+            "workload": "64 x 48 objects, 1000 pairs, Kronecker of Gaussians, lambda = 1e-2"}
 
 
 # arithmetic of the products per engine: FP32 SIMT, or 16-bit hi/lo splits on the tensor cores
@@ -505,9 +520,13 @@ def run_gvt(args, ws, rank, local):
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         rate, el, rows, cores = cpu_oracle_rate(p, args.cpu_seconds)
+        rate1, el1, rows1, _ = cpu_oracle_rate(p, min(3.0, args.cpu_seconds), nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d sampled output pairs x all %d input pairs x 9 kernels, FP64, %.1f s"
-                         % (rows, p.n, el)}
+                         % (rows, p.n, el),
+               "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                               "sample": "%d sampled output pairs, %.1f s" % (rows1, el1)},
+               "small_solve": cpu_oracle_small_solve()}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
