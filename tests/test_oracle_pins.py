@@ -418,3 +418,26 @@ def test_fingerprint_packing_round_trip():
     unpacked = ((packed[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(9, 96)[:, :77]
     np.testing.assert_array_equal(unpacked, bits)
     assert np.all((packed[:, 2] >> np.uint32(13)) == 0)   # bits past the length are zero
+
+
+def test_kernel_value_is_the_kernel_matrix_entry():
+    """The oracle's single-entry call k((a, b), (c, e)) equals the matching entry of its explicit
+    pairwise kernel matrix for all nine kernels (argument order: output pair, then input pair)."""
+    rng = np.random.default_rng(35)
+    m, q = 7, 5
+    A = rng.standard_normal((m, 3))
+    B = rng.standard_normal((q, 3))
+    M = orc.gaussian_kernel(A, gamma=0.4)
+    N = orc.gaussian_kernel(B, gamma=0.7)
+    for kind in ["kronecker", "gaussian", "linear", "poly2d", "cartesian", "symmetric", "antisymmetric",
+                 "ranking", "mlpk"]:
+        homo = kind in ("symmetric", "antisymmetric", "ranking", "mlpk")
+        qq = m if homo else q
+        d_out, t_out = synth.random_pairs(rng, 6, m, qq)
+        d_in, t_in = synth.random_pairs(rng, 5, m, qq)
+        Nk = M if homo else N
+        K = orc.kernel_matrix(kind, M, Nk, d_out, t_out, d_in, t_in)
+        for i in range(6):
+            for j in range(5):
+                val = orc.kernel_value(kind, M, Nk, d_out[i], t_out[i], d_in[j], t_in[j])
+                assert val == K[i, j], (kind, i, j)
