@@ -14,7 +14,10 @@
  * gathers u_i = <M[dhat_i, :], S[that_i, :]>.  Every pairwise kernel of
  * Table 4b is a sum of such Kronecker terms with permuted index sequences
  * (Corollary 1); the kernel ridge regression system (K + lambda I) a = y
- * (Eq. 1) is solved with conjugate gradients on top.
+ * (Eq. 1) is solved with conjugate gradients on top.  The same product also
+ * drives the paper's MINRES with early stopping (Sec. 6), multi-shift CG over a
+ * lambda sweep, batched solves of many problems, and kernel logistic
+ * regression and support vector machines (Sec. 7).
  *
  * Conventions shared by every entry point:
  *  - Every data pointer is DEVICE memory owned by the caller unless stated;
