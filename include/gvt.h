@@ -626,11 +626,11 @@ int64_t gvt_launch_count(void);
 #define GVT_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 
 /*
- * u = R(dhat,that) (M kron N) R(d,t)^T v, like gvt_matvec, for callers that
- * cannot allocate device memory: programs whose framework owns all device
- * memory through its own pool, or latency-bound loops that may not call
- * cudaMalloc / cudaFree (they can synchronise the device).  The paper has no
- * counterpart; this is a deployment variant of the Theorem 1 product.
+ * u = R(dhat,that) (M kron N) R(d,t)^T v, like gvt_matvec, with no device
+ * allocation, for callers that cannot allocate device memory: programs whose
+ * framework owns all device memory through its own pool, or latency-bound
+ * loops that may not call cudaMalloc / cudaFree (they can synchronise the
+ * device).  The paper has no counterpart.
  *
  * It needs no handle and no plan and calls no allocating routine.  Its only
  * scratch (one error word and the q_rows x m_cols intermediate S of the
@@ -638,15 +638,19 @@ int64_t gvt_launch_count(void);
  * GVT_STATIC_SCRATCH_BYTES bytes, which every device that loads the library
  * holds until the process exits.  Requests with
  * q_rows * m_cols * element size > GVT_STATIC_SCRATCH_BYTES - 256 return
- * GVT_ERR_INVALID_ARG without launching anything.
+ * GVT_ERR_INVALID_ARG without launching anything (the check divides rather
+ * than multiplies, so no declared size can wrap it).
  *
  *  - Arguments as for gvt_plan_create + gvt_matvec (device index arrays,
  *    d_out = t_out = NULL for the training operator), one column, dtype
  *    GVT_F64 or GVT_F32.  A symmetric N lets stage 1 read rows instead of
  *    columns.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *    (cudaGetSymbolAddress) and caches it.  That first use may also load the
+ *    library's device code on the device, which is when the driver reserves
+ *    the array.
+ *  - Every call synchronises `stream` (below), so no call can be captured
+ *    into a CUDA graph.
  *  - Every call clears the parts of the array it uses; the array keeps the
  *    last call's contents otherwise.  All calls share the one array, so calls
  *    whose work overlaps on the GPU (different streams, other host threads)

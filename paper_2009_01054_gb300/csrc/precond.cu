@@ -5,9 +5,11 @@
 // diagonal minus a learned rank-32 term, the structure of a Nystrom
 // preconditioner with the subspace predicted per pair by the network.
 //
-// Per training pair i a small MLP maps the features
-//   x_i = ([M[d_i,d_i], N[t_i,t_i], log(1+deg d_i), log(1+deg t_i)] - mu) / sigma
-// through 4 -> 128 -> 128 -> 33 (ReLU) to D_i = softplus(o_0) and V_i = o_{1..32};
+// Per training pair i a small MLP maps the six features
+//   x_i = ([M[d_i,d_i], N[t_i,t_i], log(1+deg d_i), log(1+deg t_i), slog g1_i, slog g2_i] - mu) / sigma
+// (g1 = K 1 and g2 = K (g1 / mean g1), the kernel-graph degrees, through the signed log
+// slog x = sign(x) log(1 + |x|)) through 6 -> 128 -> 128 -> 33 (ReLU) to D_i = softplus(o_0)
+// and V_i = o_{1..32};
 //   P r = s (z - V (I + V^T V)^{-1} V^T z),   s = sqrt(D),  z = s r,
 // a diagonal matrix minus a rank-32 term in the Woodbury form, symmetric
 // positive definite for any network output.  It approximates (K + lambda I)^{-1}

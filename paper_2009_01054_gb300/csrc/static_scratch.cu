@@ -128,13 +128,16 @@ gvt_status run_static(int64_t m_rows, int64_t m_cols, int64_t q_rows, int64_t q_
                       const gvt_matrix* M, const gvt_matrix* N, const T* v, T* u, cudaStream_t s)
 {
     const int64_t X = m_cols, Y = q_rows;
-    const size_t s_bytes = sizeof(T) * (size_t)X * (size_t)Y;
-    if (s_bytes > kStaticBytes - kStaticHeader) {
-        set_error("gvt_matvec_static: q_rows * m_cols * element size = " + std::to_string(s_bytes) +
-                  " bytes exceeds the static scratch of " +
-                  std::to_string(kStaticBytes - kStaticHeader) + " bytes");
+    // Y * X elements must fit the scratch after its header; compare by division so that large
+    // declared sizes cannot wrap the product.
+    const uint64_t cap_elems = (kStaticBytes - kStaticHeader) / sizeof(T);
+    if (X > 0 && (uint64_t)Y > cap_elems / (uint64_t)X) {
+        set_error("gvt_matvec_static: q_rows * m_cols = " + std::to_string(Y) + " * " + std::to_string(X) +
+                  " elements exceed the static scratch of " + std::to_string(kStaticBytes - kStaticHeader) +
+                  " bytes");
         return GVT_ERR_INVALID_ARG;
     }
+    const size_t s_bytes = sizeof(T) * (size_t)X * (size_t)Y;
     void* base = nullptr;
     GVT_CHECK(static_scratch(&base));
     unsigned int* bad = static_cast<unsigned int*>(base);

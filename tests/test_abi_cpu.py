@@ -166,3 +166,20 @@ def test_solve_defaults(lib):
     assert o.rel_tol == 1e-6 and o.mode == gvt.GVT_SOLVE_FP64_CG and o.inner_tol == 1e-3
     assert o.precond_budget == 0 and not o.precond
     assert gvt.gvt_version() >= 10000
+
+
+def test_static_product_refuses_sizes_whose_byte_count_wraps(lib):
+    """gvt_matvec_static refuses a declared q_rows x m_cols whose byte count wraps 2^64 (2^29 x 2^32
+    FP64 elements = 2^64 bytes, 0 after wrapping) before any CUDA call: the check runs on the host,
+    so it is exercised here without a GPU.  The matrix structs only declare their extents."""
+    buf = (ctypes.c_double * 4)()
+    X, Y = 1 << 32, 1 << 29
+    Mm = gvt.gvt_matrix(ctypes.cast(buf, ctypes.c_void_p), 1, X, X, gvt.GVT_F64, 0)
+    Nm = gvt.gvt_matrix(ctypes.cast(buf, ctypes.c_void_p), Y, 1, 1, gvt.GVT_F64, 0)
+    idx = (ctypes.c_int32 * 1)()
+    st = lib.gvt_matvec_static(1, X, Y, 1, ctypes.cast(idx, ctypes.c_void_p), ctypes.cast(idx, ctypes.c_void_p),
+                               1, None, None, 0, ctypes.byref(Mm), ctypes.byref(Nm),
+                               ctypes.cast(buf, ctypes.c_void_p), ctypes.cast(buf, ctypes.c_void_p),
+                               gvt.GVT_F64, None)
+    assert st == gvt.GVT_ERR_INVALID_ARG
+    assert "static scratch" in gvt.last_error()

@@ -4,14 +4,17 @@ Callers that cannot allocate device memory (a framework that owns all device
 memory through its own pool, or a latency-bound loop where cudaMalloc and
 cudaFree are not allowed) use gvt_matvec_static, whose scratch is a fixed
 static device array.  This file checks, through the C ABI, that two calls in
-a row agree with the existing gvt_matvec (plan + handle) within the tolerances
-of the other parity tests (1e-10 FP64, 1e-5 FP32, normwise), that the shared
-array is cleared between calls, and that requests beyond its size are
-refused.  It is named so that pytest collects it last.
+a row agree with the FP64 oracle's product and with the existing gvt_matvec
+(plan + handle) within the tolerances of the other parity tests (1e-10 FP64,
+1e-5 FP32, normwise), that the shared array is cleared between calls, that a
+call leaves the device's free memory and torch's allocation unchanged, and
+that requests beyond its size are refused.  It is named so that pytest
+collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle as orc
 from paper_2009_01054_gb300 import gvt, synth
 
 torch = pytest.importorskip("torch")
@@ -24,16 +27,24 @@ def normwise(u, ref):
     return float(np.max(np.abs(u - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
 
-def _static(M, N, d, t, do, to, v, m_shape, q_shape, sym=True):
+def _static(M, N, d, t, do, to, v, m_shape, q_shape, sym=True, check_memory=False):
+    """One call through the C ABI into a preallocated output; with check_memory, the device's free
+    bytes and torch's allocated bytes are read right before and after the call itself."""
     u = torch.empty(do.numel() if do is not None else d.numel(), dtype=v.dtype, device="cuda")
+    mats = (gvt.matrix(M, sym), gvt.matrix(N, sym))
+    torch.cuda.synchronize()
+    before = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()) if check_memory else None
     gvt.gvt_matvec_static(m_shape[0], m_shape[1], q_shape[0], q_shape[1],
                           gvt.ptr(d), gvt.ptr(t), d.numel(),
                           gvt.ptr(do) if do is not None else None,
                           gvt.ptr(to) if to is not None else None,
                           do.numel() if do is not None else 0,
-                          gvt.matrix(M, sym), gvt.matrix(N, sym), gvt.ptr(v), gvt.ptr(u),
+                          mats[0], mats[1], gvt.ptr(v), gvt.ptr(u),
                           gvt.dtype_code(v), gvt.stream_ptr())
     torch.cuda.synchronize()
+    if check_memory:
+        after = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated())
+        assert after == before, (before, after)   # the call allocated no device memory
     return u.double().cpu().numpy()
 
 
@@ -75,10 +86,19 @@ def test_static_matches_planned_matvec_twice(dtype, case):
                    gvt.dtype_code(vv), gvt.stream_ptr())
     torch.cuda.synchronize()
     ref = ref.double().cpu().numpy()
+    # the oracle's product on the same (dtype-rounded) kernel matrices and v, in FP64
+    d_o = d if do is None else do
+    t_o = t if to is None else to
+    oref = orc.pairwise_matvec("kronecker", M.double().cpu().numpy(), N.double().cpu().numpy(),
+                               d_o, t_o, d, t, vv.double().cpu().numpy())
     u1 = _static(M, N, dd, tt, ddo, tto, vv, tuple(M.shape), tuple(N.shape), sym)
-    u2 = _static(M, N, dd, tt, ddo, tto, vv, tuple(M.shape), tuple(N.shape), sym)
+    u2 = _static(M, N, dd, tt, ddo, tto, vv, tuple(M.shape), tuple(N.shape), sym, check_memory=True)
+    print("%s %s: static vs oracle %.2e / %.2e, vs gvt_matvec %.2e" %
+          (case, dtype, normwise(u1, oref), normwise(u2, oref), normwise(u1, ref)))
+    assert normwise(u1, oref) <= TOL[dtype]
+    assert normwise(u2, oref) <= TOL[dtype]     # second call: the shared array was cleared
     assert normwise(u1, ref) <= TOL[dtype]
-    assert normwise(u2, ref) <= TOL[dtype]      # second call: the shared array was cleared
+    assert normwise(u2, ref) <= TOL[dtype]
     plan.close()
     H.close()
 
