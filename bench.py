@@ -1,26 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the generalized vec trick (GVT) path on one GB300 per rank.
 
-Workload (the homogeneous drug-drug configuration): m = q = 2000 objects,
-64-d N(0,1) features, Gaussian base kernel (gamma = 1/64), n = 200k ordered
-pairs drawn uniformly without replacement, v ~ N(0,1), FP32 on the GPU.
-One step applies all nine pairwise kernels of Table 4b (Kronecker, Gaussian,
-linear, poly2d, Cartesian, symmetric, anti-symmetric, ranking, MLPK; 27
-Kronecker terms of Corollary 1) to v over the training pairs: 9 calls of
+Headline workload (the kernel-filling scale, the largest configuration): m = q = 20000 objects
+on each side, 256-d N(0,1) features, Gaussian base kernels M and N (gamma = 1/256), n = 10M
+training pairs with power-law degrees (Zipf 1.1 weights on drug and target ids), v ~ N(0,1),
+FP32 on the GPU.  One step is one product u = R (M kron N) R^T v of the Gaussian pairwise
+kernel of Table 4b (one Kronecker term of Corollary 1) over the training pairs: one call of
 gvt_pairwise_kernel_matvec through the C ABI.
 
-value = pair-terms/s = sum over kernels of n * nhat * T_kernel / step time
-(implicit kernel-matrix entries applied per second).  L2 is flushed (512 MB
-write) before every timed step, outside the per-step CUDA events.
+value = pair-terms/s = n * nhat * T / step time (T Kronecker terms; implicit kernel-matrix
+entries applied per second).  The kernel matrices (1.6 GB each in FP32) exceed L2, and L2 is
+also flushed (512 MB write) before every timed step, outside the per-step CUDA events.
 
-Also reported: the roofline of the dominant stage (live CUDA events around
-each stage launch), the FP64 oracle on the host cores (cpu_baseline), an
-end-to-end number through the same API with host buffers, SM clocks during
-the timed region, and the KRR solve time (FP64 CG vs mixed-precision
-refinement) on the Merget-shaped problem.
+roofline: the dominant kernel's algorithmic work per launch (2 qbar n flops for stage 1 and
+2 m nhat for stage 2 per Kronecker term, counting only the pairs the launch serves) over its
+CUDA-event duration, against the measured peak of its arithmetic.  The dense tensor-core GEMM's
+executed flops are reported apart as `tensor_pipe`.
 
---impl reference times the FP64 oracle (plain C, OpenMP) on the host cores on
-a bounded sample of the same workload.
+Other sections of the JSON line: all nine kernels of Table 4b on the homogeneous 2000-object
+configuration (`all_kernels`), the FP64 oracle on the host cores (`cpu_baseline`), an
+end-to-end number through the same API with host buffers (`e2e`), SM clocks during the timed
+region, KRR solves on the Merget-shaped problem (`solve`), solves at the kernel-filling scale
+(`c5_solve`), the batched solve (`batched`) and the tcgen05 GEMM alone (`tensor_stage1_gemm`).
+
+--impl reference times the FP64 oracle (plain C, OpenMP) on the host cores on a bounded sample
+of the same workload (sampled output rows, each against all input pairs).
 """
 import argparse
 import hashlib
@@ -41,20 +45,35 @@ TERMS = {"kronecker": 1, "gaussian": 1, "linear": 2, "poly2d": 3, "cartesian": 2
          "symmetric": 2, "antisymmetric": 2, "ranking": 4, "mlpk": 10}
 METRIC = "GVT pair-terms/s and KRR-CG solve time at rel. residual 1e-6 vs plain FP64 CG"
 UNIT = "pair-terms/s"
-WORKLOAD = ("homogeneous drug-drug: m=q=2000, 64-d features, Gaussian base kernel gamma=1/64, "
-            "n=200k uniform ordered pairs, all 9 pairwise kernels (27 Kronecker terms), FP32")
+WORKLOADS = {
+    "c5": ("kernel-filling scale: m=q=20000, 256-d features, Gaussian base kernels gamma=1/256, "
+           "n=10M pairs with Zipf(1.1) degrees, Gaussian pairwise kernel (1 Kronecker term), FP32"),
+    "c2": ("homogeneous drug-drug: m=q=2000, 64-d features, Gaussian base kernel gamma=1/64, "
+           "n=200k uniform ordered pairs, all 9 pairwise kernels (27 Kronecker terms), FP32"),
+}
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP64: the nominal GB300 rate (no measured figure exists for it)
 FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gvt", choices=["gvt", "reference"])
+    ap.add_argument("--headline", default="c5", choices=["c5", "c2"],
+                    help="workload of `value`: c5 = kernel-filling scale (10M Zipf pairs, Gaussian kernel); "
+                         "c2 = homogeneous 2000 objects, all nine kernels")
+    ap.add_argument("--no-all-kernels", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-c5-solve", action="store_true")
+    ap.add_argument("--c5-fp64-cg", action="store_true",
+                    help="also run plain FP64 CG at the kernel-filling scale (lambda = 1); minutes of GPU time")
+    ap.add_argument("--c5-bounded-iters", type=int, default=240,
+                    help="inner-iteration cap of the bounded lambda = 1e-2 attempt at the kernel-filling scale "
+                         "(0: skip it)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--engine", default="auto", choices=["simt", "tc", "tc16", "auto"],
@@ -62,15 +81,16 @@ def parse():
                          "GEMM; tc16 = both stages as tcgen05 FP16x3 GEMMs; auto = per-stage cost model")
     ap.add_argument("--streams", type=int, default=3,
                     help="streams (each with its own handle and plan) over which the nine independent "
-                         "products of a step are spread")
+                         "products of an all-kernels step are spread")
     ap.add_argument("--tc-pairs", default="auto", choices=["auto", "off", "on"],
                     help="tile form of the tensor-core GEMM: auto = the library's choice (one SM per tile); "
                          "off = one SM per 128-row tile; on = SM pairs (256-row tiles, tcgen05 cta_group::2)")
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=256)
-    ap.add_argument("--batched-sample", type=int, default=8,
-                    help="problems of the plain FP64 CG comparison run system by system (0: skip it)")
+    ap.add_argument("--batched-sample", type=int, default=32,
+                    help="problems (every k-th of the set) solved both batched and by plain FP64 CG system by "
+                         "system, for the measured speed-up (0: skip the comparison)")
     return ap.parse_args()
 
 
@@ -100,13 +120,17 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def workload(seed):
+def workload(name, seed):
     from paper_2009_01054_gb300 import synth
-    return synth.homogeneous(seed)
+    return synth.zipf(seed, labels=True) if name == "c5" else synth.homogeneous(seed)
 
 
-def pair_terms_per_step(n):
-    return float(n) * float(n) * sum(TERMS.values())
+def kinds_of(name):
+    return ["gaussian"] if name == "c5" else KINDS
+
+
+def pair_terms_per_step(n, kinds):
+    return float(n) * float(n) * sum(TERMS[k] for k in kinds)
 
 
 # --------------------------------------------------------------------- clocks
@@ -163,24 +187,44 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- oracle (CPU)
-def cpu_oracle_rate(p, seconds, rows_per_call=64, seed=0, nthreads=0):
+def oracle_rows(p, kinds, idx, v, nthreads=0):
+    """The FP64 oracle's products at output rows idx (each against all input pairs).  The
+    heterogeneous problem evaluates only the kernel rows those outputs need; the homogeneous
+    one (2000 objects) evaluates its whole kernel matrix."""
+    import numpy as np
+    import oracle as orc
+    out = {}
+    if p.homogeneous:
+        M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
+        for kind in kinds:
+            out[kind] = orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, v, nthreads=nthreads)
+        return out
+    ud, id_ = np.unique(p.d[idx], return_inverse=True)
+    ut, it_ = np.unique(p.t[idx], return_inverse=True)
+    Mo = orc.gaussian_kernel(p.Xd[ud], p.Xd, gamma=p.gamma, nthreads=nthreads)
+    No = orc.gaussian_kernel(p.Xt[ut], p.Xt, gamma=p.gamma, nthreads=nthreads)
+    for kind in kinds:
+        out[kind] = orc.pairwise_matvec(kind, Mo, No, id_.astype(np.int32), it_.astype(np.int32), p.d, p.t, v,
+                                        nthreads=nthreads)
+    return out
+
+
+def cpu_oracle_rate(p, kinds, seconds, rows_per_call=64, seed=0, nthreads=0):
     """FP64 oracle pair-terms/s on sampled output rows (each row against all inputs); nthreads = 0
     uses every host core."""
     import numpy as np
     import oracle as orc
-    M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
     rng = np.random.default_rng(seed)
     rows_done = 0
     t0 = time.perf_counter()
     while True:
         idx = rng.choice(p.n, rows_per_call, replace=False)
-        for kind in KINDS:
-            orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, p.v, nthreads=nthreads)
+        oracle_rows(p, kinds, idx, p.v, nthreads=nthreads)
         rows_done += rows_per_call
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    rate = rows_done * float(p.n) * sum(TERMS.values()) / el
+    rate = rows_done * float(p.n) * sum(TERMS[k] for k in kinds) / el
     return rate, el, rows_done, (orc.num_threads() if nthreads == 0 else nthreads)
 
 
@@ -203,8 +247,10 @@ def cpu_oracle_small_solve():
 DTYPE_OF_ENGINE = {"simt": "f32", "tc": "bf16x3 stage 1 + f32 stage 2", "tc16": "f16x3 (f32 accumulate)",
                    "auto": "f16x3 (f32 accumulate) where dense, else f32"}
 
-KERNEL_SOURCE = {"stage1_dense_kernel": "stages.cu", "stage2_dense_kernel": "stages.cu",
+KERNEL_SOURCE = {"stage1_sparse_kernel": "stages.cu", "stage2_gather_kernel": "stages.cu",
                  "gemv_rows_multi_vec_kernel": "stages.cu", "tc_gemm_kernel": "tc_gemm.cu"}
+KERNEL_OF_STAT = {"sparse_stage1": "stage1_sparse_kernel", "sparse_stage2": "stage2_gather_kernel",
+                  "one_sided": "gemv_rows_multi_vec_kernel", "tc_gemm": "tc_gemm_kernel"}
 
 
 def kernel_text(kernel_name):
@@ -230,9 +276,9 @@ def kernel_text(kernel_name):
     return None
 
 
-def traffic_for(kernel_name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the kernel as its source
-    reads now (the record keeps the sha256 of the kernel's definition)."""
+def traffic_for(kernel_name, workload_name):
+    """DRAM bytes per launch from a committed ncu summary of this workload, if it was taken on the
+    kernel as its source reads now (the record keeps the sha256 of the kernel's definition)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -240,9 +286,73 @@ def traffic_for(kernel_name):
         text = kernel_text(kernel_name)
         if not rec or text is None or rec.get("kernel_sha256") != hashlib.sha256(text.encode()).hexdigest():
             return None
-        return rec.get("dram_bytes_per_launch")
+        per = rec.get("dram_bytes_per_launch")
+        return per.get(workload_name) if isinstance(per, dict) else None
     except Exception:
         return None
+
+
+def roofline(stats, K, peaks, peak_src, elem_bytes, workload_name):
+    """Roofline of the dominant kernel (largest summed device time among the tensor-core GEMM,
+    the sparse stage-1 kernel, the sampled gather-dot kernel and the one-sided pass) from the
+    library's per-launch CUDA events.  achieved = the method's algorithmic work per launch
+    (`useful_flops`, SURVEY-defined units: 2 qbar n per stage-1 term, 2 m nhat per stage-2 term)
+    / the launch's average duration."""
+    cand = [k for k in ("tc_gemm", "sparse_stage1", "sparse_stage2", "one_sided") if stats[k]["launches"] > 0]
+    if not cand:
+        return None, None
+    dom = max(cand, key=lambda k: stats[k]["ms"])
+    st = stats[dom]
+    L = st["launches"]
+    ms_l = st["ms"] / L
+    useful_l = st["useful_flops"] / L
+    bytes_l = st["bytes"] / L
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    kname = KERNEL_OF_STAT[dom]
+    roof = {"kernel": kname, "launches_per_step": L / K, "ms_per_launch": ms_l,
+            "algorithmic_flops_per_launch": useful_l, "algorithmic_bytes_per_launch": bytes_l,
+            "traffic": traffic_for(kname, workload_name)}
+    tensor_pipe = None
+    if dom == "tc_gemm":
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        ach = useful_l / (ms_l / 1e3) / 1e12
+        roof.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                     "peak_source": peak_src + " bf16 burst (fp16 at the nominal ratio 1)",
+                     "note": "achieved counts the GVT flops of the pairs the GEMM serves (2 qbar n or 2 m nhat "
+                             "per term), not the GEMM's own"})
+        exe = st["flops"] / L / (ms_l / 1e3) / 1e12
+        tensor_pipe = {"kernel": kname, "executed_tflops": exe, "peak": bf16, "frac": exe / bf16,
+                       "useful_share": st["useful_flops"] / max(st["flops"], 1.0),
+                       "note": "executed flops of the split GEMM (2 M N K, K = 3 x the 64-rounded inner length: "
+                               "hi*hi + hi*lo + lo*hi) per launch"}
+    else:
+        peak_alu = FP32_PEAK_TFLOPS if elem_bytes == 4 else FP64_PEAK_TFLOPS
+        ridge = peak_alu * 1e12 / (hbm * 1e9)
+        if useful_l / max(bytes_l, 1.0) > ridge:
+            ach = useful_l / (ms_l / 1e3) / 1e12
+            roof.update({"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
+                         "frac": ach / peak_alu,
+                         "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if elem_bytes == 4
+                                         else "nominal GB300 FP64 rate")})
+        else:
+            ach = bytes_l / (ms_l / 1e3) / 1e9
+            roof.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "peak_source": peak_src})
+        roof["hbm_frac"] = (bytes_l / (ms_l / 1e3) / 1e9) / hbm
+    return roof, tensor_pipe
+
+
+def stage_summary(stats, K):
+    out = {}
+    for k, st in stats.items():
+        if st["launches"] == 0:
+            continue
+        out[k] = {"launches_per_step": st["launches"] / K, "ms_per_step": st["ms"] / K,
+                  "useful_tflops": st["useful_flops"] / max(st["ms"], 1e-9) / 1e9,
+                  "algorithmic_gbs": st["bytes"] / max(st["ms"], 1e-9) / 1e6}
+        if st["flops"] != st["useful_flops"]:
+            out[k]["executed_tflops"] = st["flops"] / max(st["ms"], 1e-9) / 1e9
+    return out
 
 
 # --------------------------------------------------------------------- reference arm
@@ -253,15 +363,14 @@ def run_reference(args, ws, rank):
     import oracle as orc
     from oracle.build import build_oracle
     build_oracle()
-    p = workload(0)
-    M = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
-    rows = 256
+    p = workload(args.headline, 0)
+    kinds = kinds_of(args.headline)
+    rows = 64
     rng = np.random.default_rng(0)
 
     def step():
         idx = rng.choice(p.n, rows, replace=False)
-        for kind in KINDS:
-            orc.pairwise_matvec(kind, M, M, p.d[idx], p.t[idx], p.d, p.t, p.v)
+        oracle_rows(p, kinds, idx, p.v)
 
     for _ in range(args.warmup):
         step()
@@ -270,13 +379,14 @@ def run_reference(args, ws, rank):
         step()
     el = time.perf_counter() - t0
     ms = el / max(args.steps, 1) * 1e3
-    val = rows * float(p.n) * sum(TERMS.values()) / (ms / 1e3)
-    sample = "%d sampled output pairs per step, each against all %d input pairs, 9 kernels" % (rows, p.n)
+    val = rows * float(p.n) * sum(TERMS[k] for k in kinds) / (ms / 1e3)
+    sample = ("%d sampled output pairs per step, each against all %d input pairs, %d kernel(s), the kernel "
+              "rows they need evaluated per step" % (rows, p.n, len(kinds)))
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD + " (FP64 oracle, CPU)", "m": p.m, "n": p.n,
-                      "kernels": KINDS, "sample": sample},
+           "config": {"workload": WORKLOADS[args.headline] + " (FP64 oracle, CPU)", "m": p.m, "q": p.q,
+                      "n": p.n, "kernels": kinds, "sample": sample},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -284,8 +394,183 @@ def run_reference(args, ws, rank):
 
 
 # --------------------------------------------------------------------- GPU arm
-def run_gvt(args, ws, rank, local):
+class Products:
+    """The products of one workload: `kinds` applied to v over the training pairs, spread over
+    `nstreams` streams (each with a handle and plan of its own)."""
+
+    def __init__(self, gvt, torch, dev, p, kinds, nstreams, engine_code, pair_code):
+        self.gvt, self.torch, self.p, self.kinds = gvt, torch, p, kinds
+        S = max(1, min(nstreams, len(kinds)))
+        self.handles = [gvt.Handle() for _ in range(S)]
+        H = self.handles[0]
+        Xd = torch.as_tensor(p.Xd, device=dev)
+        self.M = gvt.gaussian_kernel(H, Xd, gamma=p.gamma, dtype=torch.float32)
+        self.N = self.M if p.homogeneous else gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=dev), gamma=p.gamma,
+                                                                  dtype=torch.float32)
+        del Xd
+        self.plans = [gvt.Plan(h, (p.m, p.m), (p.q, p.q), p.d, p.t) for h in self.handles]
+        self.v = torch.as_tensor(p.v, dtype=torch.float32, device=dev)
+        self.U = torch.empty((len(kinds), p.n), dtype=torch.float32, device=dev)
+        self.descs = [gvt.gvt_desc_make(k) for k in kinds]
+        self.Mm = gvt.matrix(self.M, symmetric=True)
+        self.Nm = gvt.matrix(self.N, symmetric=True)
+        self.stream = torch.cuda.current_stream()
+        self.streams = [self.stream] + [torch.cuda.Stream() for _ in range(S - 1)]
+        self.sps = [gvt.stream_ptr(st) for st in self.streams]
+        self.vp = gvt.ptr(self.v)
+        self.up = [gvt.ptr(self.U[i]) for i in range(len(kinds))]
+        self.fork = torch.cuda.Event()
+        self.joins = [torch.cuda.Event() for _ in range(S)]
+        self.S = S
+        for h in self.handles:
+            gvt.gvt_set_tc_pairs(h.h, pair_code)
+        self.set_engine(engine_code)
+
+    def set_engine(self, code):
+        for h in self.handles:
+            self.gvt.gvt_set_stage1_engine(h.h, code)
+
+    def step(self, nstreams=None, after=None):
+        gvt = self.gvt
+        ns = self.S if nstreams is None else nstreams
+        # the products of one step on one handle share the split copies of the kernel matrices:
+        # each handle splits them once per step (the scope ends with the step)
+        for h in self.handles:
+            gvt.gvt_factor_cache_begin(h.h)
+        if ns > 1:
+            self.fork.record(self.stream)
+            for st in self.streams[1:ns]:
+                st.wait_event(self.fork)
+        for i, d in enumerate(self.descs):
+            j = i % ns
+            gvt.gvt_pairwise_kernel_matvec(self.plans[j].p, d, self.Mm, self.Nm, self.vp, self.up[i], 1,
+                                           gvt.GVT_F32, self.sps[j])
+            if after is not None:
+                after(i, self.streams[j])
+        for j in range(1, ns):
+            self.joins[j].record(self.streams[j])
+            self.stream.wait_event(self.joins[j])
+        for h in self.handles:
+            gvt.gvt_factor_cache_end(h.h)
+
+    def close(self):
+        for pl in self.plans:
+            pl.close()
+        for h in self.handles:
+            h.close()
+
+
+def time_steps(torch, step, K, flush, stream):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / K
+
+
+def bench_products(args, gvt, torch, dev, name, p, K, W, ws, dist, local, flush, peaks, peak_src, with_e2e):
+    """Timed steps of one workload: value, roofline, stage summary, clocks, e2e, engines."""
+    engine_code = {"simt": gvt.GVT_STAGE1_SIMT, "tc": gvt.GVT_STAGE1_TC_BF16X3, "tc16": gvt.GVT_STAGES_TC_F16X3,
+                   "auto": gvt.GVT_STAGES_AUTO}[args.engine]
+    pair_code = {"auto": gvt.GVT_TC_PAIRS_AUTO, "off": gvt.GVT_TC_PAIRS_OFF, "on": gvt.GVT_TC_PAIRS_ON}[args.tc_pairs]
+    kinds = kinds_of(name)
+    pr = Products(gvt, torch, dev, p, kinds, args.streams, engine_code, pair_code)
+    for _ in range(max(W, 3)):
+        pr.step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    l0 = gvt.gvt_launch_count()
+    step_ms = time_steps(torch, pr.step, K, flush, pr.stream)
+    launches = gvt.gvt_launch_count() - l0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    # the same K steps again on one stream with the library's per-launch CUDA events on (kept out
+    # of the timed steps above so that `value` carries no instrumentation): the roofline's launch
+    # durations are each launch's own, not shared with another stream's
+    H = pr.handles[0]
+    gvt.gvt_stats_enable(H.h, True)
+    for _ in range(K):
+        flush.zero_()
+        pr.step(nstreams=1)
+    torch.cuda.synchronize()
+    stats = gvt.gvt_stats_read(H.h)
+    gvt.gvt_stats_enable(H.h, False)
+    pts = pair_terms_per_step(p.n, kinds)
+    step_ms_max, value = job_rate(step_ms, pts, ws, dist, dev)
+    roof, tpipe = roofline(stats, K, peaks, peak_src, 4, name)
+    res = {"workload": WORKLOADS[name], "m": p.m, "q": p.q, "n": p.n, "nhat": p.n, "kernels": kinds,
+           "kronecker_terms": sum(TERMS[k] for k in kinds), "pair_terms_per_step": pts,
+           "ms_per_step": step_ms_max, "value": value, "unit": UNIT, "streams": pr.S,
+           "gpu_launches": launches, "clocks": clk, "roofline": roof, "tensor_pipe": tpipe,
+           "stages": stage_summary(stats, K)}
+    if with_e2e:
+        # end to end through the same API with host buffers: v in from pinned memory, each kernel's
+        # result back to pinned memory on a copy stream while the next products run
+        vh = torch.as_tensor(p.v, dtype=torch.float32).pin_memory()
+        Uh = torch.empty((len(kinds), p.n), dtype=torch.float32).pin_memory()
+        copy_stream = torch.cuda.Stream()
+        done = [torch.cuda.Event() for _ in kinds]
+
+        def copy_back(i, st):
+            done[i].record(st)
+            copy_stream.wait_event(done[i])
+            with torch.cuda.stream(copy_stream):
+                Uh[i].copy_(pr.U[i], non_blocking=True)
+
+        def step_e2e():
+            pr.v.copy_(vh, non_blocking=True)
+            pr.step(after=copy_back)
+            pr.stream.wait_stream(copy_stream)
+
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        Ke = max(10, K // 2)
+        e2e_ms = time_steps(torch, step_e2e, Ke, flush, pr.stream)
+        assert torch.equal(Uh[-1], pr.U[-1].cpu())
+        e2e_ms_max, e2e_value = job_rate(e2e_ms, pts, ws, dist, dev)
+        res["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(vh.numel() * 4),
+                      "d2h_bytes_per_step": int(Uh.numel() * 4), "ms_per_step": e2e_ms_max}
+    # the same steps on the FP32 SIMT engine, for comparison (device-timed like `value`)
+    if args.engine != "simt":
+        pr.set_engine(gvt.GVT_STAGE1_SIMT)
+        for _ in range(2):
+            pr.step()
+        torch.cuda.synchronize()
+        simt_ms = time_steps(torch, pr.step, max(3, min(K, 10)), flush, pr.stream)
+        res["engines"] = {"simt_f32": {"ms_per_step": simt_ms, "value": ws * pts / (simt_ms / 1e3), "unit": UNIT},
+                          args.engine: {"ms_per_step": step_ms_max, "value": value, "unit": UNIT}}
+        pr.set_engine(engine_code)
+    return pr, res
+
+
+def sampled_error(gvt, torch, pr, p, kinds, rows=64):
+    """Normwise error of the FP32 products vs the FP64 oracle on sampled output rows."""
     import numpy as np
+    idx = np.random.default_rng(1).choice(p.n, rows, replace=False)
+    pr.step(nstreams=1)
+    torch.cuda.synchronize()
+    ref = oracle_rows(p, kinds, idx, p.v.astype(np.float32).astype(np.float64))
+    out = {}
+    for i, kind in enumerate(kinds):
+        u = pr.U[i].double().cpu().numpy()
+        out[kind] = float(np.max(np.abs(u[idx] - ref[kind])) / np.max(np.abs(ref[kind])))
+    out["max"] = max(out.values())
+    out["sample"] = "%d output rows, normwise max|u - u*| / max|u*|, FP64 oracle on the FP32-rounded v" % rows
+    out["fp32_tolerance"] = 1e-5
+    return out
+
+
+def run_gvt(args, ws, rank, local):
     import torch
 
     from paper_2009_01054_gb300 import build as gbuild
@@ -304,273 +589,79 @@ def run_gvt(args, ws, rank, local):
     if local != 0:
         gbuild.build()
     dev = torch.device("cuda", local)
-    p = workload(rank)
-    H = gvt.Handle()
-    X = torch.as_tensor(p.Xd, device=dev)
-    M = gvt.gaussian_kernel(H, X, gamma=p.gamma, dtype=torch.float32)
-    plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
-    v = torch.as_tensor(p.v, dtype=torch.float32, device=dev)
-    U = torch.empty((len(KINDS), p.n), dtype=torch.float32, device=dev)
-    descs = [gvt.gvt_desc_make(k) for k in KINDS]
-    Mm = gvt.matrix(M, symmetric=True)
-    sp = gvt.stream_ptr()
-    engine_code = {"simt": gvt.GVT_STAGE1_SIMT, "tc": gvt.GVT_STAGE1_TC_BF16X3, "tc16": gvt.GVT_STAGES_TC_F16X3,
-                   "auto": gvt.GVT_STAGES_AUTO}[args.engine]
-    stream = torch.cuda.current_stream()
-    vp = gvt.ptr(v)
-    up = [gvt.ptr(U[i]) for i in range(len(KINDS))]
-    # the nine products are independent: with S streams, product i runs on stream i % S with a
-    # handle and plan of its own, forked from and joined back into the main stream
-    S = max(1, args.streams)
-    extra_h = [gvt.Handle() for _ in range(S - 1)]
-    handles = [H] + extra_h
-    plans = [plan] + [gvt.Plan(h, (p.m, p.m), (p.m, p.m), p.d, p.t) for h in extra_h]
-    streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
-    sps = [sp] + [gvt.stream_ptr(st) for st in streams[1:]]
-    fork = torch.cuda.Event()
-    joins = [torch.cuda.Event() for _ in range(S)]
-
-    def set_engine(code):
-        for h in handles:
-            gvt.gvt_set_stage1_engine(h.h, code)
-
-    pair_code = {"auto": gvt.GVT_TC_PAIRS_AUTO, "off": gvt.GVT_TC_PAIRS_OFF, "on": gvt.GVT_TC_PAIRS_ON}
-    for h in handles:
-        gvt.gvt_set_tc_pairs(h.h, pair_code[args.tc_pairs])
-
-    set_engine(engine_code)
-
-    def step(nstreams=S, after=None):
-        # the products of one step on one handle share the split copies of M: each handle splits
-        # it once per step (the scope ends with the step, so the next step splits again)
-        for h in handles:
-            gvt.gvt_factor_cache_begin(h.h)
-        if nstreams > 1:
-            fork.record(stream)
-            for st in streams[1:nstreams]:
-                st.wait_event(fork)
-        for i, d in enumerate(descs):
-            j = i % nstreams
-            gvt.gvt_pairwise_kernel_matvec(plans[j].p, d, Mm, Mm, vp, up[i], 1, gvt.GVT_F32, sps[j])
-            if after is not None:
-                after(i, streams[j])
-        for j in range(1, nstreams):
-            joins[j].record(streams[j])
-            stream.wait_event(joins[j])
-        for h in handles:
-            gvt.gvt_factor_cache_end(h.h)
-
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    l0 = gvt.gvt_launch_count()
-    for k in range(K):
-        flush.zero_()
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    launches = gvt.gvt_launch_count() - l0
-    barrier()
-    clk = clocks.stop()
-    # the same K steps again with the library's per-stage CUDA events on (kept out of the timed
-    # steps above so that `value` carries no instrumentation): the roofline's launch durations
-    # (one stream: each launch's event-bracketed duration is its own, not shared with another stream's)
-    gvt.gvt_stats_enable(H.h, True)
-    for k in range(K):
-        flush.zero_()
-        step(nstreams=1)
-    torch.cuda.synchronize()
-    stats = gvt.gvt_stats_read(H.h)
-    gvt.gvt_stats_enable(H.h, False)
-    step_ms = sum(a.elapsed_time(b) for a, b in ev) / K
-    pts = pair_terms_per_step(p.n)
-    step_ms_max, value = job_rate(step_ms, pts, ws, dist, dev)
-
-    # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
-    dom = max(("stage1", "stage2", "one_sided"), key=lambda k: stats[k]["ms"])
-    tg = stats["tc_gemm"]
-    if tg["launches"] > 0 and tg["ms"] >= max(stats[k]["ms"] for k in ("stage1", "stage2", "one_sided")) / 2:
-        # the dense engines: the split GEMM is the dominant kernel (its launches are a part of both
-        # stages' time); FP16 and BF16 run at the same nominal tensor rate, so the measured BF16 peak
-        # applies to the FP16 splits unchanged
-        bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        per_launch_ms = tg["ms"] / tg["launches"]
-        achieved = tg["flops"] / tg["ms"] / 1e9
-        useful = (stats["stage1"]["flops"] + stats["stage2"]["flops"]) / max(tg["flops"], 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
-                "frac": achieved / bf16, "peak_source": peak_src + " bf16 burst (fp16 nominal ratio 1)",
-                "kernel": "tc_gemm_kernel", "traffic": traffic_for("tc_gemm_kernel"),
-                "ms_per_launch": per_launch_ms, "launches_per_step": tg["launches"] // K,
-                "algorithmic_flops_per_launch": tg["flops"] / tg["launches"],
-                "algorithmic_bytes_per_launch": tg["bytes"] / tg["launches"],
-                "note": "flops of the split GEMM C = A' B'^T (2 M N K, K = 3 x the 64-rounded inner length: "
-                        "hi*hi + hi*lo + lo*hi); the stages' useful GVT flops are %.1f%% of them" % (100 * useful)}
-        dom = None
-    if dom is not None:
-        st = stats[dom]
-        per_launch_ms = st["ms"] / max(st["launches"], 1)
-        flops_l = st["flops"] / max(st["launches"], 1)
-        bytes_l = st["bytes"] / max(st["launches"], 1)
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        ridge = FP32_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
-        if flops_l / max(bytes_l, 1.0) > ridge:
-            achieved = flops_l / (per_launch_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-        else:
-            achieved = bytes_l / (per_launch_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "peak_source": peak_src}
-        kname = {"stage1": "stage1_dense_kernel", "stage2": "stage2_dense_kernel",
-                 "one_sided": "gemv_rows_multi_vec_kernel"}[dom]
-        roof.update({"kernel": kname, "traffic": traffic_for(kname), "ms_per_launch": per_launch_ms,
-                     "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
-                     "hbm_frac": (bytes_l / (per_launch_ms / 1e3) / 1e9) / hbm})
-    stage_summary = {k: {"launches": stats[k]["launches"] // K,
-                         "ms_per_step": stats[k]["ms"] / K,
-                         "tflops": (stats[k]["flops"] / max(stats[k]["ms"], 1e-9)) / 1e9,
-                         "gbs": (stats[k]["bytes"] / max(stats[k]["ms"], 1e-9)) / 1e6}
-                     for k in stats}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    K, W = args.steps, args.warmup
 
-    # ---- end to end through the same API with host buffers
-    vh = torch.as_tensor(p.v, dtype=torch.float32).pin_memory()
-    Uh = torch.empty((len(KINDS), p.n), dtype=torch.float32).pin_memory()
-    Ke = max(10, K // 5)
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
-    copy_stream = torch.cuda.Stream()
-    done = [torch.cuda.Event() for _ in KINDS]
+    head = args.headline
+    p = workload(head, rank)
+    pr, res = bench_products(args, gvt, torch, dev, head, p, K, W, ws, dist, local, flush, peaks, peak_src, True)
+    accuracy = sampled_error(gvt, torch, pr, p, kinds_of(head)) if rank == 0 else None
+    pr.close()
+    del pr
+    torch.cuda.empty_cache()
 
-    def copy_back(i, st):
-        done[i].record(st)
-        copy_stream.wait_event(done[i])
-        with torch.cuda.stream(copy_stream):
-            Uh[i].copy_(U[i], non_blocking=True)
+    others = {}
+    if not args.no_all_kernels and head != "c2":
+        p2 = workload("c2", rank)
+        pr2, r2 = bench_products(args, gvt, torch, dev, "c2", p2, K, W, ws, dist, local, flush, peaks, peak_src,
+                                 False)
+        if rank == 0:
+            r2["error_vs_fp64_oracle"] = sampled_error(gvt, torch, pr2, p2, KINDS)
+        pr2.close()
+        del pr2
+        torch.cuda.empty_cache()
+        others["all_kernels"] = r2
 
-    def step_e2e():
-        # v in from pinned memory; each kernel's result goes back on a copy stream while the
-        # next products run; the step ends when the last copy has landed
-        v.copy_(vh, non_blocking=True)
-        step(after=copy_back)
-        stream.wait_stream(copy_stream)
-
-    barrier()
-    torch.cuda.synchronize()
-    for k in range(Ke):
-        flush.zero_()
-        ev2[k][0].record(stream)
-        step_e2e()
-        ev2[k][1].record(stream)
-    torch.cuda.synchronize()
-    assert torch.equal(Uh[-1], U[-1].cpu())
-    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2) / Ke
-    e2e_ms_max, e2e_value = job_rate(e2e_ms, pts, ws, dist, dev)
-    e2e = {"value": e2e_value, "unit": UNIT,
-           "h2d_bytes_per_step": int(vh.numel() * 4), "d2h_bytes_per_step": int(Uh.numel() * 4),
-           "ms_per_step": e2e_ms_max}
-
-    # ---- the same steps on the FP32 SIMT engine, for comparison (device-timed like `value`)
-    engines = None
-    if args.engine != "simt":
-        set_engine(gvt.GVT_STAGE1_SIMT)
-        for _ in range(3):
-            step()
-        ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        torch.cuda.synchronize()
-        for k in range(K):
-            flush.zero_()
-            ev3[k][0].record(stream)
-            step()
-            ev3[k][1].record(stream)
-        torch.cuda.synchronize()
-        simt_ms = sum(a.elapsed_time(b) for a, b in ev3) / K
-        engines = {"simt_f32": {"ms_per_step": simt_ms, "value": ws * pts / (simt_ms / 1e3), "unit": UNIT},
-                   args.engine: {"ms_per_step": step_ms_max, "value": value, "unit": UNIT}}
-        set_engine(engine_code)
-
-    # ---- KRR solve: plain FP64 CG vs mixed-precision refinement
-    accuracy = None
-    if rank == 0:
-        accuracy = sampled_error(p, M, plan, gvt, torch, dev)
-        accuracy["fp32_tolerance"] = 1e-5
-    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    H = gvt.Handle()
     tc_gemm = bench_tc_gemm(H, gvt, torch, dev, peaks) if rank == 0 else None
     solve = None
     if not args.no_solve and rank == 0:
         solve = bench_solve(H, gvt, torch, dev, [float(x) for x in args.solve_lambdas.split(",")])
+    c5_solve = None
+    if not args.no_c5_solve and rank == 0:
+        c5_solve = bench_c5_solve(H, gvt, torch, dev, p if head == "c5" else workload("c5", 0), args)
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(H, gvt, torch, dev, args.batched_problems, args.batched_sample)
+    H.close()
 
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
-        rate, el, rows, cores = cpu_oracle_rate(p, args.cpu_seconds)
-        rate1, el1, rows1, _ = cpu_oracle_rate(p, min(3.0, args.cpu_seconds), nthreads=1)
+        kinds = kinds_of(head)
+        rate, el, rows, cores = cpu_oracle_rate(p, kinds, args.cpu_seconds)
+        rate1, el1, rows1, _ = cpu_oracle_rate(p, kinds, min(3.0, args.cpu_seconds), rows_per_call=8, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d sampled output pairs x all %d input pairs x 9 kernels, FP64, %.1f s"
-                         % (rows, p.n, el),
+               "sample": "%d sampled output pairs x all %d input pairs x %d kernel(s), FP64, %.1f s"
+                         % (rows, p.n, len(kinds), el),
                "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
                                "sample": "%d sampled output pairs, %.1f s" % (rows1, el1)},
                "small_solve": cpu_oracle_small_solve()}
 
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
-               "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
+        cfg = {k: res[k] for k in ("workload", "m", "q", "n", "nhat", "kernels", "kronecker_terms",
+                                   "pair_terms_per_step", "streams")}
+        cfg.update({"l2": "inputs larger than L2 (the kernel matrices are 1.6 GB each in FP32) and L2 flushed "
+                          "(512 MB write) before every timed step, outside the events"
+                          if head == "c5" else
+                          "flushed (512 MB write) before every timed step, outside the events",
+                    "tc_pairs": args.tc_pairs,
+                    "roofline_timing": "per-launch CUDA events of the library, over a second pass of the same K "
+                                       "steps on one stream (the timed pass runs without them)",
+                    "parallelism": "replicas: independent problems per rank (seed = rank)"})
+        out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": ws, "steps": K,
+               "warmup": W, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_OF_ENGINE[args.engine], "data": "synthetic",
-               "config": {"workload": WORKLOAD, "m": p.m, "q": p.m, "n": p.n, "nhat": p.n,
-                          "kernels": KINDS, "kronecker_terms": sum(TERMS.values()),
-                          "pair_terms_per_step": pts,
-                          "l2": "flushed (512 MB write) before every timed step, outside the events",
-                          "streams": S, "tc_pairs": args.tc_pairs,
-                          "kernel_matrix_splits": "once per step per stream (gvt_factor_cache_begin/end "
-                                                  "around each step)",
-                          "roofline_timing": "per-stage CUDA events of the library, over a second pass of the same "
-                                             "K steps (the timed pass runs without them)",
-                          "parallelism": "replicas: independent problems per rank (seed = rank)"},
-               "roofline": roof, "stages": stage_summary, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clk, "gpu_launches": launches,
-               "engine": args.engine, "engines": engines,
+               "config": cfg, "roofline": res["roofline"], "tensor_pipe": res["tensor_pipe"],
+               "stages": res["stages"], "cpu_baseline": cpu, "e2e": res.get("e2e"),
+               "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
+               "engine": args.engine, "engines": res.get("engines"),
                "error_vs_fp64_oracle": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve,
-               "batched": batched}
+               "c5_solve": c5_solve, "batched": batched}
+        out.update(others)
         print(json.dumps(out), flush=True)
-    for pl in plans:
-        pl.close()
-    for h in handles:
-        h.close()
     if dist is not None:
         dist.destroy_process_group()
-
-
-def sampled_error(p, M, plan, gvt, torch, dev, rows=64):
-    """Normwise error of the timed FP32 products vs the FP64 oracle on sampled output rows."""
-    import numpy as np
-    import oracle as orc
-    Mo = orc.gaussian_kernel(p.Xd, gamma=p.gamma)
-    idx = np.random.default_rng(1).choice(p.n, rows, replace=False)
-    v = torch.as_tensor(p.v, dtype=torch.float32, device=dev)
-    out = {}
-    for kind in KINDS:
-        u = gvt.pairwise_kernel_matvec(plan, kind, M, M, v).double().cpu().numpy()
-        ref = orc.pairwise_matvec(kind, Mo, Mo, p.d[idx], p.t[idx], p.d, p.t, p.v.astype(np.float32))
-        out[kind] = float(np.max(np.abs(u[idx] - ref)) / np.max(np.abs(ref)))
-    out["max"] = max(out.values())
-    out["sample"] = "%d output rows, normwise max|u - u*| / max|u*|" % rows
-    return out
 
 
 def bench_tc_gemm(H, gvt, torch, dev, peaks, reps=50):
@@ -600,6 +691,14 @@ def bench_tc_gemm(H, gvt, torch, dev, peaks, reps=50):
             "note": "includes launch and the split-K zeroing; small GEMM (16 x 1 output tiles x 10 K splits)"}
 
 
+def timed_solve(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, (time.perf_counter() - t0) * 1e3
+
+
 def bench_solve(H, gvt, torch, dev, lambdas):
     """Merget-shaped KRR (m=2000, q=250, n=120k, Kronecker kernel): wall time to FP64 rel.
     residual 1e-6 for plain FP64 CG, FP32-inner refinement, tensor-core-inner refinement, and
@@ -620,33 +719,23 @@ def bench_solve(H, gvt, torch, dev, lambdas):
         r = {}
         for name, mode, inner, engine in variants:
             gvt.gvt_set_stage1_engine(H.h, engine)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=2,
-                                           max_iter=20000, inner_dtype=inner)
-            torch.cuda.synchronize()
-            wall = (time.perf_counter() - t0) * 1e3
+            (a, st, info), wall = timed_solve(torch, lambda: gvt.krr_cg_solve(
+                H, plan, "kronecker", M, N, y, lam, mode=mode, check_every=2, max_iter=20000, inner_dtype=inner))
             gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
             r[name] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
                        "refinements": int(info.refinements), "rel_residual": info.rel_residual}
         # the paper's own solver (Sec. 6): FP64 MINRES to the same residual
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        a, st, info, _ = gvt.krr_minres_solve(H, plan, "kronecker", M, N, y, lam, rel_tol=1e-6, max_iter=20000)
-        torch.cuda.synchronize()
-        r["fp64_minres"] = {"ms": (time.perf_counter() - t0) * 1e3, "status": gvt.STATUS_NAMES[st],
-                            "iterations": int(info.iterations), "rel_residual": info.rel_residual}
-        for name in ("mixed_ir_f32", "mixed_ir_tc_bf16x3", "mixed_ir_tc_f16x3"):
-            if r[name]["status"] == "GVT_OK" and r["fp64_cg"]["status"] == "GVT_OK":
+        (a, st, info, _), wall = timed_solve(torch, lambda: gvt.krr_minres_solve(
+            H, plan, "kronecker", M, N, y, lam, rel_tol=1e-6, max_iter=20000))
+        r["fp64_minres"] = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
+                            "rel_residual": info.rel_residual}
+        for name in r:
+            if name != "fp64_cg" and r[name]["status"] == "GVT_OK" and r["fp64_cg"]["status"] == "GVT_OK":
                 r[name]["speedup_vs_fp64_cg"] = r["fp64_cg"]["ms"] / r[name]["ms"]
         res["runs"]["lambda=%g" % lam] = r
     # the whole sweep from one Krylov space: multi-shift FP64 CG against the separate FP64 CG solves
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    A, st, info, rr = gvt.krr_cg_solve_multishift(H, plan, "kronecker", M, N, y, lambdas, rel_tol=1e-6,
-                                                  max_iter=20000)
-    torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1e3
+    (A, st, info, rr), ms = timed_solve(torch, lambda: gvt.krr_cg_solve_multishift(
+        H, plan, "kronecker", M, N, y, lambdas, rel_tol=1e-6, max_iter=20000))
     sep = sum(res["runs"]["lambda=%g" % lam]["fp64_cg"]["ms"] for lam in lambdas)
     res["fp64_cg_multishift_sweep"] = {"ms": ms, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
                                        "rel_residuals": rr, "fp64_cg_separate_ms": sep,
@@ -655,10 +744,71 @@ def bench_solve(H, gvt, torch, dev, lambdas):
     return res
 
 
-def bench_batched(H, gvt, torch, dev, n_probs, sample=8):
+def oracle_sampled_residual(p, a, lam, rows=200, seed=3):
+    """The oracle's FP64 residual r_i = y_i - (K a)_i - lam a_i at sampled rows i (each a sum over
+    all n pairs), and the estimate sqrt(n mean r_i^2) / ||y|| of the relative residual."""
+    import numpy as np
+    idx = np.sort(np.random.default_rng(seed).choice(p.n, rows, replace=False))
+    Ka = oracle_rows(p, ["gaussian"], idx, a)["gaussian"]
+    r = p.y[idx] - Ka - lam * a[idx]
+    est = float(np.sqrt(p.n * np.mean(r * r)) / np.linalg.norm(p.y))
+    return {"rows": rows, "estimated_rel_residual": est, "max_abs_residual": float(np.max(np.abs(r)))}
+
+
+def bench_c5_solve(H, gvt, torch, dev, p, args):
+    """Kernel ridge solves at the kernel-filling scale (m=q=20000, 10M Zipf pairs, Gaussian
+    kernel, FP64 M and N): at lambda = 1, mixed-precision refinement (FP32 inner operator on the
+    automatic engine) to FP64 rel. residual 1e-6, its residual re-checked by the oracle on sampled
+    rows, and (--c5-fp64-cg) plain FP64 CG; at lambda = 1e-2 a bounded attempt whose residual history
+    is reported."""
+    import numpy as np
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=dev), gamma=p.gamma)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    y = torch.as_tensor(p.y, device=dev)
+    res = {"workload": "kernel-filling scale: m=q=20000, 256-d, n=10M Zipf(1.1) pairs, Gaussian kernel, "
+                       "y = bilinear signal + N(0, 0.1^2)", "runs": {}}
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
+    try:
+        (a, st, info, hist), wall = timed_solve(torch, lambda: gvt.krr_cg_solve(
+            H, plan, "kronecker", M, N, y, 1.0, mode=gvt.GVT_SOLVE_MIXED_IR, check_every=2, max_iter=5000,
+            history=64))
+        r = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
+             "refinements": int(info.refinements), "rel_residual": info.rel_residual, "history": hist,
+             "inner": "FP32 CG, automatic engine (FP16x3 tensor-core stages where dense)"}
+        r["oracle_check"] = oracle_sampled_residual(p, a.cpu().numpy(), 1.0)
+        res["runs"]["lambda=1"] = {"mixed_ir": r}
+        if args.c5_fp64_cg:
+            gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+            (a2, st2, info2, hist2), wall2 = timed_solve(torch, lambda: gvt.krr_cg_solve(
+                H, plan, "kronecker", M, N, y, 1.0, check_every=5, max_iter=5000, history=256))
+            r2 = {"ms": wall2, "status": gvt.STATUS_NAMES[st2], "iterations": int(info2.iterations),
+                  "rel_residual": info2.rel_residual, "history": hist2[::4]}
+            res["runs"]["lambda=1"]["fp64_cg"] = r2
+            if st == 0 and st2 == 0:
+                r["speedup_vs_fp64_cg"] = wall2 / wall
+            gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
+        if args.c5_bounded_iters > 0:
+            (a3, st3, info3, hist3), wall3 = timed_solve(torch, lambda: gvt.krr_cg_solve(
+                H, plan, "kronecker", M, N, y, 1e-2, mode=gvt.GVT_SOLVE_MIXED_IR, check_every=2,
+                max_iter=args.c5_bounded_iters, history=64))
+            res["runs"]["lambda=0.01"] = {"mixed_ir_bounded": {
+                "ms": wall3, "status": gvt.STATUS_NAMES[st3], "iterations": int(info3.iterations),
+                "refinements": int(info3.refinements), "rel_residual": info3.rel_residual, "history": hist3,
+                "note": "bounded attempt: at most %d inner iterations" % args.c5_bounded_iters}}
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    plan.close()
+    del M, N
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_batched(H, gvt, torch, dev, n_probs, sample=32):
     """Batched uneven problems: n_probs KRR problems (m, q ~ U{32..512}, density ~ U[5%, 60%],
     32-d features, Kronecker of Gaussians) x 16 lambdas (logspace 1e-4..1) in one batched solve to
-    FP64 rel. residual 1e-6, against plain FP64 CG run system by system on a sample of problems."""
+    FP64 rel. residual 1e-6.  The speed-up over plain FP64 CG is measured on a stratified sample
+    (every k-th problem): the sample is solved batched, and by plain FP64 CG system by system."""
     from paper_2009_01054_gb300 import synth
     t0 = time.perf_counter()
     ps = synth.batched(n_probs)
@@ -673,40 +823,42 @@ def bench_batched(H, gvt, torch, dev, n_probs, sample=8):
     total_pairs = sum(p.n for p in ps)
     # first call includes the autotuner; time the second (tuned, cached) call
     gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    A, st, info, rr = gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6)
-    torch.cuda.synchronize()
-    batched_ms = (time.perf_counter() - t0) * 1e3
+    (A, st, info, rr), batched_ms = timed_solve(torch, lambda: gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6))
     worst = max(max(r) for r in rr)
-    # plain FP64 CG, one system at a time, on the first `sample` problems
-    t0 = time.perf_counter()
-    fp_iters, fp_worst, sample_pairs = 0, 0.0, 0
-    sample = max(0, sample)
-    for b in range(min(sample, len(ps))):
-        p = probs[b]
-        plan = gvt.Plan(H, tuple(p["M"].shape), tuple(p["N"].shape), p["d"], p["t"])
-        for lam in lambdas:
-            a, st2, inf2 = gvt.krr_cg_solve(H, plan, "kronecker", p["M"], p["N"], p["y"], lam, max_iter=50000,
-                                            check_every=2)
-            fp_iters += inf2.iterations
-            fp_worst = max(fp_worst, inf2.rel_residual)
-        sample_pairs += ps[b].n
-        plan.close()
-    torch.cuda.synchronize()
-    fp_ms = (time.perf_counter() - t0) * 1e3
-    est_full = fp_ms * total_pairs / max(sample_pairs, 1)
-    return {"workload": "%d problems, m,q ~ U{32..512}, density ~ U[5%%,60%%], 32-d, %d lambdas logspace(-4,0), "
-                        "%d pairs total, %d systems" % (len(ps), len(lambdas), total_pairs, len(ps) * len(lambdas)),
-            "batched_ms": batched_ms, "status": gvt.STATUS_NAMES[st], "inner_iterations": int(info.iterations),
-            "refinements": int(info.refinements), "max_rel_residual": worst,
-            "plain_fp64_cg_sample": {"problems": min(sample, len(ps)), "systems": min(sample, len(ps)) * len(lambdas),
-                                     "ms": fp_ms, "iterations": fp_iters, "max_rel_residual": fp_worst,
-                                     "pairs": sample_pairs},
-            "plain_fp64_cg_estimate_ms": est_full if sample_pairs else None,
-            "estimate_note": "plain FP64 CG time for all systems scaled from the sample by pair count",
-            "speedup_vs_plain_fp64_cg_estimate": est_full / batched_ms if sample_pairs else None,
-            "data_generation_s": gen_s}
+    out = {"workload": "%d problems, m,q ~ U{32..512}, density ~ U[5%%,60%%], 32-d, %d lambdas logspace(-4,0), "
+                       "%d pairs total, %d systems" % (len(ps), len(lambdas), total_pairs, len(ps) * len(lambdas)),
+           "batched_ms": batched_ms, "status": gvt.STATUS_NAMES[st], "inner_iterations": int(info.iterations),
+           "refinements": int(info.refinements), "max_rel_residual": worst, "data_generation_s": gen_s}
+    if sample > 0:
+        step = max(1, len(ps) // sample)
+        sel = list(range(0, len(ps), step))[:sample]
+        sub = [probs[b] for b in sel]
+        gvt.krr_solve_batched(H, sub, lambdas, rel_tol=1e-6)
+        (A2, st2, info2, rr2), sub_ms = timed_solve(torch, lambda: gvt.krr_solve_batched(H, sub, lambdas, rel_tol=1e-6))
+        per = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fp_worst = 0.0
+        for b in sel:
+            p = probs[b]
+            plan = gvt.Plan(H, tuple(p["M"].shape), tuple(p["N"].shape), p["d"], p["t"])
+            its = []
+            for lam in lambdas:
+                a, st3, inf3 = gvt.krr_cg_solve(H, plan, "kronecker", p["M"], p["N"], p["y"], lam, max_iter=50000,
+                                                check_every=2)
+                its.append(int(inf3.iterations))
+                fp_worst = max(fp_worst, inf3.rel_residual)
+            plan.close()
+            per.append({"problem": b, "m": ps[b].m, "q": ps[b].q, "n": ps[b].n, "fp64_cg_iterations": its})
+        torch.cuda.synchronize()
+        fp_ms = (time.perf_counter() - t0) * 1e3
+        out["sample"] = {"problems": len(sel), "systems": len(sel) * len(lambdas),
+                         "pairs": sum(ps[b].n for b in sel), "batched_ms": sub_ms,
+                         "batched_status": gvt.STATUS_NAMES[st2], "batched_max_rel_residual": max(max(r) for r in rr2),
+                         "plain_fp64_cg_ms": fp_ms, "plain_fp64_cg_max_rel_residual": fp_worst,
+                         "speedup_vs_plain_fp64_cg": fp_ms / sub_ms, "per_problem": per,
+                         "note": "measured on the same problems: batched solve vs plain FP64 CG system by system"}
+    return out
 
 
 def main():

@@ -355,6 +355,13 @@ typedef struct gvt_solve_opts {
                                 0 (default): max_iter / 2 */
     const struct gvt_precond* precond;  /* learned preconditioner for flexible CG (NULL: plain CG);
                                            applies to the FP64 CG and to MIXED_IR's inner solves */
+    double* history;         /* host array of 2 * history_cap doubles, or NULL: the residual
+                                history as (iteration, relative residual) pairs.  FP64_CG records
+                                every convergence check (the recursive residual); MIXED_IR records
+                                every refinement step (the true FP64 residual, at the inner
+                                iterations so far).  gvt_solve_info.history_len counts the pairs */
+    int32_t history_cap;     /* pairs `history` holds (default 0) */
+    int32_t reserved_opts;
 } gvt_solve_opts;
 
 typedef struct gvt_solve_info {
@@ -365,7 +372,7 @@ typedef struct gvt_solve_info {
     double time_ms;          /* wall-clock time of the solve on the host */
     int32_t precond_fallback;  /* 1 if flexible CG broke down or ran out of its budget and
                                   plain CG took over (the preconditioner is then ignored) */
-    int32_t reserved;
+    int32_t history_len;     /* (iteration, residual) pairs written to opts.history */
 } gvt_solve_info;
 
 typedef struct gvt_precond gvt_precond;
@@ -597,19 +604,28 @@ gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem* probs, int
  * handle while statistics are enabled.  Each stage launch is bracketed by
  * CUDA events on its own stream. */
 typedef enum gvt_stat_kind {
-    GVT_STAT_STAGE1 = 0,     /* stage 1: S = B W (sparse scatter-accumulate) */
-    GVT_STAT_STAGE2 = 1,     /* stage 2: sampled gather-dot */
+    GVT_STAT_STAGE1 = 0,     /* stage 1 as a whole, S = B W, whichever engine runs it */
+    GVT_STAT_STAGE2 = 1,     /* stage 2 as a whole: the sampled dots */
     GVT_STAT_ONE_SIDED = 2,  /* one-sided terms: segment sums, GEMV, gather */
     GVT_STAT_TC_GEMM = 3,    /* the tcgen05 GEMM launches of the dense engines alone (also counted
                                 inside their stage's record); flops = 2 M N K of the split GEMM */
-    GVT_STAT_COUNT = 4
+    GVT_STAT_SPARSE_STAGE1 = 4,  /* the sparse scatter-accumulate kernel launches alone (also
+                                    counted inside GVT_STAT_STAGE1) */
+    GVT_STAT_SPARSE_STAGE2 = 5,  /* the sampled gather-dot kernel launches alone (also counted
+                                    inside GVT_STAT_STAGE2) */
+    GVT_STAT_COUNT = 6
 } gvt_stat_kind;
 
 typedef struct gvt_kernel_stats {
     int64_t launches;        /* launches recorded */
     double ms;               /* summed device time of those launches */
-    double flops;            /* algorithmic flops (2 per multiply-add of the definition) */
+    double flops;            /* algorithmic flops (2 per multiply-add of the definition); for
+                                GVT_STAT_TC_GEMM the executed flops 2 M N K of the GEMM */
     double bytes;            /* algorithmic bytes: each operand read once, each result written once */
+    double useful_flops;     /* the method's own flops the launches carry: 2 qbar n (stage 1) or
+                                2 m nhat (stage 2) per Kronecker term, counting only the pairs the
+                                launch serves.  Equal to `flops` except for GVT_STAT_TC_GEMM, whose
+                                dense GEMM does more than the sparse work it stands in for */
 } gvt_kernel_stats;
 
 /* Start (on != 0) or stop recording; starting clears the counters. */

@@ -18,8 +18,8 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-StatScope::StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, double bytes_)
-    : h(h_), s(s_), kind(kind_), flops(flops_), bytes(bytes_)
+StatScope::StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, double bytes_, double useful_)
+    : h(h_), s(s_), kind(kind_), flops(flops_), bytes(bytes_), useful(useful_ < 0.0 ? flops_ : useful_)
 {
     if (!h || !h->stats_on) return;
     if (h->event_pool.size() < 2) {
@@ -38,10 +38,20 @@ StatScope::StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, 
 StatScope::~StatScope()
 {
     if (!e0) return;
+    // nested scopes may have used the pool up since the constructor: create the end event then
+    if (h->event_pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            h->event_pool.push_back(e0);   // drop this record
+            return;
+        }
+        h->event_pool.push_back(e);
+    }
     cudaEvent_t e1 = h->event_pool.back();
     h->event_pool.pop_back();
     cudaEventRecord(e1, s);
-    h->recs.push_back(StatRec{kind, e0, e1, flops, bytes});
+    h->recs.push_back(StatRec{kind, e0, e1, flops, bytes, useful});
 }
 
 gvt_status cuda_fail(cudaError_t e, const char* what)
@@ -632,7 +642,7 @@ gvt_status gvt_stats_read(gvt_handle* h, gvt_kernel_stats* out)
         set_error("gvt_stats_read: NULL argument");
         return GVT_ERR_INVALID_ARG;
     }
-    for (int k = 0; k < GVT_STAT_COUNT; ++k) out[k] = gvt_kernel_stats{0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < GVT_STAT_COUNT; ++k) out[k] = gvt_kernel_stats{0, 0.0, 0.0, 0.0, 0.0};
     for (auto& r : h->recs) {
         GVT_CUDA(cudaEventSynchronize(r.e1));
         float ms = 0.f;
@@ -642,6 +652,7 @@ gvt_status gvt_stats_read(gvt_handle* h, gvt_kernel_stats* out)
         o.ms += ms;
         o.flops += r.flops;
         o.bytes += r.bytes;
+        o.useful_flops += r.useful;
     }
     return GVT_OK;
 }

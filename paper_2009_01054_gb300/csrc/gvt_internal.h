@@ -44,7 +44,7 @@ void count_launches(int n);
 struct StatRec {
     int kind;
     cudaEvent_t e0, e1;
-    double flops, bytes;
+    double flops, bytes, useful;
 };
 
 // ---------------------------------------------------------------- device memory
@@ -121,9 +121,10 @@ struct StatScope {
     gvt_handle* h;
     cudaStream_t s;
     int kind;
-    double flops, bytes;
+    double flops, bytes, useful;
     cudaEvent_t e0 = nullptr;
-    StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, double bytes_);
+    // useful < 0: the launch's useful flops are its algorithmic flops
+    StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, double bytes_, double useful_ = -1.0);
     ~StatScope();
 };
 }  // namespace gvt
@@ -195,7 +196,7 @@ struct S1Sources {
 // S[y, x] = sum_src coef * sum_{j in seg_src[x]} Bt[bcol_j, y] * v[perm_j]   (y < Y, x < X)
 // Bt is B transposed: Bt[t*ldb + y] = B[y, t].  mode squares B's entries.
 template <class T>
-gvt_status stage1_dense(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
+gvt_status stage1_sparse(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
                         T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s);
 // B = identity: S[y, x] = sum_src coef * sum_{j in seg_src[x], bcol_j == y} v[perm_j]
 // (S must be zeroed by the caller; entries with bcol >= Y are skipped).
@@ -213,7 +214,7 @@ struct S2Outputs {
 };
 // u[perm_i] += coef * sum_{x < X} A[arow_i, x] * S[srow_i, x]
 template <class T>
-gvt_status stage2_dense(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
+gvt_status stage2_gather(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
                         const S2Outputs& outs, double coef, T* u, cudaStream_t s);
 // u[perm_i] += C[arow_i, srow_i] (the dense stage 2's sampled read-out)
 gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s);

@@ -387,7 +387,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                                     reinterpret_cast<float*>(base + off_wide), s));
             {
                 StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * X * 3.0 * kp,
-                             2.0 * 3.0 * kp * (Y + X) + 4.0 * Y * X);
+                             2.0 * 3.0 * kp * (Y + X) + 4.0 * Y * X, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E);
                 GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s, h->tc_pairs));
             }
         } else if (g.fb == GVT_FACTOR_IDENTITY) {
@@ -397,9 +397,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         } else {
             const FactorView<T>& B = fv[base_matrix(g.fb, homo)];
             const double bcols = (double)mats[base_matrix(g.fb, homo)]->cols;
-            StatScope st(h, s, GVT_STAT_STAGE1, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E,
-                         sz * Y * bcols + sz * Y * X + E * (8 + sz) + srcs.count * 4.0 * (X + 1));
-            GVT_CHECK(stage1_dense<T>(B.Bt, B.ldbt, sq_mode(g.fb), srcs, v, S, lds, Y, X, s));
+            const double f1 = (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E;
+            const double b1 = sz * Y * bcols + sz * Y * X + E * (8 + sz) + srcs.count * 4.0 * (X + 1);
+            StatScope st(h, s, GVT_STAT_STAGE1, f1, b1);
+            StatScope sk(h, s, GVT_STAT_SPARSE_STAGE1, f1, b1);
+            GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), srcs, v, S, lds, Y, X, s));
         }
         // every group that reads this S (same B factor, out_b range and recipe); on the dense
         // engine S is split once, and a group whose stage-2 GEMM equals the previous one (same
@@ -429,13 +431,26 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
                 float* C2 = reinterpret_cast<float*>(base + off_c2);
                 if (!(c_ptr == Fa->data && c_sq == sq_mode(g2.fa) && c_rows == mb)) {
+                    // useful flops of this GEMM: its own group's sampled dots and those of the later
+                    // groups of this S that read the same C out (until another GEMM replaces it)
+                    double c2_useful = 0.0;
+                    for (size_t gk = gj; gk < C.two.size(); ++gk) {
+                        const TwoSided& g3 = C.two[gk];
+                        if ((gk != gj && done[gk]) || g3.fb != g.fb || g3.recipe != g.recipe ||
+                            out_range(plan, g3.ob) != Y || g3.fa == GVT_FACTOR_IDENTITY || !tc2[gk])
+                            continue;
+                        const gvt_matrix* F3 = mats[base_matrix(g3.fa, homo)];
+                        if (F3->data != Fa->data || sq_mode(g3.fa) != sq_mode(g2.fa) || out_range(plan, g3.oa) != mb)
+                            break;
+                        c2_useful += (sq_mode(g3.fa) ? 3.0 : 2.0) * X * (double)n_out;
+                    }
                     GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2));
                     if (!s_split) {
                         GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s));
                         s_split = true;
                     }
                     StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * 3.0 * kp,
-                                 2.0 * 3.0 * kp * (mb + Y) + 4.0 * mb * Y);
+                                 2.0 * 3.0 * kp * (mb + Y) + 4.0 * mb * Y, c2_useful);
                     GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs));
                     c_ptr = Fa->data;
                     c_sq = sq_mode(g2.fa);
@@ -445,9 +460,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             } else {
                 const FactorView<T>& A = fv[base_matrix(g2.fa, homo)];
                 const double arows = (double)out_range(plan, g2.oa);
-                StatScope st(h, s, GVT_STAT_STAGE2, (sq_mode(g2.fa) ? 3.0 : 2.0) * X * n_out,
-                             sz * (arows * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
-                GVT_CHECK(stage2_dense<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X, outs, 1.0, u, s));
+                const double f2 = (sq_mode(g2.fa) ? 3.0 : 2.0) * X * n_out;
+                const double b2 = sz * (arows * X + (double)Y * X) + (double)n_out * (12 + 2 * sz);
+                StatScope st(h, s, GVT_STAT_STAGE2, f2, b2);
+                StatScope sk(h, s, GVT_STAT_SPARSE_STAGE2, f2, b2);
+                GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X, outs, 1.0, u, s));
             }
         }
     }

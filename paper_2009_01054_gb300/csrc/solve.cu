@@ -182,6 +182,22 @@ __global__ void copy_kernel(T* __restrict__ dst, const T* __restrict__ src, int6
         dst[i] = src[i];
 }
 
+// Residual history of a solve (gvt_solve_opts.history): (iteration, relative residual) pairs.
+struct History {
+    double* buf = nullptr;
+    int32_t cap = 0;
+    int32_t* len = nullptr;
+    double scale = 1.0;      // converts a run's residual (relative to its own b) to ||.|| / ||y||
+    int64_t offset = 0;      // iterations done before the run
+    void add(int64_t it, double rel) const
+    {
+        if (!buf || !len || *len >= cap) return;
+        buf[2 * *len] = (double)(offset + it);
+        buf[2 * *len + 1] = rel * scale;
+        ++*len;
+    }
+};
+
 unsigned vgrid(int64_t n)
 {
     int64_t g = (n + 255) / 256;
@@ -198,7 +214,7 @@ template <class T, class TA>
 gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, const gvt_matrix* N,
                   const T* b, double bnorm, double lam, TA* x, T* r, T* p, T* w, double* part, double* sc,
                   double* hsc, double tol, int64_t max_iter, int check_every, int64_t* iters, double* rel,
-                  cudaStream_t s, gvt_precond* P = nullptr, T* z = nullptr)
+                  cudaStream_t s, gvt_precond* P = nullptr, T* z = nullptr, const History* hist = nullptr)
 {
     const int64_t n = plan->n_in;
     *iters = 0;
@@ -238,6 +254,7 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
     } ev_guard{ev};
     for (auto& e : ev) GVT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     double* ring[2] = {hsc + 16, hsc + 32};   // SC_COUNT doubles each, clear of hsc[0, SC_COUNT)
+    int64_t ring_it[2] = {0, 0};              // iteration of the check held in each slot
     int pending = -1, next_slot = 0;
     // 1 = stop with GVT_OK, 2 = stop with a breakdown, 0 = go on
     auto read_check = [&](int slot) -> int {
@@ -247,6 +264,7 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
             return 2;
         }
         *rel = std::sqrt(h[SC_RR]) / bnorm;
+        if (hist) hist->add(ring_it[slot], *rel);
         return *rel <= tol ? 1 : 0;
     };
     int64_t it = 0;
@@ -278,6 +296,7 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
             next_slot ^= 1;
             GVT_CUDA(cudaMemcpyAsync(ring[slot], sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
             GVT_CUDA(cudaEventRecord(ev[slot], s));
+            ring_it[slot] = it;
             if (pending >= 0) {
                 GVT_CUDA(cudaEventSynchronize(ev[pending]));
                 const int verdict = read_check(pending);
@@ -357,6 +376,9 @@ gvt_status gvt_solve_opts_default(gvt_solve_opts* o)
     o->check_every = 1;
     o->precond_budget = 0;
     o->precond = nullptr;
+    o->history = nullptr;
+    o->history_cap = 0;
+    o->reserved_opts = 0;
     return GVT_OK;
 }
 
@@ -412,6 +434,14 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         info->time_ms = 0.0;
         return ret(GVT_OK);
     }
+    if (opts.history && opts.history_cap < 0) {
+        set_error("gvt_krr_cg_solve: history_cap < 0");
+        return ret(GVT_ERR_INVALID_ARG);
+    }
+    History hist;
+    hist.buf = opts.history;
+    hist.cap = opts.history ? opts.history_cap : 0;
+    hist.len = &info->history_len;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool homo = desc->homogeneous != 0;
     const gvt_matrix* Nn = homo ? M : N;
@@ -472,10 +502,12 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         if (ynorm == 0.0 || rn / ynorm <= opts.rel_tol) return finish(GVT_OK);
         int64_t its = 0;
         double rel = 1.0;
+        hist.add(0, rn / ynorm);
+        hist.scale = rn / ynorm;
         // CG on the correction: stop when ||r|| <= rel_tol * ||y||
         st = cg_run<double, double>(plan, desc, M, Nn, ytmp, rn, lambda, a, r, p, w, part, sc, hsc,
                                     opts.rel_tol * ynorm / rn, P ? pbudget : opts.max_iter, opts.check_every,
-                                    &its, &rel, s, P, P ? (double*)(base + o_z) : nullptr);
+                                    &its, &rel, s, P, P ? (double*)(base + o_z) : nullptr, &hist);
         info->iterations = its;
         if (P && (st == GVT_ERR_NOT_CONVERGED || st == GVT_ERR_BREAKDOWN)) {
             // fallback: plain CG from the current iterate with the remaining iterations
@@ -484,9 +516,11 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
             if (st != GVT_OK) return ret(st);
             if (rn / ynorm <= opts.rel_tol) return finish(GVT_OK);
             int64_t its2 = 0;
+            hist.scale = rn / ynorm;
+            hist.offset = its;
             st = cg_run<double, double>(plan, desc, M, Nn, ytmp, rn, lambda, a, r, p, w, part, sc, hsc,
                                         opts.rel_tol * ynorm / rn, opts.max_iter - its, opts.check_every, &its2,
-                                        &rel, s);
+                                        &rel, s, nullptr, nullptr, &hist);
             info->iterations = its + its2;
         }
         return finish(st);
@@ -515,6 +549,7 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         st = fp64_residual(plan, desc, M, Nn, y, a, lambda, w, r, part, sc, hsc, &rn, s);
         if (st != GVT_OK) return ret(st);
         info->refinements = k;
+        hist.add(total, ynorm > 0 ? rn / ynorm : 0.0);
         if (ynorm == 0.0 || rn / ynorm <= opts.rel_tol) {
             info->iterations = total;
             return finish(GVT_OK);

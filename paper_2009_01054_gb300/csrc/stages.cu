@@ -61,7 +61,7 @@ struct S1Entry {
 
 template <class T, int MODE, int NT, int RPT>
 __global__ void __launch_bounds__(NT)
-stage1_dense_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
+stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
                     const T* __restrict__ v, T* __restrict__ S, int64_t lds, int64_t Y, int64_t X)
 {
     constexpr int VEC = Vec<T>::N;
@@ -210,7 +210,7 @@ constexpr int kS2Group = 4;      // outputs per warp, processed together
 // costs 1 + kS2Group row loads per chunk instead of 2 * kS2Group.
 template <class T, int MODE>
 __global__ void __launch_bounds__(kS2Threads)
-stage2_dense_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ S, int64_t lds,
+stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ S, int64_t lds,
                     int64_t X, S2Outputs outs, T coef, T* __restrict__ u)
 {
     constexpr int VEC = Vec<T>::N;
@@ -616,13 +616,13 @@ static void launch_stage1(const T* Bt, int64_t ldb, int mode, const S1Sources& s
 {
     dim3 grid((unsigned)((Y + NT * RPT - 1) / (NT * RPT)), (unsigned)gy);
     if (mode == FM_SQUARE)
-        stage1_dense_kernel<T, FM_SQUARE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+        stage1_sparse_kernel<T, FM_SQUARE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
     else
-        stage1_dense_kernel<T, FM_DENSE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
+        stage1_sparse_kernel<T, FM_DENSE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
 }
 
 template <class T>
-gvt_status stage1_dense(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
+gvt_status stage1_sparse(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
                         T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s)
 {
     if (Y <= 0 || X <= 0) return GVT_OK;
@@ -640,7 +640,7 @@ gvt_status stage1_dense(const T* Bt, int64_t ldb, int mode, const S1Sources& src
         if (f32) launch_stage1<T, 64, 4>(Bt, ldb, mode, srcs, v, S, lds, Y, X, gy, s);
         else launch_stage1<T, 64, 2>(Bt, ldb, mode, srcs, v, S, lds, Y, X, gy, s);
     }
-    GVT_LAUNCH_CHECK("stage1_dense");
+    GVT_LAUNCH_CHECK("stage1_sparse");
     return GVT_OK;
 }
 
@@ -655,17 +655,17 @@ gvt_status stage1_identity(const S1Sources& srcs, const T* v, T* S, int64_t lds,
 }
 
 template <class T>
-gvt_status stage2_dense(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
+gvt_status stage2_gather(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
                         const S2Outputs& outs, double coef, T* u, cudaStream_t s)
 {
     if (outs.n <= 0) return GVT_OK;
     const int64_t groups = (outs.n + kS2Group - 1) / kS2Group;
     const int64_t g = std::min<int64_t>((groups + (kS2Threads / 32) - 1) / (kS2Threads / 32), 152 * 64);
     if (mode == FM_SQUARE)
-        stage2_dense_kernel<T, FM_SQUARE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
+        stage2_gather_kernel<T, FM_SQUARE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
     else
-        stage2_dense_kernel<T, FM_DENSE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
-    GVT_LAUNCH_CHECK("stage2_dense");
+        stage2_gather_kernel<T, FM_DENSE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
+    GVT_LAUNCH_CHECK("stage2_gather");
     return GVT_OK;
 }
 
@@ -852,11 +852,11 @@ gvt_status tanimoto_kernel(const uint32_t* X, int64_t rx, const uint32_t* Y, int
 }
 
 #define GVT_INST(T)                                                                                 \
-    template gvt_status stage1_dense<T>(const T*, int64_t, int, const S1Sources&, const T*, T*,      \
+    template gvt_status stage1_sparse<T>(const T*, int64_t, int, const S1Sources&, const T*, T*,      \
                                         int64_t, int64_t, int64_t, cudaStream_t);                   \
     template gvt_status stage1_identity<T>(const S1Sources&, const T*, T*, int64_t, int64_t,        \
                                            int64_t, cudaStream_t);                                  \
-    template gvt_status stage2_dense<T>(const T*, int64_t, int, const T*, int64_t, int64_t,          \
+    template gvt_status stage2_gather<T>(const T*, int64_t, int, const T*, int64_t, int64_t,          \
                                         const S2Outputs&, double, T*, cudaStream_t);                \
     template gvt_status stage2_identity<T>(const T*, int64_t, int64_t, const S2Outputs&, double, T*, \
                                            cudaStream_t);                                           \

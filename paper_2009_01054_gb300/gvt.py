@@ -52,20 +52,23 @@ class gvt_matrix(ctypes.Structure):
 class gvt_solve_opts(ctypes.Structure):
     _fields_ = [("rel_tol", c_dbl), ("max_iter", c_i64), ("mode", c_i32),
                 ("inner_dtype", c_i32), ("inner_tol", c_dbl), ("max_refine", c_i32),
-                ("check_every", c_i32), ("precond_budget", c_i32), ("precond", c_vp)]
+                ("check_every", c_i32), ("precond_budget", c_i32), ("precond", c_vp),
+                ("history", c_vp), ("history_cap", c_i32), ("reserved_opts", c_i32)]
 
 
 class gvt_solve_info(ctypes.Structure):
     _fields_ = [("iterations", c_i64), ("refinements", c_i32), ("status", c_i32),
-                ("rel_residual", c_dbl), ("time_ms", c_dbl), ("precond_fallback", c_i32), ("reserved", c_i32)]
+                ("rel_residual", c_dbl), ("time_ms", c_dbl), ("precond_fallback", c_i32), ("history_len", c_i32)]
 
 
 class gvt_kernel_stats(ctypes.Structure):
-    _fields_ = [("launches", c_i64), ("ms", c_dbl), ("flops", c_dbl), ("bytes", c_dbl)]
+    _fields_ = [("launches", c_i64), ("ms", c_dbl), ("flops", c_dbl), ("bytes", c_dbl),
+                ("useful_flops", c_dbl)]
 
 
-GVT_STAT_STAGE1, GVT_STAT_STAGE2, GVT_STAT_ONE_SIDED, GVT_STAT_TC_GEMM, GVT_STAT_COUNT = 0, 1, 2, 3, 4
-STAT_NAMES = ["stage1", "stage2", "one_sided", "tc_gemm"]
+GVT_STAT_STAGE1, GVT_STAT_STAGE2, GVT_STAT_ONE_SIDED, GVT_STAT_TC_GEMM = 0, 1, 2, 3
+GVT_STAT_SPARSE_STAGE1, GVT_STAT_SPARSE_STAGE2, GVT_STAT_COUNT = 4, 5, 6
+STAT_NAMES = ["stage1", "stage2", "one_sided", "tc_gemm", "sparse_stage1", "sparse_stage2"]
 
 
 class gvt_problem(ctypes.Structure):
@@ -235,11 +238,12 @@ def gvt_stats_enable(h, on):
 
 
 def gvt_stats_read(h):
-    """dict kind -> {launches, ms, flops, bytes}"""
+    """dict kind -> {launches, ms, flops, bytes, useful_flops}"""
     arr = (gvt_kernel_stats * GVT_STAT_COUNT)()
     _call("gvt_stats_read", h, ctypes.cast(arr, c_vp))
     return {STAT_NAMES[k]: dict(launches=arr[k].launches, ms=arr[k].ms, flops=arr[k].flops,
-                                bytes=arr[k].bytes) for k in range(GVT_STAT_COUNT)}
+                                bytes=arr[k].bytes, useful_flops=arr[k].useful_flops)
+            for k in range(GVT_STAT_COUNT)}
 
 
 def gvt_launch_count():
@@ -663,8 +667,10 @@ def krr_minres_solve(handle, plan, kind, M, N, y, lam, rel_tol=1e-6, max_iter=10
 
 def krr_cg_solve(handle, plan, kind, M, N, y, lam, a0=None, mode=GVT_SOLVE_FP64_CG, rel_tol=1e-6,
                  max_iter=10000, inner_tol=1e-3, check_every=1, symmetric=True, stream=None,
-                 inner_dtype=GVT_F32, precond=None, precond_budget=0):
-    """Solve (K + lam I) a = y; returns (a, status, info)."""
+                 inner_dtype=GVT_F32, precond=None, precond_budget=0, history=0):
+    """Solve (K + lam I) a = y; returns (a, status, info), or (a, status, info, hist) when
+    history > 0: hist is the list of (iteration, relative residual) pairs the solver recorded
+    (at most `history` of them)."""
     torch = _torch()
     a = torch.zeros_like(y) if a0 is None else a0.clone()
     o = gvt_solve_opts_default()
@@ -672,7 +678,15 @@ def krr_cg_solve(handle, plan, kind, M, N, y, lam, a0=None, mode=GVT_SOLVE_FP64_
     o.inner_dtype = inner_dtype
     o.precond = precond.p if precond is not None else None
     o.precond_budget = precond_budget
+    hbuf = None
+    if history > 0:
+        hbuf = (c_dbl * (2 * int(history)))()
+        o.history = ctypes.cast(hbuf, c_vp)
+        o.history_cap = int(history)
     st, info = gvt_krr_cg_solve(handle.h, plan.p, _desc(kind), matrix(M, symmetric),
                                 matrix(N, symmetric) if N is not None else None,
                                 ptr(y), float(lam), ptr(a), o, stream_ptr(stream))
-    return a, st, info
+    if hbuf is None:
+        return a, st, info
+    hist = [(int(hbuf[2 * k]), float(hbuf[2 * k + 1])) for k in range(info.history_len)]
+    return a, st, info, hist

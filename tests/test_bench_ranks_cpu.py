@@ -37,9 +37,9 @@ def _worker(rank, ws, port, q):
         w = bench.dist_setup()
         step_ms = 2.0 + rank            # rank 1 is the slower one
         ms, rate = bench.job_rate(step_ms, 1000.0, ws, dist, "cpu")
-        p = bench.workload(rank)
+        p = bench.workload("c2", rank)
         class A:                        # the reference arm's arguments
-            steps, warmup = 1, 0
+            steps, warmup, headline = 1, 0, "c2"
         ref = bench.run_reference(A, ws, rank) if rank != 0 else "skipped on rank 0 here"
         q.put((rank, w, ms, rate, int(p.d[:50].sum()), ref))
     finally:

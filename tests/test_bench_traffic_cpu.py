@@ -36,9 +36,11 @@ def test_traffic_records_follow_the_kernel_text(tmp_path, monkeypatch):
     assert recs
     for name, rec in recs.items():
         assert name in bench.KERNEL_SOURCE
-        assert len(rec["kernel_sha256"]) == 64 and rec["dram_bytes_per_launch"] > 0
+        assert len(rec["kernel_sha256"]) == 64 and rec["dram_bytes_per_launch"]
         ok = rec["kernel_sha256"] == hashlib.sha256(bench.kernel_text(name).encode()).hexdigest()
-        assert bench.traffic_for(name) == (rec["dram_bytes_per_launch"] if ok else None)
+        for wl, val in rec["dram_bytes_per_launch"].items():
+            assert wl in bench.WORKLOADS and val > 0
+            assert bench.traffic_for(name, wl) == (val if ok else None)
     # an edited kernel loses its record: point the bench at a copy with one changed character
     name = "tc_gemm_kernel"
     src_dir = tmp_path / "paper_2009_01054_gb300" / "csrc"
@@ -52,4 +54,5 @@ def test_traffic_records_follow_the_kernel_text(tmp_path, monkeypatch):
     assert edited != src
     (src_dir / bench.KERNEL_SOURCE[name]).write_text(edited)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_for(name) is None
+    for wl in bench.WORKLOADS:
+        assert bench.traffic_for(name, wl) is None
