@@ -714,7 +714,8 @@ def bench_solve(H, gvt, torch, dev, lambdas):
     variants = (("fp64_cg", gvt.GVT_SOLVE_FP64_CG, gvt.GVT_F32, gvt.GVT_STAGE1_SIMT),
                 ("mixed_ir_f32", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32, gvt.GVT_STAGE1_SIMT),
                 ("mixed_ir_tc_bf16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_BF16, gvt.GVT_STAGE1_SIMT),
-                ("mixed_ir_tc_f16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32, gvt.GVT_STAGES_TC_F16X3))
+                ("mixed_ir_tc_f16x3", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F32, gvt.GVT_STAGES_TC_F16X3),
+                ("mixed_ir_tc_f16x1", gvt.GVT_SOLVE_MIXED_IR, gvt.GVT_F16, gvt.GVT_STAGE1_SIMT))
     for lam in lambdas:
         r = {}
         for name, mode, inner, engine in variants:
@@ -757,10 +758,10 @@ def oracle_sampled_residual(p, a, lam, rows=200, seed=3):
 
 def bench_c5_solve(H, gvt, torch, dev, p, args):
     """Kernel ridge solves at the kernel-filling scale (m=q=20000, 10M Zipf pairs, Gaussian
-    kernel, FP64 M and N): at lambda = 1, mixed-precision refinement (FP32 inner operator on the
-    automatic engine) to FP64 rel. residual 1e-6, its residual re-checked by the oracle on sampled
-    rows, and (--c5-fp64-cg) plain FP64 CG; at lambda = 1e-2 a bounded attempt whose residual history
-    is reported."""
+    kernel, FP64 M and N): at lambda = 1, mixed-precision refinement to FP64 rel. residual 1e-6 with
+    two inner operators (single-pass FP16 tensor-core stages; FP16x3 stages on the automatic engine),
+    each residual re-checked by the oracle on sampled rows, and (--c5-fp64-cg) plain FP64 CG; at
+    lambda = 1e-2 a bounded attempt whose residual history is reported."""
     import numpy as np
     M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma)
     N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=dev), gamma=p.gamma)
@@ -770,14 +771,20 @@ def bench_c5_solve(H, gvt, torch, dev, p, args):
                        "y = bilinear signal + N(0, 0.1^2)", "runs": {}}
     gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
     try:
-        (a, st, info, hist), wall = timed_solve(torch, lambda: gvt.krr_cg_solve(
-            H, plan, "kronecker", M, N, y, 1.0, mode=gvt.GVT_SOLVE_MIXED_IR, check_every=2, max_iter=5000,
-            history=64))
-        r = {"ms": wall, "status": gvt.STATUS_NAMES[st], "iterations": int(info.iterations),
-             "refinements": int(info.refinements), "rel_residual": info.rel_residual, "history": hist,
-             "inner": "FP32 CG, automatic engine (FP16x3 tensor-core stages where dense)"}
-        r["oracle_check"] = oracle_sampled_residual(p, a.cpu().numpy(), 1.0)
-        res["runs"]["lambda=1"] = {"mixed_ir": r}
+        runs1 = {}
+        for name, inner, note in (("mixed_ir_f16x1", gvt.GVT_F16,
+                                   "FP32 CG on single-pass FP16 tensor-core stages where dense"),
+                                  ("mixed_ir_f16x3", gvt.GVT_F32,
+                                   "FP32 CG, automatic engine (FP16x3 tensor-core stages where dense)")):
+            (a, st_, info, hist), wall = timed_solve(torch, lambda: gvt.krr_cg_solve(
+                H, plan, "kronecker", M, N, y, 1.0, mode=gvt.GVT_SOLVE_MIXED_IR, check_every=2, max_iter=1500,
+                history=64, inner_dtype=inner))
+            rr = {"ms": wall, "status": gvt.STATUS_NAMES[st_], "iterations": int(info.iterations),
+                  "refinements": int(info.refinements), "rel_residual": info.rel_residual, "history": hist,
+                  "inner": note}
+            rr["oracle_check"] = oracle_sampled_residual(p, a.cpu().numpy(), 1.0)
+            runs1[name] = rr
+        res["runs"]["lambda=1"] = runs1
         if args.c5_fp64_cg:
             gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
             (a2, st2, info2, hist2), wall2 = timed_solve(torch, lambda: gvt.krr_cg_solve(
@@ -785,17 +792,19 @@ def bench_c5_solve(H, gvt, torch, dev, p, args):
             r2 = {"ms": wall2, "status": gvt.STATUS_NAMES[st2], "iterations": int(info2.iterations),
                   "rel_residual": info2.rel_residual, "history": hist2[::4]}
             res["runs"]["lambda=1"]["fp64_cg"] = r2
-            if st == 0 and st2 == 0:
-                r["speedup_vs_fp64_cg"] = wall2 / wall
+            for rr in runs1.values():
+                if rr["status"] == "GVT_OK" and st2 == 0:
+                    rr["speedup_vs_fp64_cg"] = wall2 / rr["ms"]
             gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
         if args.c5_bounded_iters > 0:
             (a3, st3, info3, hist3), wall3 = timed_solve(torch, lambda: gvt.krr_cg_solve(
                 H, plan, "kronecker", M, N, y, 1e-2, mode=gvt.GVT_SOLVE_MIXED_IR, check_every=2,
-                max_iter=args.c5_bounded_iters, history=64))
+                max_iter=args.c5_bounded_iters, history=64, inner_dtype=gvt.GVT_F16))
             res["runs"]["lambda=0.01"] = {"mixed_ir_bounded": {
                 "ms": wall3, "status": gvt.STATUS_NAMES[st3], "iterations": int(info3.iterations),
                 "refinements": int(info3.refinements), "rel_residual": info3.rel_residual, "history": hist3,
-                "note": "bounded attempt: at most %d inner iterations" % args.c5_bounded_iters}}
+                "note": "bounded attempt: at most %d inner iterations on the single-pass FP16 inner operator"
+                        % args.c5_bounded_iters}}
     finally:
         gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
     plan.close()

@@ -58,7 +58,8 @@ typedef enum gvt_status {
 typedef enum gvt_dtype {
     GVT_F64 = 0,
     GVT_F32 = 1,
-    GVT_BF16 = 2
+    GVT_BF16 = 2,
+    GVT_F16 = 3      /* only as a MIXED_IR inner precision (gvt_solve_opts.inner_dtype) */
 } gvt_dtype;
 
 /* Pairwise kernels of Table 4b.  GAUSSIAN is the Kronecker product of two
@@ -265,13 +266,19 @@ gvt_status gvt_tanimoto_kernel(gvt_handle* h, const uint32_t* X, int64_t rows_x,
  *  GVT_STAGES_AUTO      : per stage, GVT_STAGES_TC_F16X3 where a cost model (dense
  *                         GEMM time vs sparse SIMT time at measured GB300 rates)
  *                         favours it -- W dense enough -- and SIMT elsewhere.
+ *  GVT_STAGES_TC_F16X1  : per stage as GVT_STAGES_AUTO, but the dense stages are a
+ *                         single tcgen05 pass over the FP16 hi parts alone (row-scaled;
+ *                         products accurate to about 2^-11 relative, a third of the
+ *                         GEMM work).  For inner operators whose error an FP64 outer
+ *                         refinement removes (gvt_solve_opts.inner_dtype = GVT_F16).
  * Affects later products made with plans of this handle.
  */
 typedef enum gvt_stage1_engine {
     GVT_STAGE1_SIMT = 0,
     GVT_STAGE1_TC_BF16X3 = 1,
     GVT_STAGES_TC_F16X3 = 2,
-    GVT_STAGES_AUTO = 3
+    GVT_STAGES_AUTO = 3,
+    GVT_STAGES_TC_F16X1 = 4
 } gvt_stage1_engine;
 
 gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine);
@@ -342,8 +349,9 @@ typedef struct gvt_solve_opts {
     double rel_tol;          /* target ||y - (K + lambda I) a||_2 / ||y||_2 (default 1e-6) */
     int64_t max_iter;        /* total CG iterations, inner ones included (default 10000) */
     int32_t mode;            /* gvt_solve_mode (default GVT_SOLVE_FP64_CG) */
-    int32_t inner_dtype;     /* MIXED_IR inner operator: GVT_F32 (default, SIMT stages) or
-                                GVT_BF16 (FP32 CG with the GVT_STAGE1_TC_BF16X3 stage 1) */
+    int32_t inner_dtype;     /* MIXED_IR inner operator: GVT_F32 (default: the handle's engine),
+                                GVT_BF16 (FP32 CG with the GVT_STAGE1_TC_BF16X3 stage 1) or
+                                GVT_F16 (FP32 CG with the single-pass GVT_STAGES_TC_F16X1 stages) */
     double inner_tol;        /* MIXED_IR inner relative tolerance (default 1e-3) */
     int32_t max_refine;      /* MIXED_IR outer steps (default 30) */
     int32_t check_every;     /* CG iterations between convergence checks (default 1).  The host

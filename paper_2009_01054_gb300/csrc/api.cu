@@ -573,7 +573,7 @@ gvt_status gvt_set_tc_pairs(gvt_handle* h, int32_t mode)
 
 gvt_status gvt_set_stage1_engine(gvt_handle* h, int32_t engine)
 {
-    if (!h || engine < GVT_STAGE1_SIMT || engine > GVT_STAGES_AUTO) {
+    if (!h || engine < GVT_STAGE1_SIMT || engine > GVT_STAGES_TC_F16X1) {
         set_error("gvt_set_stage1_engine: bad handle or engine");
         return GVT_ERR_INVALID_ARG;
     }

@@ -7,6 +7,9 @@
 // Each FP32 operand is split into a 3K'-wide 16-bit operand (K' = K rounded
 // up to 64) so that one GEMM of the splits gives hi*hi + hi*lo + lo*hi:
 //   left  operand  [hi | hi | lo]      right operand  [hi | lo | hi]
+// or, in the single-pass form, kept as its K'-wide hi part alone (one GEMM of
+// the hi parts: FP16 products accurate to about 2^-11 relative, for inner
+// operators whose error an FP64 outer refinement removes).
 // Two split formats:
 //   BF16 : hi = bf16(x), lo = bf16(x - hi); no scaling.  Products are
 //          accurate to about 3 * 2^-17 relative.
@@ -103,19 +106,20 @@ __device__ __forceinline__ void load8(const float* sp, int64_t k0, int64_t cols,
     }
 }
 
-__device__ __forceinline__ void store3(uint4* d, int64_t q, int64_t per_row, int pattern_b, const uint4& hi,
-                                       const uint4& lo)
+__device__ __forceinline__ void store3(uint4* d, int64_t q, int64_t per_row, int pattern_b, int parts,
+                                       const uint4& hi, const uint4& lo)
 {
     d[q] = hi;
+    if (parts == 1) return;
     d[per_row + q] = pattern_b ? lo : hi;
     d[2 * per_row + q] = pattern_b ? hi : lo;
 }
 
-// One CTA per row: dst row r = 3-part split of src row r (zero beyond cols).
+// One CTA per row: dst row r = the `parts`-part split of src row r (zero beyond cols).
 template <bool F16>
 __global__ void __launch_bounds__(kSplitThreads)
 split_rows_kernel(const float* __restrict__ src, int64_t ld, int64_t cols, int square, int pattern_b,
-                  uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp)
+                  uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp, int parts)
 {
     __shared__ float red[kSplitThreads / 32];
     const int64_t r = blockIdx.x;
@@ -134,23 +138,24 @@ split_rows_kernel(const float* __restrict__ src, int64_t ld, int64_t cols, int s
         row_scale(block_max(m, red), s, inv);
         if (threadIdx.x == 0) inv_scale[r] = inv;
     }
-    uint4* d = dst + r * 3 * per_row;
+    uint4* d = dst + r * parts * per_row;
     for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
         float x[8];
         load8(row + q * 8, q * 8, cols, square, x);
         uint4 hi, lo;
         if (F16) split8_f16(x, s, hi, lo);
         else split8_bf16(x, hi, lo);
-        store3(d, q, per_row, pattern_b, hi, lo);
+        store3(d, q, per_row, pattern_b, parts, hi, lo);
     }
 }
 
 // One CTA per row x of W^T: accumulate the row's entries (its segment of every
-// source) in shared memory, then write the [hi | lo | hi] split of the row.
+// source) in shared memory, then write the [hi | lo | hi] split of the row (its hi part
+// alone when parts == 1).
 template <bool F16>
 __global__ void __launch_bounds__(kSplitThreads)
 densify_split_kernel(S1Sources srcs, const float* __restrict__ v, uint4* __restrict__ dst,
-                     float* __restrict__ inv_scale, int64_t kp)
+                     float* __restrict__ inv_scale, int64_t kp, int parts)
 {
     extern __shared__ float wrow[];
     __shared__ float red[kSplitThreads / 32];
@@ -194,7 +199,7 @@ densify_split_kernel(S1Sources srcs, const float* __restrict__ v, uint4* __restr
         row_scale(block_max(m, red), s, inv);
         if (threadIdx.x == 0) inv_scale[x] = inv;
     }
-    uint4* d = dst + x * 3 * per_row;
+    uint4* d = dst + x * parts * per_row;
     for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
         float xs[8];
 #pragma unroll
@@ -202,7 +207,7 @@ densify_split_kernel(S1Sources srcs, const float* __restrict__ v, uint4* __restr
         uint4 hi, lo;
         if (F16) split8_f16(xs, s, hi, lo);
         else split8_bf16(xs, hi, lo);
-        store3(d, q, per_row, 1, hi, lo);
+        store3(d, q, per_row, 1, parts, hi, lo);
     }
 }
 
@@ -249,18 +254,20 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 int64_t dense_kp(int64_t K) { return (K + 63) / 64 * 64; }
 
-size_t dense_operand_bytes(int64_t rows, int64_t K)
+size_t dense_operand_bytes(int64_t rows, int64_t K, int parts)
 {
-    return al256(2 * (size_t)rows * 3 * (size_t)dense_kp(K)) + al256(4 * (size_t)std::max<int64_t>(rows, 1));
+    return al256(2 * (size_t)rows * parts * (size_t)dense_kp(K)) + al256(4 * (size_t)std::max<int64_t>(rows, 1));
 }
 
-DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K)
+DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K, int parts)
 {
     DenseOperand o;
     o.data = base;
-    o.inv_scale = reinterpret_cast<float*>(static_cast<char*>(base) + al256(2 * (size_t)rows * 3 * (size_t)dense_kp(K)));
+    o.inv_scale = reinterpret_cast<float*>(static_cast<char*>(base) +
+                                           al256(2 * (size_t)rows * parts * (size_t)dense_kp(K)));
     o.rows = rows;
     o.kp = dense_kp(K);
+    o.parts = parts;
     return o;
 }
 
@@ -280,10 +287,10 @@ gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t 
     uint4* d = static_cast<uint4*>(dst.data);
     if (f16)
         split_rows_kernel<true><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
-                                                                         dst.inv_scale, dst.kp);
+                                                                         dst.inv_scale, dst.kp, dst.parts);
     else
         split_rows_kernel<false><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
-                                                                          dst.inv_scale, dst.kp);
+                                                                          dst.inv_scale, dst.kp, dst.parts);
     GVT_LAUNCH_CHECK("dense split rows");
     return GVT_OK;
 }
@@ -300,8 +307,12 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
             if (f16) GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(densify_split_kernel<true>), (int)smem));
             else GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(densify_split_kernel<false>), (int)smem));
         }
-        if (f16) densify_split_kernel<true><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp);
-        else densify_split_kernel<false><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp);
+        if (f16)
+            densify_split_kernel<true><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp,
+                                                                               dst.parts);
+        else
+            densify_split_kernel<false><<<(unsigned)X, kSplitThreads, smem, s>>>(srcs, v, d, dst.inv_scale, kp,
+                                                                                dst.parts);
         GVT_LAUNCH_CHECK("densify and split W");
         return GVT_OK;
     }
@@ -317,11 +328,12 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
 gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
                       cudaStream_t s, int pair_mode)
 {
-    if (a.kp != b.kp) {
+    if (a.kp != b.kp || a.parts != b.parts) {
         set_error("dense stage: operand widths differ");
         return GVT_ERR_INVALID_ARG;
     }
-    return tc_gemm(a.data, 3 * a.kp, b.data, 3 * b.kp, C, ldc, a.rows, b.rows, 3 * a.kp, f16,
+    const int64_t kw = (int64_t)a.parts * a.kp;
+    return tc_gemm(a.data, kw, b.data, kw, C, ldc, a.rows, b.rows, kw, f16,
                    f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s, pair_mode);
 }
 

@@ -76,6 +76,7 @@ struct FactorCacheEntry {
     const void* ptr = nullptr;
     int64_t ld = 0, rows = 0, K = 0;
     int sq = -1;
+    int parts = 3;
     bool f16 = false;
     bool valid = false;
     uint64_t used = 0;
@@ -265,17 +266,19 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                         int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode);
 
-// A split operand of the dense stages: rows x 3kp 16-bit values ([hi|hi|lo] or
-// [hi|lo|hi]), and for FP16 splits the inverse power-of-two scale of every row.
+// A split operand of the dense stages: rows x (parts * kp) 16-bit values ([hi|hi|lo] or
+// [hi|lo|hi] when parts == 3, [hi] when parts == 1), and for FP16 splits the inverse
+// power-of-two scale of every row.
 struct DenseOperand {
     void* data = nullptr;
     float* inv_scale = nullptr;
     int64_t rows = 0;
     int64_t kp = 0;   // K rounded up to 64
+    int parts = 3;
 };
 int64_t dense_kp(int64_t K);
-size_t dense_operand_bytes(int64_t rows, int64_t K);
-DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K);
+size_t dense_operand_bytes(int64_t rows, int64_t K, int parts);
+DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K, int parts);
 size_t dense_w_scratch_bytes(int64_t X, int64_t K);
 // rows of a row-major FP32 matrix (entries squared if `square`), pattern_b: [hi|lo|hi] instead of [hi|hi|lo]
 gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t cols, int square, bool f16,

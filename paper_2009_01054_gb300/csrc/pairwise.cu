@@ -43,17 +43,18 @@ struct Compiled {
     std::vector<OneSided> one;
 };
 
-// Engine choice of GVT_STAGES_AUTO for one stage: the dense FP16x3 GEMM (rows x cols
-// outputs, inner length K) against the sparse SIMT stage doing simt_flops useful flops.
-// Rates measured on GB300 at m = q = 2000 over pair densities 0.2 % to 20 %: SIMT stages about
-// 4.5e12 useful flop/s, the split GEMM about 1.2e15 flop/s, the split and densify passes about
-// 4e12 B/s, and about 8 us of fixed cost per dense stage (a dense stage measured 66 us there,
-// the SIMT stage 74 us at 2 % density; for one Kronecker term the model switches at 1.8 %).
-bool dense_pays(int64_t rows, int64_t cols, int64_t K, double simt_flops)
+// Engine choice of GVT_STAGES_AUTO (parts = 3) and GVT_STAGES_TC_F16X1 (parts = 1) for one
+// stage: the dense GEMM over `parts` 16-bit parts (rows x cols outputs, inner length K) against
+// the sparse SIMT stage doing simt_flops useful flops.  Rates measured on GB300 at m = q = 2000
+// over pair densities 0.2 % to 20 %: SIMT stages about 4.5e12 useful flop/s, the split GEMM
+// about 1.2e15 flop/s, the split and densify passes about 4e12 B/s, and about 8 us of fixed cost
+// per dense stage (a dense stage measured 66 us there, the SIMT stage 74 us at 2 % density; for
+// one Kronecker term the model switches at 1.8 % with three parts).
+bool dense_pays(int64_t rows, int64_t cols, int64_t K, double simt_flops, int parts)
 {
     const double kp = (double)dense_kp(K);
-    const double t_dense = 6.0 * rows * cols * kp / 1.2e15 +
-                           (6.0 * (double)(rows + cols) * kp + 4.0 * (double)rows * cols) / 4e12 + 8e-6;
+    const double t_dense = 2.0 * parts * rows * cols * kp / 1.2e15 +
+                           (2.0 * parts * (double)(rows + cols) * kp + 4.0 * (double)rows * cols) / 4e12 + 8e-6;
     return t_dense < simt_flops / 4.5e12;
 }
 
@@ -191,7 +192,10 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     gvt_handle* h = plan->h;
     // engine of the dense x dense groups of FP32 products (FP64 products always run the SIMT stages)
     const int engine = sizeof(T) == 4 ? h->stage1_engine : (int)GVT_STAGE1_SIMT;
-    const bool f16 = engine == GVT_STAGES_TC_F16X3 || engine == GVT_STAGES_AUTO;
+    const bool f16 = engine == GVT_STAGES_TC_F16X3 || engine == GVT_STAGES_AUTO || engine == GVT_STAGES_TC_F16X1;
+    // 16-bit parts of every dense operand: the hi/lo split (three GEMM passes) or hi alone
+    const int parts = engine == GVT_STAGES_TC_F16X1 ? 1 : 3;
+    const bool chooses = engine == GVT_STAGES_AUTO || engine == GVT_STAGES_TC_F16X1;   // per-stage cost model
     Compiled C;
     GVT_CHECK(compile(plan, desc, mats, engine == GVT_STAGE1_TC_BF16X3, C));
 
@@ -241,11 +245,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             const int64_t K = in_range(plan, ib);
             if (is_dense(g.fb) && same_ib && Y > 0 && X > 0 && K > 0) {   // stage 1 needs a dense B only
                 const double entries = (double)g.recipe.size() * plan->n_in;
-                tc1[gi] = engine == GVT_STAGES_AUTO ? dense_pays(Y, X, K, 2.0 * Y * entries) : 1;
+                tc1[gi] = chooses ? dense_pays(Y, X, K, 2.0 * Y * entries, parts) : 1;
             }
             if (tc1[gi]) {
-                slot_bytes = std::max(slot_bytes, dense_operand_bytes(Y, K));
-                w_bytes = std::max(w_bytes, dense_operand_bytes(X, K));
+                slot_bytes = std::max(slot_bytes, dense_operand_bytes(Y, K, parts));
+                w_bytes = std::max(w_bytes, dense_operand_bytes(X, K, parts));
                 wide_bytes = std::max(wide_bytes, dense_w_scratch_bytes(X, K));
             }
             for (size_t gj = gi; gj < C.two.size(); ++gj) {
@@ -254,10 +258,10 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 seen[gj] = true;
                 const int64_t mb = out_range(plan, g2.oa);
                 if (!f16 || !is_dense(g2.fa) || mb <= 0) continue;
-                tc2[gj] = engine == GVT_STAGES_AUTO ? dense_pays(mb, Y, X, 2.0 * X * (double)n_out) : 1;
+                tc2[gj] = chooses ? dense_pays(mb, Y, X, 2.0 * X * (double)n_out, parts) : 1;
                 if (!tc2[gj]) continue;
-                slot_bytes = std::max(slot_bytes, dense_operand_bytes(mb, X));
-                s_bytes = std::max(s_bytes, dense_operand_bytes(Y, X));
+                slot_bytes = std::max(slot_bytes, dense_operand_bytes(mb, X, parts));
+                s_bytes = std::max(s_bytes, dense_operand_bytes(Y, X, parts));
                 c_bytes = std::max(c_bytes, sizeof(float) * (size_t)mb * (size_t)round_up(Y, 4));
             }
         }
@@ -302,7 +306,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         int64_t rows = -1, K = -1;
         size_t off = 0;
         int64_t used = -1;
-    } slots[2];
+    } slots[2];   // (the parts count is fixed for the whole call)
     slots[0].off = off_slot0;
     slots[1].off = off_slot1;
     int64_t tick = 0;
@@ -310,17 +314,17 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         if (h->factor_cache_depth > 0) {   // a solve holds the matrices fixed: keep splits across products
             for (auto& e : h->factor_cache)
                 if (e.valid && e.ptr == F->data && e.ld == F->ld && e.rows == rows && e.K == K && e.sq == sq &&
-                    e.f16 == f16) {
+                    e.f16 == f16 && e.parts == parts) {
                     e.used = ++h->factor_cache_tick;
-                    out = dense_operand_at(e.buf.ptr, rows, K);
+                    out = dense_operand_at(e.buf.ptr, rows, K, parts);
                     return GVT_OK;
                 }
             FactorCacheEntry* lru = &h->factor_cache[0];   // an empty entry, else the least recently used
             for (auto& e : h->factor_cache)
                 if (!e.valid ? lru->valid || e.used < lru->used : lru->valid && e.used < lru->used) lru = &e;
             lru->valid = false;
-            GVT_CHECK(lru->buf.reserve(dense_operand_bytes(rows, K), s));
-            out = dense_operand_at(lru->buf.ptr, rows, K);
+            GVT_CHECK(lru->buf.reserve(dense_operand_bytes(rows, K, parts), s));
+            out = dense_operand_at(lru->buf.ptr, rows, K, parts);
             GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s));
             lru->ptr = F->data;
             lru->ld = F->ld;
@@ -328,6 +332,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             lru->K = K;
             lru->sq = sq;
             lru->f16 = f16;
+            lru->parts = parts;
             lru->valid = true;
             lru->used = ++h->factor_cache_tick;
             return GVT_OK;
@@ -335,11 +340,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         for (auto& sl : slots)
             if (sl.ptr == F->data && sl.sq == sq && sl.rows == rows && sl.K == K && sl.pattern == 0) {
                 sl.used = ++tick;
-                out = dense_operand_at(base + sl.off, rows, K);
+                out = dense_operand_at(base + sl.off, rows, K, parts);
                 return GVT_OK;
             }
         Slot& sl = slots[0].used <= slots[1].used ? slots[0] : slots[1];
-        out = dense_operand_at(base + sl.off, rows, K);
+        out = dense_operand_at(base + sl.off, rows, K, parts);
         GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s));
         sl.ptr = F->data;
         sl.sq = sq;
@@ -381,13 +386,13 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             // executed flops are recorded under GVT_STAT_TC_GEMM
             StatScope st(h, s, GVT_STAT_STAGE1, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E,
                          sz * Y * (double)K + sz * Y * X + E * (8 + sz) + srcs.count * 4.0 * (X + 1));
-            DenseOperand a1, b1 = dense_operand_at(base + off_w, X, K);
+            DenseOperand a1, b1 = dense_operand_at(base + off_w, X, K, parts);
             GVT_CHECK(factor_operand(Bm, sq_mode(g.fb), Y, K, a1));
             GVT_CHECK(dense_split_w(srcs, keys, plan->n_in, reinterpret_cast<const float*>(v), X, f16, b1,
                                     reinterpret_cast<float*>(base + off_wide), s));
             {
-                StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * X * 3.0 * kp,
-                             2.0 * 3.0 * kp * (Y + X) + 4.0 * Y * X, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E);
+                StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * X * parts * kp,
+                             2.0 * parts * kp * (Y + X) + 4.0 * Y * X, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E);
                 GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s, h->tc_pairs));
             }
         } else if (g.fb == GVT_FACTOR_IDENTITY) {
@@ -427,7 +432,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 const double kp = (double)dense_kp(X);
                 StatScope st(h, s, GVT_STAT_STAGE2, (sq_mode(g2.fa) ? 3.0 : 2.0) * X * n_out,
                              sz * ((double)mb * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
-                DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X);
+                DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X, parts);
                 const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
                 float* C2 = reinterpret_cast<float*>(base + off_c2);
                 if (!(c_ptr == Fa->data && c_sq == sq_mode(g2.fa) && c_rows == mb)) {
@@ -449,8 +454,8 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                         GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s));
                         s_split = true;
                     }
-                    StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * 3.0 * kp,
-                                 2.0 * 3.0 * kp * (mb + Y) + 4.0 * mb * Y, c2_useful);
+                    StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * parts * kp,
+                                 2.0 * parts * kp * (mb + Y) + 4.0 * mb * Y, c2_useful);
                     GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs));
                     c_ptr = Fa->data;
                     c_sq = sq_mode(g2.fa);

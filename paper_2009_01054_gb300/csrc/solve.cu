@@ -412,8 +412,9 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         set_error("gvt_krr_cg_solve: unknown mode");
         return ret(GVT_ERR_INVALID_ARG);
     }
-    if (opts.mode == GVT_SOLVE_MIXED_IR && opts.inner_dtype != GVT_F32 && opts.inner_dtype != GVT_BF16) {
-        set_error("gvt_krr_cg_solve: MIXED_IR inner operator must be GVT_F32 or GVT_BF16");
+    if (opts.mode == GVT_SOLVE_MIXED_IR && opts.inner_dtype != GVT_F32 && opts.inner_dtype != GVT_BF16 &&
+        opts.inner_dtype != GVT_F16) {
+        set_error("gvt_krr_cg_solve: MIXED_IR inner operator must be GVT_F32, GVT_BF16 or GVT_F16");
         return ret(GVT_ERR_UNSUPPORTED);
     }
     const int64_t n = plan->n_in;
@@ -564,19 +565,20 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
         const double inner_tol = std::max(opts.inner_tol, 0.5 * opts.rel_tol * ynorm / rn);
         const int saved_engine = plan->h->stage1_engine;
         if (opts.inner_dtype == GVT_BF16) plan->h->stage1_engine = GVT_STAGE1_TC_BF16X3;
+        if (opts.inner_dtype == GVT_F16) plan->h->stage1_engine = GVT_STAGES_TC_F16X1;
         const int64_t inner_budget = P ? std::min(pbudget, opts.max_iter - total) : opts.max_iter - total;
         st = cg_run<float, float>(plan, desc, &M32, &N32, r32, 1.0, lambda, c32, q32, p32, w32, part, sc,
                                   hsc, inner_tol, inner_budget, opts.check_every, &its, &rel, s,
                                   P, P ? (float*)(base + o_z) : nullptr);
         plan->h->stage1_engine = saved_engine;
-        if (opts.inner_dtype == GVT_BF16) {
+        if (opts.inner_dtype != GVT_F32 || saved_engine != GVT_STAGE1_SIMT) {
             int word = 0;
             if (cudaMemcpyAsync(&word, handle_err_word(plan->h), sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)
                 return ret(cuda_fail(cudaGetLastError(), "device error word"));
             if (word) {
                 cudaMemsetAsync(handle_err_word(plan->h), 0, sizeof(int), s);
-                set_error("a bounded wait in the tensor-core stage 1 expired");
+                set_error("a bounded wait in a tensor-core stage expired");
                 info->iterations = total + its;
                 return ret(GVT_ERR_TIMEOUT);
             }

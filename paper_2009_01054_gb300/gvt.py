@@ -22,14 +22,14 @@ GVT_ERR_BREAKDOWN, GVT_ERR_NOT_CONVERGED, GVT_ERR_TIMEOUT = 6, 7, 8
 STATUS_NAMES = {0: "GVT_OK", 1: "GVT_ERR_INVALID_ARG", 2: "GVT_ERR_INDEX_OOB",
                 3: "GVT_ERR_UNSUPPORTED", 4: "GVT_ERR_ALLOC", 5: "GVT_ERR_CUDA",
                 6: "GVT_ERR_BREAKDOWN", 7: "GVT_ERR_NOT_CONVERGED", 8: "GVT_ERR_TIMEOUT"}
-GVT_F64, GVT_F32, GVT_BF16 = 0, 1, 2
+GVT_F64, GVT_F32, GVT_BF16, GVT_F16 = 0, 1, 2, 3
 KERNELS = {"kronecker": 0, "gaussian": 1, "linear": 2, "poly2d": 3, "cartesian": 4,
            "symmetric": 5, "antisymmetric": 6, "ranking": 7, "mlpk": 8}
 HOMOGENEOUS = {"symmetric", "antisymmetric", "ranking", "mlpk"}
 GVT_FACTOR_M, GVT_FACTOR_N, GVT_FACTOR_M_SQ, GVT_FACTOR_N_SQ, GVT_FACTOR_ONES, GVT_FACTOR_IDENTITY = range(6)
 GVT_FIRST, GVT_SECOND = 0, 1
 GVT_SOLVE_FP64_CG, GVT_SOLVE_MIXED_IR = 0, 1
-GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3, GVT_STAGES_TC_F16X3, GVT_STAGES_AUTO = 0, 1, 2, 3
+GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3, GVT_STAGES_TC_F16X3, GVT_STAGES_AUTO, GVT_STAGES_TC_F16X1 = 0, 1, 2, 3, 4
 GVT_TC_PAIRS_AUTO, GVT_TC_PAIRS_OFF, GVT_TC_PAIRS_ON = 0, 1, 2
 GVT_MAX_TERMS = 16
 

@@ -14,7 +14,9 @@
 * a mixed-precision solve whose inner operator uses the tensor cores reaches
   the FP64 relative residual 1e-6 checked by the oracle;
 * the GEMM's two tile forms (one SM per 128-row tile, an SM pair per 256-row
-  tile) on the raw GEMM and on the dense engine's products.
+  tile) on the raw GEMM and on the dense engine's products;
+* the single-pass FP16 stages (GVT_STAGES_TC_F16X1) within their rounding
+  bound, and mixed-precision solves on that inner operator reaching 1e-6.
 """
 import numpy as np
 import pytest
@@ -364,4 +366,63 @@ def test_factor_cache_scope_reuses_splits_and_keys_by_matrix(H):
     assert not torch.equal(ref[("kronecker", 0)], ref[("kronecker", 1)])
     with pytest.raises(gvt.GvtError):
         gvt.gvt_factor_cache_end(H.h)
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", ["kronecker", "gaussian", "poly2d", "cartesian", "symmetric"])
+def test_single_pass_f16_stages_within_their_rounding_bound(H, kind):
+    """GVT_STAGES_TC_F16X1: the dense stages as one tcgen05 pass over FP16 hi parts of power-of-two
+    scaled rows.  Each operand entry is rounded once to FP16 (unit roundoff u = 2^-11) in stage 1
+    (N or M and W) and once more in stage 2 (A and S), so each term of u_i is off by at most about
+    4u of its magnitude: |u_i - u*_i| <= 4u (|K||v|)_i plus FP32 accumulation.  These kernels have
+    nonnegative formulas on Gaussian bases, so |K| = K and (|K||v|)_i is the oracle's product with
+    |v|.  The test asserts 8u (a factor 2 of margin) on a dense sample, where the cost model picks
+    the tensor cores (checked through the library's GEMM statistics)."""
+    rng = np.random.default_rng(17)
+    m, q, dim = 300, (300 if kind in gvt.HOMOGENEOUS else 80), 12
+    Xd = rng.standard_normal((m, dim))
+    Xt = Xd if kind in gvt.HOMOGENEOUS else rng.standard_normal((q, dim))
+    n = int(0.4 * m * q)
+    d, t = synth.random_pairs(rng, n, m, q)
+    v = rng.standard_normal(n)
+    g = 1.0 / dim
+    M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=g, dtype=torch.float32)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=g, dtype=torch.float32)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t)
+    vv = torch.as_tensor(v, dtype=torch.float32, device=DEV)
+    gvt.gvt_stats_enable(H.h, True)
+    u = _engine_product(H, gvt.GVT_STAGES_TC_F16X1, plan, kind, M, N, vv)
+    stats = gvt.gvt_stats_read(H.h)
+    gvt.gvt_stats_enable(H.h, False)
+    v64 = vv.double().cpu().numpy()
+    ref = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, v64)
+    mag = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, np.abs(v64))
+    err = float(np.max(np.abs(u - ref)) / np.max(mag))
+    print("%s single-pass FP16 stages: error %.2e of max |K||v| (normwise %.2e), %d GEMM launches"
+          % (kind, err, normwise(u, ref), stats["tc_gemm"]["launches"]))
+    assert stats["tc_gemm"]["launches"] > 0
+    assert err <= 8 * 2.0 ** -11
+    plan.close()
+
+
+@pytest.mark.parametrize("lam", [1e-1, 1e-2])
+def test_mixed_ir_with_single_pass_f16_inner_operator(H, lam):
+    """Mixed-precision refinement whose inner FP32 CG runs on the single-pass FP16 tensor-core
+    stages (inner_dtype = GVT_F16) reaches the FP64 relative residual 1e-6, recomputed by the
+    oracle over all pairs."""
+    Xd, Xt, d, t, v, g = _problem(seed=4, rho=0.4)
+    y = np.random.default_rng(6).standard_normal(len(d))
+    M = gvt.gaussian_kernel(H, torch.as_tensor(Xd, device=DEV), gamma=g)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(Xt, device=DEV), gamma=g)
+    plan = gvt.Plan(H, tuple(M.shape), tuple(N.shape), d, t)
+    a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, torch.as_tensor(y, device=DEV), lam,
+                                   mode=gvt.GVT_SOLVE_MIXED_IR, inner_dtype=gvt.GVT_F16, max_iter=20000)
+    Mo, No = orc.gaussian_kernel(Xd, gamma=g), orc.gaussian_kernel(Xt, gamma=g)
+    mv = lambda x: orc.pairwise_matvec("kronecker", Mo, No, d, t, d, t, x)
+    rr = orc.relative_residual(mv, a.cpu().numpy(), y, lam)
+    print("single-pass FP16 inner, lambda %g: status %d, %d inner iterations, %d refinements, oracle residual %.2e"
+          % (lam, st, info.iterations, info.refinements, rr))
+    assert st == 0, (st, info.iterations, info.refinements, info.rel_residual)
+    assert rr <= 1.05e-6
     plan.close()
