@@ -334,6 +334,19 @@ gvt_status gvt_set_tc_pairs(gvt_handle* h, int32_t mode);
 gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
                             int64_t ldc, int64_t M, int64_t N, int64_t K, void* stream);
 
+/*
+ * Test of the tensor-core kernels' timeout path (no counterpart in the paper; failure
+ * detection).  While `cycles` > 0, every tensor-core GEMM this handle launches makes its MMA
+ * thread first wait that many SM clock cycles on an mbarrier that nothing arrives on.  The
+ * wait expires, the kernel takes the path of any expired wait -- its other threads stop
+ * waiting, it waits (bounded) for the tile copies and MMAs it issued, frees its tensor memory
+ * and returns -- and GVT_ERR_TIMEOUT lands in the handle's error word (gvt_check_device_errors;
+ * the GEMM's output is then invalid).  cycles = 0 (the default) turns it off.  The one-SM tile
+ * form only: a GEMM in the SM-pair form (gvt_set_tc_pairs ON) returns GVT_ERR_UNSUPPORTED while
+ * it is on.  GVT_ERR_INVALID_ARG for cycles outside [0, 4e9].
+ */
+gvt_status gvt_set_tc_stall_test(gvt_handle* h, int64_t cycles);
+
 /* Convert n elements between dtypes (device to device, round to nearest). */
 gvt_status gvt_convert(const void* src, int32_t src_dtype, void* dst, int32_t dst_dtype,
                        int64_t n, void* stream);

@@ -607,7 +607,18 @@ gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const voi
         set_error("gvt_tc_gemm_bf16: NULL argument");
         return GVT_ERR_INVALID_ARG;
     }
-    return tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, handle_err_word(h), as_stream(stream), h->tc_pairs);
+    return tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, handle_err_word(h), as_stream(stream), h->tc_pairs,
+                        h->tc_stall_cycles);
+}
+
+gvt_status gvt_set_tc_stall_test(gvt_handle* h, int64_t cycles)
+{
+    if (!h || cycles < 0 || cycles > 4000000000ll) {
+        set_error("gvt_set_tc_stall_test: bad handle or cycle count (0 .. 4e9)");
+        return GVT_ERR_INVALID_ARG;
+    }
+    h->tc_stall_cycles = cycles;
+    return GVT_OK;
 }
 
 gvt_status gvt_convert(const void* src, int32_t src_dtype, void* dst, int32_t dst_dtype, int64_t n,

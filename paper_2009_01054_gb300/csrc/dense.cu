@@ -326,7 +326,7 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
 }
 
 gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
-                      cudaStream_t s, int pair_mode)
+                      cudaStream_t s, int pair_mode, long long stall_cycles)
 {
     if (a.kp != b.kp || a.parts != b.parts) {
         set_error("dense stage: operand widths differ");
@@ -334,7 +334,7 @@ gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, fl
     }
     const int64_t kw = (int64_t)a.parts * a.kp;
     return tc_gemm(a.data, kw, b.data, kw, C, ldc, a.rows, b.rows, kw, f16,
-                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s, pair_mode);
+                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s, pair_mode, stall_cycles);
 }
 
 gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s)

@@ -94,6 +94,7 @@ struct gvt_handle {
     bool stats_on = false;
     int stage1_engine = 0;          // gvt_stage1_engine for FP32 products
     int tc_pairs = GVT_TC_PAIRS_AUTO;   // gvt_tc_pairs: tile form of the tensor-core GEMM
+    long long tc_stall_cycles = 0;      // > 0: test stall of the GEMMs' timeout path (gvt_set_tc_stall_test)
     std::map<std::tuple<int, int64_t, int>, int> batch_tune;   // batched stage-1 tile choice
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;
@@ -259,12 +260,14 @@ size_t dtype_size(int dt);
 inline int* handle_err_word(gvt_handle* h) { return static_cast<int*>(h->status.ptr) + 16; }
 // C[M x N] = row_scale[m] col_scale[n] (A B^T)[m, n] on the tensor cores; A, B both FP16 (f16) or
 // both BF16, K-major; the scales may be NULL; pair_mode is a gvt_tc_pairs value.
+// stall_cycles > 0 (one-SM form only): the test stall of the timeout path (the GEMM's MMA thread
+// waits that many cycles on a barrier nothing arrives on; the result is then invalid).
 gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                    int64_t N, int64_t K, bool f16, const float* row_scale, const float* col_scale, int* err,
-                   cudaStream_t s, int pair_mode);
+                   cudaStream_t s, int pair_mode, long long stall_cycles = 0);
 // C[M x N] (FP32, ld ldc) = A[M x K] B[N x K]^T, A and B BF16 K-major (K % 64 == 0).
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
-                        int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode);
+                        int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode, long long stall_cycles = 0);
 
 // A split operand of the dense stages: rows x (parts * kp) 16-bit values ([hi|hi|lo] or
 // [hi|lo|hi] when parts == 3, [hi] when parts == 1), and for FP16 splits the inverse
@@ -288,7 +291,7 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
                          int64_t X, bool f16, const DenseOperand& dst, float* wide_scratch, cudaStream_t s);
 // C[a.rows x b.rows] = a b^T with the FP16 row scales applied
 gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
-                      cudaStream_t s, int pair_mode);
+                      cudaStream_t s, int pair_mode, long long stall_cycles = 0);
 
 // ---------------------------------------------------------------- pairwise driver
 // u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).

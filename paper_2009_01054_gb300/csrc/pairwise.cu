@@ -393,7 +393,8 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             {
                 StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * X * parts * kp,
                              2.0 * parts * kp * (Y + X) + 4.0 * Y * X, (sq_mode(g.fb) ? 3.0 : 2.0) * Y * E);
-                GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s, h->tc_pairs));
+                GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(S), lds, handle_err_word(h), s, h->tc_pairs,
+                                     h->tc_stall_cycles));
             }
         } else if (g.fb == GVT_FACTOR_IDENTITY) {
             GVT_CHECK(vec_zero<T>(S, Y * lds, s));
@@ -456,7 +457,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                     }
                     StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * mb * Y * parts * kp,
                                  2.0 * parts * kp * (mb + Y) + 4.0 * mb * Y, c2_useful);
-                    GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs));
+                    GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs, h->tc_stall_cycles));
                     c_ptr = Fa->data;
                     c_sq = sq_mode(g2.fa);
                     c_rows = mb;

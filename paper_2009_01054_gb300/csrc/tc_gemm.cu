@@ -36,10 +36,13 @@
 // hop to every ring slot and measured half the speed.)
 // Epilogue: the folding warps stage the 128 x BN tile in the (then idle) ring
 // memory and store it row by row, 32 consecutive columns per warp instruction.
-// Every wait on an mbarrier is bounded by a clock budget; on expiry the
-// thread records GVT_ERR_TIMEOUT in a device error word, the kernel waits
-// (bounded) for the copies it issued and for its MMAs, frees its TMEM and
-// returns.
+// Every wait on an mbarrier is bounded by a clock budget, and the waits of the
+// pipeline also end as soon as another thread of the CTA has timed out; on
+// expiry the thread records GVT_ERR_TIMEOUT in a device error word, the kernel
+// waits (bounded) for the copies it issued and for its MMAs, frees its TMEM
+// and returns.  A test switch (stall_cycles > 0, one-SM form only) makes the
+// MMA thread first wait on a barrier that nothing arrives on, for that many
+// cycles, so that the timeout path runs on demand.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -65,7 +68,8 @@ struct TcShared {
     uint64_t empty[TC_MAX_STAGES];
     uint64_t acc_full[2];    // chunk accumulated into TMEM buffer b
     uint64_t acc_empty[2];   // folding warps have read buffer b
-    uint64_t mma_done;       // every MMA this CTA issued has completed (SM-pair form)
+    uint64_t mma_done;       // every MMA this CTA issued has completed
+    uint64_t never;          // nothing arrives on it: the target of the test stall
     uint32_t tmem_base;
     int timeout;
     int issued;      // TMA stage loads issued
@@ -120,13 +124,17 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
+// Bounded wait for the phase with the given parity; false on timeout, or as soon as *abort (a
+// shared-memory flag, may be NULL) is set by another thread that timed out.
 template <bool CLUSTER = false>
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort = nullptr,
+                                          long long budget = TC_TIMEOUT_CYCLES)
 {
     const long long t0 = clock64();
-    while (!(CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)))
-        if (clock64() - t0 > TC_TIMEOUT_CYCLES) return false;
+    while (!(CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))) {
+        if (clock64() - t0 > budget) return false;
+        if (abort && *(const volatile int*)abort) return false;
+    }
     return true;
 }
 
@@ -333,7 +341,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t ldc, int M, int N, int kb_total, int kb_per_split,
                int atomic_out, const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-               int* __restrict__ err)
+               int* __restrict__ err, long long stall_cycles)
 {
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "UMMA N");
     static_assert(!PAIR || BN % 16 == 0, "UMMA N for M = 256");
@@ -375,6 +383,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             mbar_init(&sh->acc_empty[b], PAIR ? 2 * TC_FOLD_WARPS : TC_FOLD_WARPS);
         }
         mbar_init(&sh->mma_done, 1);
+        mbar_init(&sh->never, 1);
         sh->timeout = 0;
         sh->issued = 0;
         sh->consumed = 0;
@@ -396,7 +405,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             int i = 0;
             for (; i < nkb; ++i) {
                 const int st = i % TC_STAGES;
-                if (i >= TC_STAGES && !mbar_wait(&sh->empty[st], ((i / TC_STAGES) - 1) & 1)) {
+                if (i >= TC_STAGES && !mbar_wait(&sh->empty[st], ((i / TC_STAGES) - 1) & 1, &sh->timeout)) {
                     atomicExch(&sh->timeout, 1);
                     break;
                 }
@@ -422,9 +431,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             constexpr uint32_t idesc = idesc_f16kind_f32<BN, F16, PAIR>();
             int i = 0;
             bool ok = true;
+            if (!PAIR && stall_cycles > 0 && !mbar_wait(&sh->never, 0, nullptr, stall_cycles)) {
+                atomicExch(&sh->timeout, 1);   // the test stall: nothing arrives on `never`
+                ok = false;
+            }
             for (int c = 0; c < nchunks && ok; ++c) {
                 const int b = c & 1;
-                if (c >= 2 && !mbar_wait<PAIR>(&sh->acc_empty[b], ((c >> 1) - 1) & 1)) {
+                if (c >= 2 && !mbar_wait<PAIR>(&sh->acc_empty[b], ((c >> 1) - 1) & 1, &sh->timeout)) {
                     atomicExch(&sh->timeout, 1);
                     break;
                 }
@@ -433,7 +446,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 const int i_end = min(nkb, (c + 1) * TC_CHUNK);
                 for (; i < i_end; ++i) {
                     const int st = i % TC_STAGES;
-                    if (!mbar_wait<PAIR>(&sh->full[st], (i / TC_STAGES) & 1) || *(volatile int*)&sh->timeout) {
+                    if (!mbar_wait<PAIR>(&sh->full[st], (i / TC_STAGES) & 1, &sh->timeout) ||
+                        *(volatile int*)&sh->timeout) {
                         atomicExch(&sh->timeout, 1);
                         ok = false;
                         break;
@@ -454,6 +468,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 // the peer's shared memory and TMEM stay in use until these MMAs complete
                 umma_commit_local_pair(&sh->mma_done);
                 if (!mbar_wait(&sh->mma_done, 0)) atomicExch(&sh->timeout, 1);
+            } else if (i > 0) {
+                // TMEM is freed at the end: every MMA issued must have completed by then, also
+                // when a timeout left its accumulator unread
+                umma_commit<false>(&sh->mma_done);
+                if (!mbar_wait(&sh->mma_done, 0)) atomicExch(&sh->timeout, 1);
             }
         }
     } else {
@@ -469,7 +488,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         bool good = nkb > 0;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            if (!mbar_wait(&sh->acc_full[b], (c >> 1) & 1)) {
+            if (!mbar_wait(&sh->acc_full[b], (c >> 1) & 1, &sh->timeout)) {
                 atomicExch(&sh->timeout, 1);
                 good = false;
                 break;
@@ -601,7 +620,7 @@ gvt_status make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K,
 
 template <int BN, bool F16, bool PAIR>
 gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M, int64_t N,
-                     int64_t K, const float* rs, const float* cs, int* err, cudaStream_t s)
+                     int64_t K, const float* rs, const float* cs, int* err, long long stall, cudaStream_t s)
 {
     const int pairs = (int)((M + 2 * TC_BM - 1) / (2 * TC_BM));
     const int gx = PAIR ? 2 * pairs : (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
@@ -633,26 +652,27 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     cfg.attrs = attr;
     cfg.numAttrs = PAIR ? 1 : 0;
     GVT_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, C, ldc, (int)M, (int)N, kb_total, kb_per, atomic_out, rs, cs,
-                                err));
+                                err, stall));
     GVT_LAUNCH_CHECK("tc_gemm");
     return GVT_OK;
 }
 
 template <bool F16, bool PAIR>
 gvt_status launch_tc_bn(int BN, const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M,
-                        int64_t N, int64_t K, const float* rs, const float* cs, int* err, cudaStream_t s)
+                        int64_t N, int64_t K, const float* rs, const float* cs, int* err, long long stall,
+                        cudaStream_t s)
 {
-    if (BN == 64) return launch_tc<64, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    if (BN == 128) return launch_tc<128, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    if (BN == 224) return launch_tc<224, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    return launch_tc<256, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+    if (BN == 64) return launch_tc<64, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
+    if (BN == 128) return launch_tc<128, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
+    if (BN == 224) return launch_tc<224, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
+    return launch_tc<256, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
 }
 
 }  // namespace
 
 gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                    int64_t N, int64_t K, bool f16, const float* row_scale, const float* col_scale, int* err,
-                   cudaStream_t s, int pair_mode)
+                   cudaStream_t s, int pair_mode, long long stall_cycles)
 {
     if (M <= 0 || N <= 0) return GVT_OK;
     if (K <= 0 || K % TC_BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N ||
@@ -669,6 +689,10 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
     // SM pairs only on request: on GB300 both forms reach the same rate on these shapes (the
     // pair form reads 30 % fewer operand bytes per SM, but the loads are not the bound)
     const bool pair = pair_mode == GVT_TC_PAIRS_ON;
+    if (stall_cycles > 0 && pair) {
+        set_error("tc_gemm: the test stall exists in the one-SM tile form only");
+        return GVT_ERR_UNSUPPORTED;
+    }
     // widest N tile that still gives >= 64 output tiles (fewer split-K partial sums to reduce);
     // 224 instead of 256 where it fills more of the 152 SMs in the same single wave
     const int64_t gx = (M + TC_BM - 1) / TC_BM;
@@ -686,16 +710,16 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
     const float* rs = row_scale;
     const float* cs = col_scale;
     if (f16)
-        return pair ? launch_tc_bn<true, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s)
-                    : launch_tc_bn<true, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s);
-    return pair ? launch_tc_bn<false, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s)
-                : launch_tc_bn<false, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, s);
+        return pair ? launch_tc_bn<true, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s)
+                    : launch_tc_bn<true, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s);
+    return pair ? launch_tc_bn<false, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s)
+                : launch_tc_bn<false, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s);
 }
 
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
-                        int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode)
+                        int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode, long long stall_cycles)
 {
-    return tc_gemm(A, lda, B, ldb, C, ldc, M, N, K, false, nullptr, nullptr, err, s, pair_mode);
+    return tc_gemm(A, lda, B, ldb, C, ldc, M, N, K, false, nullptr, nullptr, err, s, pair_mode, stall_cycles);
 }
 
 }  // namespace gvt

@@ -141,6 +141,7 @@ SIGNATURES = [
                                     c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     ("gvt_check_device_errors", c_i32, [c_vp, c_vp]),
     ("gvt_tc_gemm_bf16", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]),
+    ("gvt_set_tc_stall_test", c_i32, [c_vp, c_i64]),
     ("gvt_matvec_static", c_i32, [c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
                                   _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp, c_i32, c_vp]),
 ]
@@ -417,6 +418,12 @@ def gvt_check_device_errors(h, stream):
 
 def gvt_tc_gemm_bf16(h, A, lda, B, ldb, C, ldc, M, N, K, stream):
     _call("gvt_tc_gemm_bf16", h, A, lda, B, ldb, C, ldc, M, N, K, stream)
+
+
+def gvt_set_tc_stall_test(h, cycles):
+    """Test of the tensor-core timeout path (see include/gvt.h): cycles > 0 makes every GEMM of this
+    handle stall on a barrier nothing arrives on; 0 turns it off."""
+    _call("gvt_set_tc_stall_test", h, int(cycles))
 
 
 def gvt_solve_opts_default():
