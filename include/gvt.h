@@ -532,9 +532,15 @@ gvt_status gvt_krr_minres_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* d
  * output.  The paper solves with an unpreconditioned method (Sec. 6); this is
  * an addition used with flexible CG; the true FP64 residual still decides convergence.
  * Parameters: gvt_precond_num_params() floats, layout W1[128x6] b1[128]
- * W2[128x128] b2[128] W3[33x128] b3[33] (row-major).
+ * W2[128x128] b2[128] W3[33x128] b3[33] (row-major), held in FP32.
  */
 int64_t gvt_precond_num_params(void);
+
+/* Arithmetic of the network's forward and backward passes: GVT_BF16 (the default: every layer
+ * and backward product a tcgen05 GEMM on BF16 operands with FP32 accumulation; gradients
+ * reproducible to rounding) or GVT_F32 (SIMT, FP32 throughout; bitwise reproducible).  The
+ * low-rank algebra, the loss and the application of P are FP32/FP64 in both. */
+gvt_status gvt_precond_set_dtype(gvt_precond* p, int32_t dtype);
 
 /* Create for a training plan, the pairwise kernel `desc` and its FP64 kernel
  * matrices (the features need two products with K), with initial parameters

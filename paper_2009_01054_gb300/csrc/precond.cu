@@ -17,11 +17,24 @@
 // the exact solver with the loss mean_k ||P r_k - e_k||^2 / ||e_k||^2, by the
 // forward / backward kernels below and Adam.
 //
-// The MLP kernels work on tiles of 32 pairs held in shared memory (lane = pair,
-// warp = a block of 16 hidden units).  The backward kernel recomputes the
-// forward pass of its tile and keeps the weight gradients of all its tiles in
-// registers; blocks write partial gradients that one kernel sums in a fixed
-// order, so training is bitwise reproducible.
+// Two arithmetics for the network:
+//  * BF16 on the tensor cores (the default): every layer and every backward
+//    product is one call of the library's tcgen05 GEMM (BF16 operands, FP32
+//    accumulation in tensor memory).  Forward: Z1 = [x | 1] W1'^T (the bias b1 rides
+//    on a constant-one feature), H1 = relu(Z1); Z2 = H1 W2^T, H2 = relu(Z2 + b2);
+//    O = H2 W3^T + b3.  Backward: dH2 = dO W3, dZ2 = dH2 [H2 > 0], dH1 = dZ2 W2,
+//    dZ1 = dH1 [H1 > 0], and the weight gradients dW = dZ^T H as GEMMs over the pairs
+//    (K = n, split across SMs), from pair-contiguous transposed copies of the
+//    activations that the elementwise passes write beside the row-major ones.
+//    The bias gradients db2, db3 are column sums in FP64.  The split-K reduction
+//    adds with atomics, so BF16 training is reproducible to rounding, not bitwise.
+//  * FP32 SIMT (gvt_precond_set_dtype GVT_F32): tiles of 32 pairs held in
+//    shared memory (lane = pair, warp = a block of 16 hidden units).  The backward
+//    kernel recomputes the forward pass of its tile and keeps the weight gradients
+//    of all its tiles in registers; blocks write partial gradients that one kernel
+//    sums in a fixed order, so FP32 training is bitwise reproducible.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <vector>
 
@@ -353,6 +366,197 @@ __global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ g,
     }
 }
 
+// ------------------------------------------------------------------ BF16 tensor-core MLP
+// Padded widths of the GEMM operands: the 6 features and the constant one in 64 columns, the
+// 33 outputs in 64 columns (forward) and 128 rows (the transposed output gradient).
+constexpr int XW = 64;       // [x | 1 | 0...] width
+constexpr int OW = 64;       // output width of the layer-3 GEMM
+constexpr int OTR = 128;     // rows of the transposed output gradient
+
+__device__ __forceinline__ __nv_bfloat16 bf(float x) { return __float2bfloat16_rn(x); }
+
+// BF16 weight operands from the FP32 parameters (every one K-major for the GEMM):
+// W1b[u][f] = W1[u][f] (f < 6), b1[u] (f = 6), 0; W2b = W2; W2T[k][u] = W2[u][k];
+// W3b[o][k] = W3[o][k] (o < 33), 0; W3T[k][o] = W3[o][k] (o < 33), 0.
+__global__ void pack_weights_kernel(const float* __restrict__ th, __nv_bfloat16* __restrict__ W1b,
+                                    __nv_bfloat16* __restrict__ W2b, __nv_bfloat16* __restrict__ W2T,
+                                    __nv_bfloat16* __restrict__ W3b, __nv_bfloat16* __restrict__ W3T)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int e = tid; e < PH * XW; e += nt) {
+        const int u = e / XW, f = e % XW;
+        W1b[e] = bf(f < PF ? th[OFF_W1 + u * PF + f] : f == PF ? th[OFF_B1 + u] : 0.f);
+    }
+    for (int e = tid; e < PH * PH; e += nt) {
+        const int u = e / PH, k = e % PH;
+        W2b[e] = bf(th[OFF_W2 + e]);
+        W2T[k * PH + u] = bf(th[OFF_W2 + e]);
+    }
+    for (int e = tid; e < OW * PH; e += nt) {
+        const int o = e / PH, k = e % PH;
+        const float w = o < PO ? th[OFF_W3 + o * PH + k] : 0.f;
+        W3b[e] = bf(w);
+        W3T[k * OW + o] = bf(w);
+    }
+}
+
+// Xb[i] = [x_i | 1 | 0...] (n x 64), XbT its transpose (64 x np, zero past n)
+__global__ void pack_x_kernel(const float* __restrict__ X, int64_t n, int64_t np, __nv_bfloat16* __restrict__ Xb,
+                              __nv_bfloat16* __restrict__ XbT)
+{
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * XW; e += nt) {
+        const int64_t i = e / XW;
+        const int f = (int)(e % XW);
+        Xb[e] = bf(f < PF ? X[i * PF + f] : f == PF ? 1.f : 0.f);
+    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)XW * np; e += nt) {
+        const int f = (int)(e / np);
+        const int64_t i = e % np;
+        XbT[e] = bf(i < n && f < PF ? X[i * PF + f] : (i < n && f == PF) ? 1.f : 0.f);
+    }
+}
+
+// One block per 32 pairs: h = relu(z + b) (b may be NULL) to H (n x 128) and, if HT, to its
+// transpose HT (128 x np; zero for the padding pairs n <= i < np).
+constexpr int ACT_ROWS = 32;
+__global__ void __launch_bounds__(256)
+act_kernel(const float* __restrict__ Z, const float* __restrict__ th_bias, int64_t n, int64_t np,
+           __nv_bfloat16* __restrict__ H, __nv_bfloat16* __restrict__ HT)
+{
+    __shared__ float tile[ACT_ROWS][PH + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * ACT_ROWS;
+    for (int e = threadIdx.x; e < ACT_ROWS * PH; e += blockDim.x) {
+        const int r = e / PH, u = e % PH;
+        const int64_t i = i0 + r;
+        float h = 0.f;
+        if (i < n) {
+            h = fmaxf(Z[i * PH + u] + (th_bias ? th_bias[u] : 0.f), 0.f);
+            H[i * PH + u] = bf(h);
+        }
+        tile[r][u] = h;
+    }
+    if (!HT) return;
+    __syncthreads();
+    for (int e = threadIdx.x; e < ACT_ROWS * PH; e += blockDim.x) {
+        const int u = e / ACT_ROWS, r = e % ACT_ROWS;
+        const int64_t i = i0 + r;
+        if (i < np) HT[(int64_t)u * np + i] = bf(tile[r][u]);
+    }
+}
+
+// O[i][o] = Ob[i][o] + b3[o] (o < 33), s_i = sqrt(scale softplus(o_0))
+__global__ void out3_kernel(const float* __restrict__ Ob, const float* __restrict__ th, int64_t n,
+                            float* __restrict__ O, float* __restrict__ s_out, float scale)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * PO;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / PO;
+        const int o = (int)(e % PO);
+        const float v = Ob[i * OW + o] + th[OFF_B3 + o];
+        O[e] = v;
+        if (o == 0) s_out[i] = sqrtf(scale * softplusf(v));
+    }
+}
+
+// output gradient to the GEMM operands: dOb (n x 64, zero past 33) and dOT (128 x np, zero past
+// 33 rows and n columns)
+__global__ void pack_go_kernel(const float* __restrict__ GO, int64_t n, int64_t np, __nv_bfloat16* __restrict__ dOb,
+                               __nv_bfloat16* __restrict__ dOT)
+{
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * OW; e += nt) {
+        const int64_t i = e / OW;
+        const int o = (int)(e % OW);
+        dOb[e] = bf(o < PO ? GO[i * PO + o] : 0.f);
+    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)OTR * np; e += nt) {
+        const int o = (int)(e / np);
+        const int64_t i = e % np;
+        dOT[e] = bf(o < PO && i < n ? GO[i * PO + o] : 0.f);
+    }
+}
+
+// One block per 32 pairs: g = D [H > 0] to G (n x 128, if G) and GT (128 x np); per-block
+// column sums of g (FP64) into part[block][128] (if part).
+__global__ void __launch_bounds__(256)
+relu_grad_kernel(const float* __restrict__ D, const __nv_bfloat16* __restrict__ Hm, int64_t n, int64_t np,
+                 __nv_bfloat16* __restrict__ G, __nv_bfloat16* __restrict__ GT, double* __restrict__ part)
+{
+    __shared__ float tile[ACT_ROWS][PH + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * ACT_ROWS;
+    for (int e = threadIdx.x; e < ACT_ROWS * PH; e += blockDim.x) {
+        const int r = e / PH, u = e % PH;
+        const int64_t i = i0 + r;
+        float g = 0.f;
+        if (i < n) {
+            g = __bfloat162float(Hm[i * PH + u]) > 0.f ? D[i * PH + u] : 0.f;
+            if (G) G[i * PH + u] = bf(g);
+        }
+        tile[r][u] = g;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ACT_ROWS * PH; e += blockDim.x) {
+        const int u = e / ACT_ROWS, r = e % ACT_ROWS;
+        const int64_t i = i0 + r;
+        if (i < np) GT[(int64_t)u * np + i] = bf(tile[r][u]);
+    }
+    if (part && threadIdx.x < PH) {
+        double acc = 0.0;
+        for (int r = 0; r < ACT_ROWS; ++r) acc += (double)tile[r][threadIdx.x];
+        part[(int64_t)blockIdx.x * PH + threadIdx.x] = acc;
+    }
+}
+
+// column sums of GO (n x 33) per block of 256 pairs (FP64)
+__global__ void go_colsum_kernel(const float* __restrict__ GO, int64_t n, double* __restrict__ part)
+{
+    __shared__ double sh[8][PO];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double a0 = 0.0, a1 = 0.0;   // columns lane and 32 + lane (lane 0 only)
+    for (int64_t i = (int64_t)blockIdx.x * 256 + w; i < n && i < (int64_t)(blockIdx.x + 1) * 256; i += 8) {
+        a0 += GO[i * PO + lane];
+        if (lane == 0) a1 += GO[i * PO + 32];
+    }
+    sh[w][lane] = a0;
+    if (lane == 0) sh[w][32] = a1;
+    __syncthreads();
+    if (threadIdx.x < PO) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
+        part[(int64_t)blockIdx.x * PO + threadIdx.x] = t;
+    }
+}
+
+// gradient vector from the GEMM outputs and the bias partial sums (summed in block order)
+__global__ void grad_assemble_kernel(const float* __restrict__ dW1g, const float* __restrict__ dW2g,
+                                     const float* __restrict__ dW3g, const double* __restrict__ db2part, int nb2,
+                                     const double* __restrict__ db3part, int nb3, float* __restrict__ grad)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < NPARAM; j += gridDim.x * blockDim.x) {
+        float g;
+        if (j < OFF_B1) {
+            const int u = (j - OFF_W1) / PF, f = (j - OFF_W1) % PF;
+            g = dW1g[u * XW + f];
+        } else if (j < OFF_W2) {
+            g = dW1g[(j - OFF_B1) * XW + PF];
+        } else if (j < OFF_B2) {
+            g = dW2g[j - OFF_W2];
+        } else if (j < OFF_W3) {
+            double t = 0.0;
+            for (int b = 0; b < nb2; ++b) t += db2part[(int64_t)b * PH + (j - OFF_B2)];
+            g = (float)t;
+        } else if (j < OFF_B3) {
+            g = dW3g[j - OFF_W3];   // rows o < 33 of the 128 x 128 product, row-major like W3
+        } else {
+            double t = 0.0;
+            for (int b = 0; b < nb3; ++b) t += db3part[(int64_t)b * PO + (j - OFF_B3)];
+            g = (float)t;
+        }
+        grad[j] = g;
+    }
+}
+
 // ------------------------------------------------------------------ low-rank algebra
 constexpr int RB = 256;   // blocks of the reduction kernels
 
@@ -625,6 +829,16 @@ struct gvt_precond {
     float mu[gvt::PF], sd[gvt::PF];
     double scale = 1.0;      // D = scale * softplus(o_0)
     bool ready = false;      // O, s, L hold the current parameters' outputs
+    int dtype = GVT_BF16;    // arithmetic of the network: GVT_BF16 (tensor cores) or GVT_F32 (SIMT)
+    // BF16 path (allocated on first use): operands of the GEMMs, np = n rounded up to 64
+    int64_t np = 0;
+    bool bf_ready = false;   // buffers allocated and the features packed
+    bool acts_t = false;     // the transposed activations of the current parameters are stored
+    __nv_bfloat16 *Xb = nullptr, *XbT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *H2T = nullptr;
+    __nv_bfloat16 *dOb = nullptr, *dOT = nullptr, *dZ2 = nullptr, *dZ2T = nullptr, *dZ1T = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2T = nullptr, *W3b = nullptr, *W3T = nullptr;
+    float *Z = nullptr, *Ob = nullptr, *dW1g = nullptr, *dW2g = nullptr, *dW3g = nullptr;
+    double *db2part = nullptr, *db3part = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -656,14 +870,103 @@ gvt_status mlp_smem_attr()
     return GVT_OK;
 }
 
-// O, s, L for the current parameters
-gvt_status forward(gvt_precond* p, cudaStream_t st)
+unsigned ew_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+// BF16 path: buffers and the packed features, once
+gvt_status bf16_setup(gvt_precond* p, cudaStream_t st)
 {
-    GVT_CHECK(mlp_smem_attr());
-    mlp_forward_kernel<<<kMlpBlocks * 1, PT, sizeof(MlpSmem), st>>>(p->theta, p->X, p->n, p->O, p->s, (float)p->scale);
+    if (p->bf_ready) return GVT_OK;
+    const int64_t n = std::max<int64_t>(p->n, 1);
+    p->np = (n + 63) / 64 * 64;
+    const int64_t np = p->np;
+    GVT_CHECK(palloc(p, &p->Xb, n * XW)); GVT_CHECK(palloc(p, &p->XbT, XW * np));
+    GVT_CHECK(palloc(p, &p->H1, n * PH)); GVT_CHECK(palloc(p, &p->H1T, PH * np));
+    GVT_CHECK(palloc(p, &p->H2, n * PH)); GVT_CHECK(palloc(p, &p->H2T, PH * np));
+    GVT_CHECK(palloc(p, &p->dOb, n * OW)); GVT_CHECK(palloc(p, &p->dOT, OTR * np));
+    GVT_CHECK(palloc(p, &p->dZ2, n * PH)); GVT_CHECK(palloc(p, &p->dZ2T, PH * np)); GVT_CHECK(palloc(p, &p->dZ1T, PH * np));
+    GVT_CHECK(palloc(p, &p->W1b, PH * XW)); GVT_CHECK(palloc(p, &p->W2b, PH * PH)); GVT_CHECK(palloc(p, &p->W2T, PH * PH));
+    GVT_CHECK(palloc(p, &p->W3b, OW * PH)); GVT_CHECK(palloc(p, &p->W3T, PH * OW));
+    GVT_CHECK(palloc(p, &p->Z, n * PH)); GVT_CHECK(palloc(p, &p->Ob, n * OW));
+    GVT_CHECK(palloc(p, &p->dW1g, PH * XW)); GVT_CHECK(palloc(p, &p->dW2g, PH * PH)); GVT_CHECK(palloc(p, &p->dW3g, OTR * PH));
+    GVT_CHECK(palloc(p, &p->db2part, (np / ACT_ROWS) * PH));
+    GVT_CHECK(palloc(p, &p->db3part, ((n + 255) / 256) * PO));
+    if (p->n > 0) {
+        pack_x_kernel<<<ew_grid(XW * np), 256, 0, st>>>(p->X, p->n, np, p->Xb, p->XbT);
+        GVT_LAUNCH_CHECK("preconditioner pack features");
+    }
+    p->bf_ready = true;
+    return GVT_OK;
+}
+
+// C (rows x cols, ld ldc) = A B^T on the tensor cores (BF16 operands, K-major)
+gvt_status gemm_bf16(gvt_precond* p, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
+                     float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, cudaStream_t st)
+{
+    return tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, handle_err_word(p->h), st, GVT_TC_PAIRS_OFF);
+}
+
+// BF16 forward: O and s (and, with want_t, the transposed activations for the backward GEMMs)
+gvt_status forward_bf16(gvt_precond* p, bool want_t, cudaStream_t st)
+{
+    GVT_CHECK(bf16_setup(p, st));
+    const int64_t n = p->n, np = p->np;
+    if (n == 0) return GVT_OK;
+    pack_weights_kernel<<<64, 256, 0, st>>>(p->theta, p->W1b, p->W2b, p->W2T, p->W3b, p->W3T);
+    GVT_LAUNCH_CHECK("preconditioner pack weights");
+    const unsigned ab = (unsigned)(np / ACT_ROWS);
+    GVT_CHECK(gemm_bf16(p, p->Xb, XW, p->W1b, XW, p->Z, PH, n, PH, XW, st));
+    act_kernel<<<ab, 256, 0, st>>>(p->Z, nullptr, n, np, p->H1, want_t ? p->H1T : nullptr);
+    GVT_LAUNCH_CHECK("preconditioner layer 1");
+    GVT_CHECK(gemm_bf16(p, p->H1, PH, p->W2b, PH, p->Z, PH, n, PH, PH, st));
+    act_kernel<<<ab, 256, 0, st>>>(p->Z, p->theta + OFF_B2, n, np, p->H2, want_t ? p->H2T : nullptr);
+    GVT_LAUNCH_CHECK("preconditioner layer 2");
+    GVT_CHECK(gemm_bf16(p, p->H2, PH, p->W3b, PH, p->Ob, OW, n, OW, PH, st));
+    out3_kernel<<<ew_grid(n * PO), 256, 0, st>>>(p->Ob, p->theta, n, p->O, p->s, (float)p->scale);
+    GVT_LAUNCH_CHECK("preconditioner layer 3");
+    p->acts_t = want_t;
+    return GVT_OK;
+}
+
+// BF16 backward from GO = dL/do (n x 33): p->grad (the forward with want_t must be current)
+gvt_status backward_bf16(gvt_precond* p, cudaStream_t st)
+{
+    const int64_t n = p->n, np = p->np;
+    if (n == 0) return GVT_OK;
+    const unsigned ab = (unsigned)(np / ACT_ROWS);
+    const int nb3 = (int)((n + 255) / 256);
+    pack_go_kernel<<<ew_grid(OTR * np), 256, 0, st>>>(p->GO, n, np, p->dOb, p->dOT);
+    go_colsum_kernel<<<nb3, 256, 0, st>>>(p->GO, n, p->db3part);
+    GVT_LAUNCHED(2, "preconditioner output gradient");
+    GVT_CHECK(gemm_bf16(p, p->dOb, OW, p->W3T, OW, p->Z, PH, n, PH, OW, st));            // dH2
+    relu_grad_kernel<<<ab, 256, 0, st>>>(p->Z, p->H2, n, np, p->dZ2, p->dZ2T, p->db2part);
+    GVT_LAUNCH_CHECK("preconditioner layer-2 gradient");
+    GVT_CHECK(gemm_bf16(p, p->dZ2, PH, p->W2T, PH, p->Z, PH, n, PH, PH, st));            // dH1
+    relu_grad_kernel<<<ab, 256, 0, st>>>(p->Z, p->H1, n, np, nullptr, p->dZ1T, nullptr);
+    GVT_LAUNCH_CHECK("preconditioner layer-1 gradient");
+    GVT_CHECK(gemm_bf16(p, p->dZ1T, np, p->XbT, np, p->dW1g, XW, PH, XW, np, st));       // dW1 | db1
+    GVT_CHECK(gemm_bf16(p, p->dZ2T, np, p->H1T, np, p->dW2g, PH, PH, PH, np, st));       // dW2
+    GVT_CHECK(gemm_bf16(p, p->dOT, np, p->H2T, np, p->dW3g, PH, OTR, PH, np, st));       // dW3
+    grad_assemble_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(p->dW1g, p->dW2g, p->dW3g, p->db2part, (int)ab,
+                                                                p->db3part, nb3, p->grad);
+    GVT_LAUNCH_CHECK("preconditioner gradient");
+    return GVT_OK;
+}
+
+// O, s, L for the current parameters (with want_t, in BF16, also the activations the backward
+// GEMMs read)
+gvt_status forward(gvt_precond* p, cudaStream_t st, bool want_t = false)
+{
+    if (p->dtype == GVT_BF16) {
+        GVT_CHECK(forward_bf16(p, want_t, st));
+    } else {
+        GVT_CHECK(mlp_smem_attr());
+        mlp_forward_kernel<<<kMlpBlocks * 1, PT, sizeof(MlpSmem), st>>>(p->theta, p->X, p->n, p->O, p->s,
+                                                                        (float)p->scale);
+        GVT_LAUNCH_CHECK("preconditioner forward");
+    }
     gram_kernel<<<RB, 256, 0, st>>>(p->O, p->n, p->red);
     chol_kernel<<<1, PR, 0, st>>>(p->red, RB, p->L);
-    GVT_LAUNCHED(3, "preconditioner forward");
+    GVT_LAUNCHED(2, "preconditioner forward");
     p->ready = true;
     return GVT_OK;
 }
@@ -691,7 +994,7 @@ namespace {
 // loss and dL/dtheta (into p->grad) for K <= KMAX pairs
 gvt_status loss_grad(gvt_precond* p, const float* R, const float* E, int K, cudaStream_t st)
 {
-    GVT_CHECK(forward(p, st));
+    GVT_CHECK(forward(p, st, true));
     const int64_t n = p->n;
     double* part = p->red;                       // RB * 32 * K
     double* epart = p->red + (size_t)RB * PR * KMAX;
@@ -700,9 +1003,11 @@ gvt_status loss_grad(gvt_precond* p, const float* R, const float* E, int K, cuda
     loss_pass1_kernel<<<RB, 256, 0, st>>>(p->O, p->s, R, E, n, K, p->H, p->ee, p->lpart, part);
     loss_mid_kernel<<<1, 256, 0, st>>>(p->lpart, part, RB, K, p->L, p->H, p->Gh, p->sym, p->loss);
     loss_pass2_kernel<<<RB * 2, 256, 0, st>>>(p->O, p->s, R, E, n, K, p->H, p->Gh, p->sym, p->ee, p->GO, p->scale);
+    GVT_LAUNCHED(5, "preconditioner loss");
+    if (p->dtype == GVT_BF16) return backward_bf16(p, st);
     mlp_backward_kernel<<<kMlpBlocks, PT, sizeof(MlpSmem), st>>>(p->theta, p->X, n, p->GO, p->gpart);
     grad_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(p->gpart, kMlpBlocks, p->grad);
-    GVT_LAUNCHED(7, "preconditioner loss gradient");
+    GVT_LAUNCHED(2, "preconditioner backward");
     return GVT_OK;
 }
 }  // namespace
@@ -803,6 +1108,19 @@ gvt_status gvt_precond_destroy(gvt_precond* p)
 }
 
 int64_t gvt_precond_num_params(void) { return NPARAM; }
+
+gvt_status gvt_precond_set_dtype(gvt_precond* p, int32_t dtype)
+{
+    if (!p || (dtype != GVT_BF16 && dtype != GVT_F32)) {
+        set_error("gvt_precond_set_dtype: bad preconditioner or dtype (GVT_BF16 or GVT_F32)");
+        return GVT_ERR_INVALID_ARG;
+    }
+    if (dtype != p->dtype) {
+        p->dtype = dtype;
+        p->ready = false;
+    }
+    return GVT_OK;
+}
 
 gvt_status gvt_precond_params(gvt_precond* p, float* host, int32_t set, void* stream)
 {

@@ -127,6 +127,7 @@ SIGNATURES = [
     ("gvt_factor_cache_begin", c_i32, [c_vp]),
     ("gvt_factor_cache_end", c_i32, [c_vp]),
     ("gvt_precond_num_params", c_i64, []),
+    ("gvt_precond_set_dtype", c_i32, [c_vp, c_i32]),
     ("gvt_precond_create", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp,
                                    _P(c_vp)]),
     ("gvt_precond_destroy", c_i32, [c_vp]),
@@ -311,6 +312,10 @@ class Precond:
               ctypes.byref(matrix(N, symmetric)) if N is not None else None, th.ctypes.data_as(c_vp),
               stream_ptr(stream), ctypes.byref(self.p))
         self.n = plan.n_in
+
+    def set_dtype(self, dtype):
+        """Arithmetic of the network: GVT_BF16 (tensor cores, the default) or GVT_F32 (SIMT)."""
+        _call("gvt_precond_set_dtype", self.p, int(dtype))
 
     def params(self):
         import numpy as np
