@@ -576,21 +576,25 @@ gvt_status gvt_precond_loss_grad(gvt_precond* p, const float* R, const float* E,
 gvt_status gvt_precond_scale(gvt_precond* p, double* get, const double* set);
 
 /* `steps` Adam steps (learning rate lr) on minibatches of `batch` <= 16
- * consecutive columns of the K_total pairs (R, E as above), cycling.
+ * consecutive columns of the K_total pairs (R, E: device, n x K_total column-major,
+ * stored as data_dtype GVT_F32 or GVT_BF16), cycling.
  * loss_history (host, may be NULL) receives each step's minibatch loss. */
-gvt_status gvt_precond_train(gvt_precond* p, const float* R, const float* E, int64_t K_total, int32_t steps,
-                             int32_t batch, double lr, double* loss_history, void* stream);
+gvt_status gvt_precond_train(gvt_precond* p, const void* R, const void* E, int32_t data_dtype, int64_t K_total,
+                             int32_t steps, int32_t batch, double lr, double* loss_history, void* stream);
 
 /*
- * Training data for the preconditioner from the exact solver: plain FP64 CG
- * from a = 0 on (K_desc + lambda I) a = y; at the iterations listed in iters
- * (host, ascending, `count` of them) the residual r_k and the correction
- * e_k = a_star - a_k (a_star: device FP64, the converged solution) are stored
- * as FP32 columns of R and E (device, n x count).  Synchronises.
+ * Training data for the preconditioner from the exact solver: plain CG from a = 0 on
+ * (K_desc + lambda I) a = y with the exact GVT product, in FP64 (op_dtype GVT_F64, M and N
+ * FP64) or in FP32 (op_dtype GVT_F32, M and N FP32, the handle's engine: for problems where an
+ * FP64 product costs too much); at the iterations listed in iters (host, ascending, `count` of
+ * them) the residual r_k and the correction e_k = a_star - a_k (a_star: device FP64, the
+ * converged solution) are stored as columns of R and E (device, n x count, store_dtype GVT_F32
+ * or GVT_BF16).  Synchronises.
  */
 gvt_status gvt_cg_record_pairs(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
                                const gvt_matrix* N, const double* y, double lambda, const double* a_star,
-                               const int64_t* iters, int64_t count, float* R, float* E, void* stream);
+                               const int64_t* iters, int64_t count, int32_t op_dtype, void* R, void* E,
+                               int32_t store_dtype, void* stream);
 
 /* ------------------------------------------------------------ batched solves */
 

@@ -54,6 +54,11 @@ constexpr int PT = 256;       // threads
 
 __device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
 
+// an element of the training pairs or of a vector, as double (FP32, FP64 or BF16 storage)
+__device__ __forceinline__ double ldv(float x) { return (double)x; }
+__device__ __forceinline__ double ldv(double x) { return x; }
+__device__ __forceinline__ double ldv(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
 // ------------------------------------------------------------------ features
 __device__ __forceinline__ float slogf(double x) { return (float)(x < 0 ? -log1p(-x) : log1p(x)); }
 
@@ -337,13 +342,15 @@ __global__ void grad_reduce_kernel(const float* __restrict__ gpart, int nb, floa
 }
 
 // per-block sums of r.e and e.e
-__global__ void rescale_kernel(const float* __restrict__ R, const float* __restrict__ E, int64_t n, double* __restrict__ part)
+template <class TR>
+__global__ void rescale_kernel(const TR* __restrict__ R, const TR* __restrict__ E, int64_t n, double* __restrict__ part)
 {
     __shared__ double sh[2][256];
     double re = 0.0, rr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        re += (double)R[i] * E[i];
-        rr += (double)E[i] * E[i];
+        const double e = ldv(E[i]);
+        re += ldv(R[i]) * e;
+        rr += e * e;
     }
     sh[0][threadIdx.x] = re;
     sh[1][threadIdx.x] = rr;
@@ -628,10 +635,10 @@ vtz_kernel(const float* __restrict__ O, const float* __restrict__ s, const T* __
         double acc = 0.0, ee = 0.0;
         if (k < K)
             for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-                const double z = (double)s[i] * (double)R[(int64_t)k * n + i];
+                const double z = (double)s[i] * ldv(R[(int64_t)k * n + i]);
                 acc += (double)O[i * PO + 1 + lane] * z;
                 if (E && lane == 0) {
-                    const double e = E[(int64_t)k * n + i];
+                    const double e = ldv(E[(int64_t)k * n + i]);
                     ee += e * e;
                 }
             }
@@ -683,9 +690,10 @@ __global__ void papply_kernel(const float* __restrict__ O, const float* __restri
 constexpr int KMAX = 16;   // pairs per minibatch
 
 // pass 1: per k, loss numerator sum of rho^2, and g_c = -V^T g_y (partials)
+template <class TR>
 __global__ void __launch_bounds__(256)
-loss_pass1_kernel(const float* __restrict__ O, const float* __restrict__ s, const float* __restrict__ R,
-                  const float* __restrict__ E, int64_t n, int K, const double* __restrict__ C,
+loss_pass1_kernel(const float* __restrict__ O, const float* __restrict__ s, const TR* __restrict__ R,
+                  const TR* __restrict__ E, int64_t n, int K, const double* __restrict__ C,
                   const double* __restrict__ ee, double* __restrict__ lpart, double* __restrict__ gpart)
 {
     __shared__ double c[PR * KMAX];
@@ -701,7 +709,7 @@ loss_pass1_kernel(const float* __restrict__ O, const float* __restrict__ s, cons
             double vc = vj * c[lane * K + k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) vc += __shfl_xor_sync(0xffffffffu, vc, o);
-            const double si = s[i], r = R[(int64_t)k * n + i], e = E[(int64_t)k * n + i];
+            const double si = s[i], r = ldv(R[(int64_t)k * n + i]), e = ldv(E[(int64_t)k * n + i]);
             const double y = si * r - vc;
             const double rho = si * y - e;
             const double gout = 2.0 * rho / (ee[k] * K);
@@ -723,9 +731,10 @@ loss_pass1_kernel(const float* __restrict__ O, const float* __restrict__ s, cons
 }
 
 // pass 2: per-pair output gradient dL/do (n x 33); Gh = G^{-1} g_c, sym = g_G + g_G^T
+template <class TR>
 __global__ void __launch_bounds__(256)
-loss_pass2_kernel(const float* __restrict__ O, const float* __restrict__ s, const float* __restrict__ R,
-                  const float* __restrict__ E, int64_t n, int K, const double* __restrict__ C,
+loss_pass2_kernel(const float* __restrict__ O, const float* __restrict__ s, const TR* __restrict__ R,
+                  const TR* __restrict__ E, int64_t n, int K, const double* __restrict__ C,
                   const double* __restrict__ Gh, const double* __restrict__ sym, const double* __restrict__ ee,
                   float* __restrict__ GO, double scale)
 {
@@ -749,7 +758,7 @@ loss_pass2_kernel(const float* __restrict__ O, const float* __restrict__ s, cons
                 vc += __shfl_xor_sync(0xffffffffu, vc, o);
                 vg += __shfl_xor_sync(0xffffffffu, vg, o);
             }
-            const double r = R[(int64_t)k * n + i], e = E[(int64_t)k * n + i];
+            const double r = ldv(R[(int64_t)k * n + i]), e = ldv(E[(int64_t)k * n + i]);
             const double z = si * r;
             const double y = z - vc;
             const double rho = si * y - e;
@@ -991,18 +1000,20 @@ int64_t precond_size(const gvt_precond* p) { return p->n; }
 }  // namespace gvt
 
 namespace {
-// loss and dL/dtheta (into p->grad) for K <= KMAX pairs
-gvt_status loss_grad(gvt_precond* p, const float* R, const float* E, int K, cudaStream_t st)
+// loss and dL/dtheta (into p->grad) for K <= KMAX pairs (R, E stored as TR)
+template <class TR>
+gvt_status loss_grad(gvt_precond* p, const TR* R, const TR* E, int K, cudaStream_t st)
 {
     GVT_CHECK(forward(p, st, true));
     const int64_t n = p->n;
     double* part = p->red;                       // RB * 32 * K
     double* epart = p->red + (size_t)RB * PR * KMAX;
-    vtz_kernel<float><<<RB, 256, 0, st>>>(p->O, p->s, R, n, K, E, part, epart);
+    vtz_kernel<TR><<<RB, 256, 0, st>>>(p->O, p->s, R, n, K, E, part, epart);
     sum_solve_kernel<<<1, 32, 0, st>>>(part, epart, RB, K, p->L, p->H, p->ee);
-    loss_pass1_kernel<<<RB, 256, 0, st>>>(p->O, p->s, R, E, n, K, p->H, p->ee, p->lpart, part);
+    loss_pass1_kernel<TR><<<RB, 256, 0, st>>>(p->O, p->s, R, E, n, K, p->H, p->ee, p->lpart, part);
     loss_mid_kernel<<<1, 256, 0, st>>>(p->lpart, part, RB, K, p->L, p->H, p->Gh, p->sym, p->loss);
-    loss_pass2_kernel<<<RB * 2, 256, 0, st>>>(p->O, p->s, R, E, n, K, p->H, p->Gh, p->sym, p->ee, p->GO, p->scale);
+    loss_pass2_kernel<TR><<<RB * 2, 256, 0, st>>>(p->O, p->s, R, E, n, K, p->H, p->Gh, p->sym, p->ee, p->GO,
+                                                  p->scale);
     GVT_LAUNCHED(5, "preconditioner loss");
     if (p->dtype == GVT_BF16) return backward_bf16(p, st);
     mlp_backward_kernel<<<kMlpBlocks, PT, sizeof(MlpSmem), st>>>(p->theta, p->X, n, p->GO, p->gpart);
@@ -1184,7 +1195,7 @@ gvt_status gvt_precond_loss_grad(gvt_precond* p, const float* R, const float* E,
         return GVT_ERR_INVALID_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    GVT_CHECK(loss_grad(p, R, E, (int)K, st));
+    GVT_CHECK(loss_grad<float>(p, R, E, (int)K, st));
     if (loss_host) GVT_CUDA(cudaMemcpyAsync(loss_host, p->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (grad_host) GVT_CUDA(cudaMemcpyAsync(grad_host, p->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, st));
     GVT_CUDA(cudaStreamSynchronize(st));
@@ -1209,18 +1220,17 @@ gvt_status gvt_precond_scale(gvt_precond* p, double* get, const double* set)
     return GVT_OK;
 }
 
-gvt_status gvt_precond_train(gvt_precond* p, const float* R, const float* E, int64_t K_total, int32_t steps,
-                             int32_t batch, double lr, double* loss_history, void* stream)
+}  // extern "C"
+
+namespace {
+template <class TR>
+gvt_status train(gvt_precond* p, const TR* R, const TR* E, int64_t K_total, int32_t steps, int32_t batch, double lr,
+                 double* loss_history, cudaStream_t st)
 {
-    if (!p || !R || !E || K_total < 1 || steps < 0 || batch < 1 || batch > KMAX || !(lr > 0.0)) {
-        set_error("gvt_precond_train: bad argument (1 <= batch <= 16)");
-        return GVT_ERR_INVALID_ARG;
-    }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = p->n;
     if (p->step == 0 && n > 0) {
         // output scale c = sum e.e / sum r.e: e ~ c r fitted towards the corrections (about 1 / lambda)
-        rescale_kernel<<<RB, 256, 0, st>>>(R, E, n * K_total, p->red);
+        rescale_kernel<TR><<<RB, 256, 0, st>>>(R, E, n * K_total, p->red);
         GVT_LAUNCH_CHECK("rescale");
         std::vector<double> part(2 * RB);
         GVT_CUDA(cudaMemcpyAsync(part.data(), p->red, sizeof(double) * 2 * RB, cudaMemcpyDeviceToHost, st));
@@ -1237,7 +1247,7 @@ gvt_status gvt_precond_train(gvt_precond* p, const float* R, const float* E, int
         // minibatch: `batch` consecutive pair columns, cycling through the data set
         const int64_t k0 = ((int64_t)it * batch) % K_total;
         const int K = (int)std::min<int64_t>(batch, K_total - k0);
-        GVT_CHECK(loss_grad(p, R + k0 * n, E + k0 * n, K, st));
+        GVT_CHECK(loss_grad<TR>(p, R + k0 * n, E + k0 * n, K, st));
         ++p->step;
         const float b1c = 1.f - std::pow(0.9f, (float)p->step), b2c = 1.f - std::pow(0.999f, (float)p->step);
         adam_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(p->theta, p->grad, p->m, p->v, (float)lr, b1c, b2c);
@@ -1248,5 +1258,21 @@ gvt_status gvt_precond_train(gvt_precond* p, const float* R, const float* E, int
     GVT_CUDA(cudaStreamSynchronize(st));
     return GVT_OK;
 }
+}  // namespace
 
-}  // extern "C"
+extern "C" gvt_status gvt_precond_train(gvt_precond* p, const void* R, const void* E, int32_t data_dtype,
+                                        int64_t K_total, int32_t steps, int32_t batch, double lr,
+                                        double* loss_history, void* stream)
+{
+    if (!p || !R || !E || K_total < 1 || steps < 0 || batch < 1 || batch > KMAX || !(lr > 0.0) ||
+        (data_dtype != GVT_F32 && data_dtype != GVT_BF16)) {
+        set_error("gvt_precond_train: bad argument (1 <= batch <= 16, data GVT_F32 or GVT_BF16)");
+        return GVT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (data_dtype == GVT_BF16)
+        return train<__nv_bfloat16>(p, static_cast<const __nv_bfloat16*>(R), static_cast<const __nv_bfloat16*>(E),
+                                    K_total, steps, batch, lr, loss_history, st);
+    return train<float>(p, static_cast<const float*>(R), static_cast<const float*>(E), K_total, steps, batch, lr,
+                        loss_history, st);
+}

@@ -11,6 +11,8 @@
 //   p = r + beta p
 // Dot products reduce in FP64 in a fixed order (per-block partials, then one
 // block), so a run is bitwise reproducible.
+#include <cuda_bf16.h>
+
 #include <chrono>
 #include <cmath>
 
@@ -165,13 +167,16 @@ __global__ void axpy_f32_kernel(double* __restrict__ a, const float* __restrict_
         a[i] += scale * (double)c[i];
 }
 
-// R = (float) r ; E = (float) (a_star - x)
-__global__ void record_kernel(const double* __restrict__ r, const double* __restrict__ x,
-                              const double* __restrict__ a_star, int64_t n, float* __restrict__ R, float* __restrict__ E)
+// R = r ; E = a_star - x, stored as FP32 or BF16
+__device__ __forceinline__ void store_as(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_as(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+template <class T, class TS>
+__global__ void record_kernel(const T* __restrict__ r, const T* __restrict__ x,
+                              const double* __restrict__ a_star, int64_t n, TS* __restrict__ R, TS* __restrict__ E)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        R[i] = (float)r[i];
-        E[i] = (float)(a_star[i] - x[i]);
+        store_as(R + i, (double)r[i]);
+        store_as(E + i, a_star[i] - (double)x[i]);
     }
 }
 
@@ -354,8 +359,100 @@ gvt_status fp64_residual(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix*
     return GVT_OK;
 }
 
+// CG from zero on (K + lambda I) x = y in operator precision T; at the listed iterations the
+// residual and a_star - x go to columns of R and E (storage TS).
+template <class T, class TS>
+gvt_status record_run(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, const gvt_matrix* Nn,
+                      const double* y, double lambda, const double* a_star, const int64_t* iters, int64_t count,
+                      TS* R, TS* E, cudaStream_t s)
+{
+    const int64_t n = plan->n_in;
+    Arena& ws = h->solve_ws;
+    ws.reset();
+    const size_t o_x = ws.take(sizeof(T) * n), o_r = ws.take(sizeof(T) * n), o_p = ws.take(sizeof(T) * n),
+                 o_w = ws.take(sizeof(T) * n), o_y = ws.take(sizeof(T) * n);
+    const size_t o_part = ws.take(8 * kRedBlocks), o_sc = ws.take(8 * SC_COUNT);
+    GVT_CHECK(ws.commit(s));
+    char* base = ws.base();
+    T* x = (T*)(base + o_x);
+    T* r = (T*)(base + o_r);
+    T* p = (T*)(base + o_p);
+    T* w = (T*)(base + o_w);
+    T* yy = (T*)(base + o_y);
+    double* part = (double*)(base + o_part);
+    double* sc = (double*)(base + o_sc);
+    if (sizeof(T) == 8) {
+        copy_kernel<double><<<vgrid(n), 256, 0, s>>>(reinterpret_cast<double*>(yy), y, n);
+        GVT_LAUNCH_CHECK("record init");
+    } else {
+        GVT_CHECK(convert(y, GVT_F64, yy, GVT_F32, n, s));
+    }
+    GVT_CHECK(vec_zero<T>(x, n, s));
+    copy_kernel<T><<<vgrid(n), 256, 0, s>>>(r, yy, n);
+    copy_kernel<T><<<vgrid(n), 256, 0, s>>>(p, yy, n);
+    dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
+    finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 2);
+    GVT_LAUNCHED(4, "record init");
+    int64_t j = 0;
+    for (int64_t it = 0; j < count; ++it) {
+        if (it == iters[j]) {
+            record_kernel<T, TS><<<vgrid(n), 256, 0, s>>>(r, x, a_star, n, R + j * n, E + j * n);
+            GVT_LAUNCH_CHECK("record");
+            ++j;
+            if (j == count) break;
+        }
+        GVT_CHECK(pairwise_apply<T>(plan, desc, M, Nn, p, w, s));
+        shift_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lambda, n, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
+        update_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
+        pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
+        GVT_LAUNCHED(5, "record iteration");
+    }
+    GVT_CUDA(cudaStreamSynchronize(s));
+    return GVT_OK;
+}
+
 }  // namespace
 }  // namespace gvt
+
+extern "C" gvt_status gvt_cg_record_pairs(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
+                                          const gvt_matrix* N, const double* y, double lambda, const double* a_star,
+                                          const int64_t* iters, int64_t count, int32_t op_dtype, void* R, void* E,
+                                          int32_t store_dtype, void* stream)
+{
+    using namespace gvt;
+    if (!h || !plan || !desc || !M || !y || !a_star || !iters || count < 1 || !R || !E || !plan->out_is_in ||
+        !(lambda > 0.0) || (op_dtype != GVT_F64 && op_dtype != GVT_F32) ||
+        (store_dtype != GVT_F32 && store_dtype != GVT_BF16)) {
+        set_error("gvt_cg_record_pairs: bad argument");
+        return GVT_ERR_INVALID_ARG;
+    }
+    const gvt_matrix* Nn = desc->homogeneous ? M : N;
+    if (!Nn || M->dtype != op_dtype || Nn->dtype != op_dtype) {
+        set_error("gvt_cg_record_pairs: M and N must have the operator dtype");
+        return GVT_ERR_INVALID_ARG;
+    }
+    for (int64_t j = 1; j < count; ++j)
+        if (iters[j] <= iters[j - 1] || iters[0] < 0) {
+            set_error("gvt_cg_record_pairs: iterations must be ascending and >= 0");
+            return GVT_ERR_INVALID_ARG;
+        }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op_dtype == GVT_F64) {
+        if (store_dtype == GVT_BF16)
+            return record_run<double, __nv_bfloat16>(h, plan, desc, M, Nn, y, lambda, a_star, iters, count,
+                                                     static_cast<__nv_bfloat16*>(R), static_cast<__nv_bfloat16*>(E), s);
+        return record_run<double, float>(h, plan, desc, M, Nn, y, lambda, a_star, iters, count,
+                                         static_cast<float*>(R), static_cast<float*>(E), s);
+    }
+    if (store_dtype == GVT_BF16)
+        return record_run<float, __nv_bfloat16>(h, plan, desc, M, Nn, y, lambda, a_star, iters, count,
+                                                static_cast<__nv_bfloat16*>(R), static_cast<__nv_bfloat16*>(E), s);
+    return record_run<float, float>(h, plan, desc, M, Nn, y, lambda, a_star, iters, count, static_cast<float*>(R),
+                                    static_cast<float*>(E), s);
+}
+
 
 using namespace gvt;
 
@@ -598,61 +695,6 @@ gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
     }
     info->iterations = total;
     return finish(GVT_ERR_NOT_CONVERGED);
-}
-
-gvt_status gvt_cg_record_pairs(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M,
-                               const gvt_matrix* N, const double* y, double lambda, const double* a_star,
-                               const int64_t* iters, int64_t count, float* R, float* E, void* stream)
-{
-    if (!h || !plan || !desc || !M || !y || !a_star || !iters || count < 1 || !R || !E || !plan->out_is_in ||
-        !(lambda > 0.0) || M->dtype != GVT_F64) {
-        set_error("gvt_cg_record_pairs: bad argument");
-        return GVT_ERR_INVALID_ARG;
-    }
-    for (int64_t j = 1; j < count; ++j)
-        if (iters[j] <= iters[j - 1] || iters[0] < 0) {
-            set_error("gvt_cg_record_pairs: iterations must be ascending and >= 0");
-            return GVT_ERR_INVALID_ARG;
-        }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t n = plan->n_in;
-    const gvt_matrix* Nn = desc->homogeneous ? M : N;
-    Arena& ws = h->solve_ws;
-    ws.reset();
-    const size_t o_x = ws.take(8 * n), o_r = ws.take(8 * n), o_p = ws.take(8 * n), o_w = ws.take(8 * n);
-    const size_t o_part = ws.take(8 * kRedBlocks), o_sc = ws.take(8 * SC_COUNT);
-    GVT_CHECK(ws.commit(s));
-    char* base = ws.base();
-    double* x = (double*)(base + o_x);
-    double* r = (double*)(base + o_r);
-    double* p = (double*)(base + o_p);
-    double* w = (double*)(base + o_w);
-    double* part = (double*)(base + o_part);
-    double* sc = (double*)(base + o_sc);
-    GVT_CHECK(vec_zero<double>(x, n, s));
-    copy_kernel<double><<<vgrid(n), 256, 0, s>>>(r, y, n);
-    copy_kernel<double><<<vgrid(n), 256, 0, s>>>(p, y, n);
-    dot_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
-    finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 2);
-    GVT_LAUNCHED(4, "record init");
-    int64_t j = 0;
-    for (int64_t it = 0; j < count; ++it) {
-        if (it == iters[j]) {
-            record_kernel<<<vgrid(n), 256, 0, s>>>(r, x, a_star, n, R + j * n, E + j * n);
-            GVT_LAUNCH_CHECK("record");
-            ++j;
-            if (j == count) break;
-        }
-        GVT_CHECK(pairwise_apply<double>(plan, desc, M, Nn, p, w, s));
-        shift_dot_kernel<double><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lambda, n, part);
-        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
-        update_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
-        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
-        pupdate_kernel<double><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
-        GVT_LAUNCHED(5, "record iteration");
-    }
-    GVT_CUDA(cudaStreamSynchronize(s));
-    return GVT_OK;
 }
 
 }  // extern "C"

@@ -137,9 +137,9 @@ SIGNATURES = [
     ("gvt_precond_apply", c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
     ("gvt_precond_loss_grad", c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     ("gvt_precond_scale", c_i32, [c_vp, c_vp, c_vp]),
-    ("gvt_precond_train", c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_vp, c_vp]),
+    ("gvt_precond_train", c_i32, [c_vp, c_vp, c_vp, c_i32, c_i64, c_i32, c_i32, c_dbl, c_vp, c_vp]),
     ("gvt_cg_record_pairs", c_i32, [c_vp, c_vp, _P(gvt_desc), _P(gvt_matrix), _P(gvt_matrix), c_vp, c_dbl,
-                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
+                                     c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_i32, c_vp]),
     ("gvt_check_device_errors", c_i32, [c_vp, c_vp]),
     ("gvt_tc_gemm_bf16", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]),
     ("gvt_set_tc_stall_test", c_i32, [c_vp, c_i64]),
@@ -369,10 +369,11 @@ class Precond:
         return get.value
 
     def train(self, R, E, steps, batch=8, lr=1e-3):
+        """R, E: CUDA tensors n x K (float32 or bfloat16), as returned by cg_record_pairs."""
         import numpy as np
         Rc, Ec = R.t().contiguous(), E.t().contiguous()
         hist = np.zeros(max(steps, 1))
-        _call("gvt_precond_train", self.p, ptr(Rc), ptr(Ec), R.shape[1], steps, batch, float(lr),
+        _call("gvt_precond_train", self.p, ptr(Rc), ptr(Ec), dtype_code(R), R.shape[1], steps, batch, float(lr),
               hist.ctypes.data_as(c_vp), stream_ptr())
         return hist[:steps]
 
@@ -388,16 +389,19 @@ class Precond:
             pass
 
 
-def cg_record_pairs(handle, plan, kind, M, N, y, lam, a_star, iters, symmetric=True, stream=None):
-    """(R, E) float32 n x len(iters): residuals and corrections a* - a_k of plain FP64 CG."""
+def cg_record_pairs(handle, plan, kind, M, N, y, lam, a_star, iters, symmetric=True, stream=None, store=None):
+    """(R, E) n x len(iters): residuals and corrections a* - a_k of plain CG in the precision of M
+    and N (FP64, or FP32 on the handle's engine), stored as `store` (torch.float32 by default, or
+    torch.bfloat16)."""
     import numpy as np
     torch = _torch()
     it = np.ascontiguousarray(iters, dtype=np.int64)
-    R = torch.empty((len(it), plan.n_in), dtype=torch.float32, device="cuda")
+    store = store or torch.float32
+    R = torch.empty((len(it), plan.n_in), dtype=store, device="cuda")
     E = torch.empty_like(R)
     _call("gvt_cg_record_pairs", handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
           ctypes.byref(matrix(N, symmetric)) if N is not None else None, ptr(y), float(lam), ptr(a_star),
-          it.ctypes.data_as(c_vp), len(it), ptr(R), ptr(E), stream_ptr(stream))
+          it.ctypes.data_as(c_vp), len(it), dtype_code(M), ptr(R), ptr(E), dtype_code(R), stream_ptr(stream))
     return R.t(), E.t()
 
 

@@ -1,8 +1,14 @@
 """Learned preconditioner on the GPU against the FP64 oracle, and what it gains.
 
-* features, network outputs, P r, the loss and its parameter gradient computed
-  by the library's kernels equal the oracle's (oracle/precond.py, itself pinned
-  by finite differences) to FP32 accuracy;
+* FP32 network (SIMT): features, network outputs, P r, the loss and its
+  parameter gradient computed by the library's kernels equal the oracle's
+  (oracle/precond.py, itself pinned by finite differences) to FP32 accuracy;
+* BF16 network on the tensor cores (the default): outputs within the BF16
+  bound of the oracle's; P r and the loss at the network's own outputs equal
+  the oracle's to FP32 accuracy; the gradient equals the oracle's backward of
+  the same output gradient within the BF16 bound of the backward products;
+* training pairs recorded by FP32 CG (the handle's engine) and stored in BF16
+  train the network as the FP64-recorded FP32 pairs do;
 * training on residual -> correction pairs from the exact solver lowers the
   loss; flexible CG with the trained P reaches the FP64 relative residual 1e-6
   (re-checked by the oracle), alone and inside mixed-precision refinement, and
@@ -76,18 +82,55 @@ def rel(a, b):
     return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def test_forward_apply_and_gradient_match_oracle(H):
+# BF16 bounds, unit roundoff u = 2^-9 for BF16 operands with FP32 accumulation.  The bound of a
+# rounded sum is stated against the sum of the magnitudes of its terms (the network's sums cancel
+# heavily, so a plain normwise ratio says little):
+# * forward: the three layers round their input activations and weights once each, so an output
+#   is off by a few u of the magnitudes feeding it: max|o - o*| <= 8u max(|W3| |h2| + |b3|);
+# * backward: each weight-gradient entry sum_p g_p h_p (and each bias sum) is off by at most about
+#   8u of sum_p |g_p| |h_p| with the backward magnitudes |g| propagated through |W| (a ReLU mask
+#   that flips where z ~ 0 moves one term, within that magnitude).
+BF16_U = 2.0 ** -9
+
+
+def bf16_magnitudes(theta, cache, g_o):
+    """Magnitude sums of the backward products: for each parameter block, sum over pairs of
+    |gradient flowing in| x |activation|, the gradients propagated with |W| and without masks."""
+    pp = lp.unpack(theta)
+    X, z1, h1, z2, h2 = cache
+    ag_o = np.abs(g_o)
+    ag_h2 = ag_o @ np.abs(pp["W3"])
+    ag_h1 = ag_h2 @ np.abs(pp["W2"])
+    return {"W3": ag_o.T @ np.abs(h2), "b3": ag_o.sum(0), "W2": ag_h2.T @ np.abs(h1), "b2": ag_h2.sum(0),
+            "W1": ag_h1.T @ np.abs(X), "b1": ag_h1.sum(0)}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_forward_apply_and_gradient_match_oracle(H, dtype):
     P = setup(H, n=3000)
     theta = lp.init_params(3, out_scale=0.2)
     theta = theta + 0.02 * np.random.default_rng(1).standard_normal(theta.shape)
     pc = gvt.Precond(H, P["plan"], "kronecker", P["M"], P["N"], theta)
+    pc.set_dtype(gvt.GVT_F32 if dtype == "f32" else gvt.GVT_BF16)
     mu, sd, X = pc.features()
     Xo = oracle_X(P)
     assert rel(X.cpu().numpy(), Xo) <= 1e-5
     th32 = theta.astype(np.float32).astype(np.float64)   # the GPU holds FP32 parameters
-    o_ref, _ = lp.mlp_forward(th32, X.double().cpu().numpy())
+    Xg = X.double().cpu().numpy()
+    o_ref, cache = lp.mlp_forward(th32, Xg)
     O = pc.outputs().cpu().numpy()
-    assert rel(O, o_ref) <= 1e-5
+    err_o = rel(O, o_ref)
+    if dtype == "f32":
+        print("f32 network: outputs vs oracle %.2e" % err_o)
+        assert err_o <= 1e-5
+    else:
+        pp = lp.unpack(th32)
+        mag_o = np.abs(cache[4]) @ np.abs(pp["W3"]).T + np.abs(pp["b3"])
+        err_m = float(np.max(np.abs(O - o_ref)) / np.max(mag_o))
+        print("bf16 network: outputs vs oracle %.2e normwise, %.2e of the magnitudes (bound %.1e)"
+              % (err_o, err_m, 8 * BF16_U))
+        assert err_m <= 8 * BF16_U
+    # P r from the network's own outputs: FP32/FP64 arithmetic in both dtypes
     D, V = lp.outputs_to_DV(O.astype(np.float64))
     r = np.random.default_rng(2).standard_normal(len(P["d"]))
     z = pc.apply(torch.as_tensor(r, device=DEV)).cpu().numpy()
@@ -99,10 +142,50 @@ def test_forward_apply_and_gradient_match_oracle(H):
     for scale in (1.0, 37.5):
         pc.scale(scale)
         loss, g = pc.loss_grad(torch.as_tensor(R, device=DEV), torch.as_tensor(E, device=DEV))
-        L_ref, g_ref = lp.loss_and_grad(th32, X.double().cpu().numpy(), R.astype(np.float64),
-                                        E.astype(np.float64), scale)
-        assert abs(loss - L_ref) <= 1e-5 * abs(L_ref), scale
-        assert rel(g, g_ref) <= 1e-4, scale
+        if dtype == "f32":
+            L_ref, g_ref = lp.loss_and_grad(th32, Xg, R.astype(np.float64), E.astype(np.float64), scale)
+            assert abs(loss - L_ref) <= 1e-5 * abs(L_ref), scale
+            assert rel(g, g_ref) <= 1e-4, scale
+        else:
+            # the loss and its output gradient at the network's own outputs, then the oracle's
+            # backward of that output gradient
+            L_ref, g_o = lp.loss_and_output_grad(O.astype(np.float64), R.astype(np.float64),
+                                                 E.astype(np.float64), scale)
+            g_ref = lp.mlp_backward(th32, cache, g_o)
+            mags = bf16_magnitudes(th32, cache, g_o)
+            gu, gr = lp.unpack(np.asarray(g, np.float64)), lp.unpack(g_ref)
+            errs = {k: float(np.max(np.abs(gu[k] - gr[k])) / np.max(mags[k])) for k in mags}
+            print("bf16 network, scale %g: loss %.4e vs %.4e; gradient errors of the magnitudes %s (normwise %.2e)"
+                  % (scale, loss, L_ref, " ".join("%s %.1e" % kv for kv in sorted(errs.items())), rel(g, g_ref)))
+            assert abs(loss - L_ref) <= 1e-5 * abs(L_ref), scale
+            assert max(errs.values()) <= 8 * BF16_U, (scale, errs)
+    pc.close()
+    P["plan"].close()
+
+
+def test_fp32_recorded_bf16_stored_pairs_match_and_train(H):
+    """Pairs recorded by FP32 CG on FP32 kernel matrices and stored in BF16 agree with the FP64 CG's
+    FP32-stored pairs to BF16 and FP32-CG accuracy over the first iterations, and train the BF16
+    network (the loss falls)."""
+    P = setup(H, n=3000)
+    lam = 1e-1
+    y = torch.as_tensor(P["y"], device=DEV)
+    a_star, st, _ = gvt.krr_cg_solve(H, P["plan"], "kronecker", P["M"], P["N"], y, lam, rel_tol=1e-10,
+                                     max_iter=20000)
+    assert st == 0
+    iters = list(range(0, 24, 2))
+    R64, E64 = gvt.cg_record_pairs(H, P["plan"], "kronecker", P["M"], P["N"], y, lam, a_star, iters)
+    Rb, Eb = gvt.cg_record_pairs(H, P["plan"], "kronecker", P["M"].float(), P["N"].float(), y, lam, a_star, iters,
+                                 store=torch.bfloat16)
+    assert Rb.dtype == torch.bfloat16
+    for k in range(len(iters)):
+        er = float(torch.norm(Rb[:, k].double() - R64[:, k].double()) / torch.norm(R64[:, k].double()))
+        ee = float(torch.norm(Eb[:, k].double() - E64[:, k].double()) / torch.norm(E64[:, k].double()))
+        assert er <= 1e-2 and ee <= 1e-2, (k, er, ee)
+    pc = gvt.Precond(H, P["plan"], "kronecker", P["M"], P["N"], lp.init_params(0, out_scale=0.01))
+    hist = pc.train(Rb, Eb, steps=200, batch=6, lr=3e-3)
+    print("BF16-stored pairs: loss %.3f -> %.3f" % (np.mean(hist[:5]), np.mean(hist[-10:])))
+    assert np.mean(hist[-10:]) < 0.95 * np.mean(hist[:5])
     pc.close()
     P["plan"].close()
 
