@@ -261,3 +261,20 @@ def random_pairs(rng, n, m_ids, q_ids):
     """n pairs drawn with replacement (duplicates allowed), for edge-case tests."""
     return (rng.integers(0, m_ids, n).astype(np.int32),
             rng.integers(0, q_ids, n).astype(np.int32))
+
+
+def mlp_init_params(seed=0, out_scale=0.01, n_feat=6, hidden=128, rank=32):
+    """Seeded initial parameters of the preconditioner network (layout W1[128x6] b1 W2[128x128] b2
+    W3[33x128] b3, float32): He-style normal draws for W1 and W2, a small output layer whose first
+    row is zero, zero biases except b3[0] = log(e - 1), so that softplus(o_0) starts at 1."""
+    rng = np.random.default_rng(seed)
+    n_out = 1 + rank
+    W1 = rng.standard_normal((hidden, n_feat)) * np.sqrt(2.0 / n_feat)
+    W2 = rng.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden)
+    W3 = rng.standard_normal((n_out, hidden)) * out_scale
+    W3[0] = 0.0
+    b3 = np.zeros(n_out)
+    b3[0] = np.log(np.expm1(1.0))
+    parts = [W1, np.zeros(hidden), W2, np.zeros(hidden), W3, b3]
+    return np.concatenate([x.reshape(-1) for x in parts]).astype(np.float32)
+

@@ -3,6 +3,8 @@ features, 10M pairs with power-law degrees (Zipf 1.1 weights).
 
 The GVT product runs on the whole sample, and 200 sampled output rows are
 checked against the FP64 oracle; each row is a sum over all 10M input pairs.
+A mixed-precision solve at lambda = 1 is re-checked by the oracle's residual
+on 200 sampled rows.
 * FP32 operands under the automatic engine (here the dense tensor-core
   stages): normwise error within the FP32 tolerance 1e-5;
 * FP64 operands (SIMT stages): within 1e-10.
@@ -30,10 +32,15 @@ def H():
     h.close()
 
 
-def test_kernel_filling_scale_sampled_parity(H):
+@pytest.fixture(scope="module")
+def zipf_problem():
     t0 = time.perf_counter()
-    p = synth.zipf(0)
-    gen_s = time.perf_counter() - t0
+    p = synth.zipf(0, labels=True)
+    return p, time.perf_counter() - t0
+
+
+def test_kernel_filling_scale_sampled_parity(H, zipf_problem):
+    p, gen_s = zipf_problem
     rng = np.random.default_rng(7)
     rows = np.sort(rng.choice(p.n, 200, replace=False))
     # kernel rows of the sampled outputs only (the oracle's M and N for those rows)
@@ -66,6 +73,46 @@ def test_kernel_filling_scale_sampled_parity(H):
               % (dtype, ms, float(p.n) * p.n / (ms / 1e3), err, gen_s))
         assert err <= tol
         del M, N, v, u
+    plan.close()
+
+
+def test_kernel_filling_scale_mixed_solve_sampled_residual(H, zipf_problem):
+    """The kernel-filling configuration's kernel ridge system at lambda = 1: mixed-precision
+    refinement on the single-pass FP16 tensor-core inner operator reaches the FP64 relative residual
+    1e-6, and the oracle recomputes the residual r_i = y_i - (K a)_i - lambda a_i at 200 sampled rows,
+    each a sum over all 10M pairs: its estimate sqrt(n mean r_i^2) / ||y|| of the relative residual
+    agrees with the solver's to sampling accuracy (and meets 1e-6 with that margin)."""
+    p, _ = zipf_problem
+    lam = 1.0
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=DEV), gamma=p.gamma)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=DEV), gamma=p.gamma)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
+    try:
+        t0 = time.perf_counter()
+        a, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, torch.as_tensor(p.y, device=DEV), lam,
+                                       mode=gvt.GVT_SOLVE_MIXED_IR, inner_dtype=gvt.GVT_F16, check_every=2,
+                                       max_iter=2000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    finally:
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    assert st == 0, (st, info.iterations, info.refinements, info.rel_residual)
+    rng = np.random.default_rng(9)
+    rows = np.sort(rng.choice(p.n, 200, replace=False))
+    ud, id_ = np.unique(p.d[rows], return_inverse=True)
+    ut, it_ = np.unique(p.t[rows], return_inverse=True)
+    Mo = orc.gaussian_kernel(p.Xd[ud], p.Xd, gamma=p.gamma)
+    No = orc.gaussian_kernel(p.Xt[ut], p.Xt, gamma=p.gamma)
+    an = a.cpu().numpy()
+    Ka = orc.pairwise_matvec("kronecker", Mo, No, id_.astype(np.int32), it_.astype(np.int32), p.d, p.t, an)
+    r = p.y[rows] - Ka - lam * an[rows]
+    est = float(np.sqrt(p.n * np.mean(r * r)) / np.linalg.norm(p.y))
+    print("kernel-filling solve, lambda 1, single-pass FP16 inner: %.1f s, %d inner iterations, %d refinements, "
+          "residual %.2e, oracle estimate on 200 rows %.2e" % (wall, info.iterations, info.refinements,
+                                                              info.rel_residual, est))
+    assert info.rel_residual <= 1e-6
+    assert est <= 2e-6 and 0.5 * info.rel_residual <= est <= 2.0 * info.rel_residual
     plan.close()
 
 
