@@ -324,6 +324,28 @@ typedef enum gvt_tc_pairs {
 gvt_status gvt_set_tc_pairs(gvt_handle* h, int32_t mode);
 
 /*
+ * Per-tile dense/sparse stages under GVT_STAGES_AUTO and GVT_STAGES_TC_F16X1 (FP32 products of a
+ * Kronecker term whose two factors are kernel matrices).  With power-law degrees W is dense in a
+ * few rows and columns and sparse elsewhere: ids are relabelled by decreasing degree (the plan
+ * keeps the relabelling, built on the host on first use), W^T is cut into tiles of 256 columns by
+ * 64 rows and the output grid into tiles of 128 by 256; tiles with more pairs than a measured
+ * break-even count run on the tensor-core GEMM (block-sparse in stage 1, a tile list in stage 2),
+ * the other pairs on the SIMT stages.  Theorem 1's cost then holds on the sparse part while the
+ * dense part runs at tensor-core rate.  Results equal the other forms' to rounding.
+ *  GVT_TILES_AUTO : the cost model picks SIMT, dense or per tile for each stage, on plans of at
+ *                   least 2^20 pairs (default);
+ *  GVT_TILES_OFF  : never per tile;
+ *  GVT_TILES_ON   : per tile wherever the form applies, whatever the cost model says (tests).
+ */
+typedef enum gvt_stage_tiles {
+    GVT_TILES_AUTO = 0,
+    GVT_TILES_OFF = 1,
+    GVT_TILES_ON = 2
+} gvt_stage_tiles;
+
+gvt_status gvt_set_stage_tiles(gvt_handle* h, int32_t mode);
+
+/*
  * The tensor-core GEMM behind GVT_STAGE1_TC_BF16X3, exposed for testing:
  * C[M x N] = A[M x K] B[N x K]^T with A, B BF16 row-major (K innermost,
  * K a multiple of 64, lda and ldb multiples of 8, 16-byte aligned), C FP32

@@ -611,6 +611,16 @@ gvt_status gvt_tc_gemm_bf16(gvt_handle* h, const void* A, int64_t lda, const voi
                         h->tc_stall_cycles);
 }
 
+gvt_status gvt_set_stage_tiles(gvt_handle* h, int32_t mode)
+{
+    if (!h || mode < GVT_TILES_AUTO || mode > GVT_TILES_ON) {
+        set_error("gvt_set_stage_tiles: bad handle or mode");
+        return GVT_ERR_INVALID_ARG;
+    }
+    h->stage_tiles = mode;
+    return GVT_OK;
+}
+
 gvt_status gvt_set_tc_stall_test(gvt_handle* h, int64_t cycles)
 {
     if (!h || cycles < 0 || cycles > 4000000000ll) {

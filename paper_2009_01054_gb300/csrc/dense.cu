@@ -115,15 +115,17 @@ __device__ __forceinline__ void store3(uint4* d, int64_t q, int64_t per_row, int
     d[2 * per_row + q] = pattern_b ? hi : lo;
 }
 
-// One CTA per row: dst row r = the `parts`-part split of src row r (zero beyond cols).
+// One CTA per row: dst row r = the `parts`-part split of src row rowperm[r] (r without rowperm),
+// its entry k taken from column colperm[k] (k without colperm); zero beyond cols.
 template <bool F16>
 __global__ void __launch_bounds__(kSplitThreads)
 split_rows_kernel(const float* __restrict__ src, int64_t ld, int64_t cols, int square, int pattern_b,
-                  uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp, int parts)
+                  uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp, int parts,
+                  const int32_t* __restrict__ rowperm, const int32_t* __restrict__ colperm)
 {
     __shared__ float red[kSplitThreads / 32];
     const int64_t r = blockIdx.x;
-    const float* row = src + r * ld;
+    const float* row = src + (rowperm ? (int64_t)rowperm[r] : r) * ld;
     const int64_t per_row = kp / 8;
     float s = 1.f;
     if (F16) {
@@ -138,14 +140,79 @@ split_rows_kernel(const float* __restrict__ src, int64_t ld, int64_t cols, int s
         row_scale(block_max(m, red), s, inv);
         if (threadIdx.x == 0) inv_scale[r] = inv;
     }
+    // (a column permutation leaves the row's largest magnitude, hence its scale, unchanged)
     uint4* d = dst + r * parts * per_row;
     for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
         float x[8];
-        load8(row + q * 8, q * 8, cols, square, x);
+        if (colperm) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t k = q * 8 + e;
+                const float a = k < cols ? __ldg(row + colperm[k]) : 0.f;
+                x[e] = square ? a * a : a;
+            }
+        } else {
+            load8(row + q * 8, q * 8, cols, square, x);
+        }
         uint4 hi, lo;
         if (F16) split8_f16(x, s, hi, lo);
         else split8_bf16(x, hi, lo);
         store3(d, q, per_row, pattern_b, parts, hi, lo);
+    }
+}
+
+// Dense tiles of W^T in relabelled coordinates, one CTA per relabelled row x': the entries of
+// original column x = xperm[x'] (its segment of the source ordered by x) whose relabelled row
+// k' = krank[bcol] falls in a dense tile (dense[(x' / bn) * nk + k' / 64]) are accumulated in
+// shared memory at k', then the row is split like densify_split_kernel's.
+template <bool F16>
+__global__ void __launch_bounds__(kSplitThreads)
+densify_tiles_kernel(S1Source src, const int32_t* __restrict__ xperm, const int32_t* __restrict__ krank,
+                     const uint8_t* __restrict__ dense, int bn, int64_t nk, const float* __restrict__ v,
+                     uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp, int parts)
+{
+    extern __shared__ float wrow[];
+    __shared__ float red[kSplitThreads / 32];
+    const int64_t xr = blockIdx.x;
+    for (int64_t k = threadIdx.x; k < kp; k += blockDim.x) wrow[k] = 0.f;
+    __syncthreads();
+    const int32_t x = xperm[xr];
+    const uint8_t* drow = dense + (xr / bn) * nk;
+    const float c = (float)src.coef;
+    for (int32_t j = src.seg[x] + (int32_t)threadIdx.x; j < src.seg[x + 1]; j += (int32_t)blockDim.x) {
+        const int32_t k = krank[src.bcol[j]];
+        if (drow[k >> 6]) atomicAdd(&wrow[k], c * v[src.perm[j]]);
+    }
+    __syncthreads();
+    const int64_t per_row = kp / 8;
+    float s = 1.f;
+    if (F16) {
+        float m = 0.f;
+        for (int64_t k = threadIdx.x; k < kp; k += blockDim.x) m = fmaxf(m, fabsf(wrow[k]));
+        float inv;
+        row_scale(block_max(m, red), s, inv);
+        if (threadIdx.x == 0) inv_scale[xr] = inv;
+    }
+    uint4* d = dst + xr * parts * per_row;
+    for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
+        float xs[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xs[e] = wrow[q * 8 + e];
+        uint4 hi, lo;
+        if (F16) split8_f16(xs, s, hi, lo);
+        else split8_bf16(xs, hi, lo);
+        store3(d, q, per_row, 1, parts, hi, lo);
+    }
+}
+
+// S[y, x] += Sd[y, xrank[x]] (the dense tiles' part, computed in relabelled columns)
+__global__ void merge_cols_kernel(float* __restrict__ S, int64_t lds, const float* __restrict__ Sd, int64_t ldsd,
+                                  const int32_t* __restrict__ xrank, int64_t Y, int64_t X)
+{
+    for (int64_t y = blockIdx.x; y < Y; y += gridDim.x) {
+        float* srow = S + y * lds;
+        const float* drow = Sd + y * ldsd;
+        for (int64_t x = threadIdx.x; x < X; x += blockDim.x) srow[x] += __ldg(drow + xrank[x]);
     }
 }
 
@@ -277,7 +344,8 @@ size_t dense_w_scratch_bytes(int64_t X, int64_t K)
 }
 
 gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t cols, int square, bool f16,
-                            int pattern_b, const DenseOperand& dst, cudaStream_t s)
+                            int pattern_b, const DenseOperand& dst, cudaStream_t s, const int32_t* rowperm,
+                            const int32_t* colperm)
 {
     if (rows <= 0) return GVT_OK;
     if (rows > INT32_MAX) {
@@ -287,10 +355,12 @@ gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t 
     uint4* d = static_cast<uint4*>(dst.data);
     if (f16)
         split_rows_kernel<true><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
-                                                                         dst.inv_scale, dst.kp, dst.parts);
+                                                                         dst.inv_scale, dst.kp, dst.parts, rowperm,
+                                                                         colperm);
     else
         split_rows_kernel<false><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
-                                                                          dst.inv_scale, dst.kp, dst.parts);
+                                                                          dst.inv_scale, dst.kp, dst.parts, rowperm,
+                                                                          colperm);
     GVT_LAUNCH_CHECK("dense split rows");
     return GVT_OK;
 }
@@ -326,7 +396,7 @@ gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSo
 }
 
 gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
-                      cudaStream_t s, int pair_mode, long long stall_cycles)
+                      cudaStream_t s, int pair_mode, long long stall_cycles, const TcSparse* sparse)
 {
     if (a.kp != b.kp || a.parts != b.parts) {
         set_error("dense stage: operand widths differ");
@@ -334,7 +404,42 @@ gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, fl
     }
     const int64_t kw = (int64_t)a.parts * a.kp;
     return tc_gemm(a.data, kw, b.data, kw, C, ldc, a.rows, b.rows, kw, f16,
-                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s, pair_mode, stall_cycles);
+                   f16 ? a.inv_scale : nullptr, f16 ? b.inv_scale : nullptr, err, s, pair_mode, stall_cycles, sparse);
+}
+
+gvt_status dense_densify_tiles(const S1Source& src, const int32_t* xperm, const int32_t* krank, const uint8_t* dense,
+                               int bn, int64_t nk, const float* v, int64_t X, bool f16, const DenseOperand& dst,
+                               cudaStream_t s)
+{
+    if (X <= 0) return GVT_OK;
+    const int64_t kp = dst.kp;
+    if (4 * kp > kRowSmemMax) {
+        set_error("dense tiles: W rows too wide for shared memory");
+        return GVT_ERR_UNSUPPORTED;
+    }
+    const size_t smem = 4 * (size_t)kp;
+    if (smem > 48 * 1024) {
+        if (f16) GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(densify_tiles_kernel<true>), (int)smem));
+        else GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(densify_tiles_kernel<false>), (int)smem));
+    }
+    uint4* d = static_cast<uint4*>(dst.data);
+    if (f16)
+        densify_tiles_kernel<true><<<(unsigned)X, kSplitThreads, smem, s>>>(src, xperm, krank, dense, bn, nk, v, d,
+                                                                            dst.inv_scale, kp, dst.parts);
+    else
+        densify_tiles_kernel<false><<<(unsigned)X, kSplitThreads, smem, s>>>(src, xperm, krank, dense, bn, nk, v, d,
+                                                                             dst.inv_scale, kp, dst.parts);
+    GVT_LAUNCH_CHECK("densify dense tiles of W");
+    return GVT_OK;
+}
+
+gvt_status dense_merge_cols(float* S, int64_t lds, const float* Sd, int64_t ldsd, const int32_t* xrank, int64_t Y,
+                            int64_t X, cudaStream_t s)
+{
+    if (Y <= 0 || X <= 0) return GVT_OK;
+    merge_cols_kernel<<<(unsigned)std::min<int64_t>(Y, 152 * 8), 256, 0, s>>>(S, lds, Sd, ldsd, xrank, Y, X);
+    GVT_LAUNCH_CHECK("merge dense part of S");
+    return GVT_OK;
 }
 
 gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s)

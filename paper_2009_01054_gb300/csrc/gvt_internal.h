@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <deque>
 #include <map>
 #include <string>
 #include <tuple>
@@ -74,6 +75,8 @@ struct Arena {
 // A split copy of a kernel matrix kept across products while a solve holds its matrices fixed.
 struct FactorCacheEntry {
     const void* ptr = nullptr;
+    const int32_t* rowperm = nullptr;   // row and column relabelling of the split (NULL: none)
+    const int32_t* colperm = nullptr;
     int64_t ld = 0, rows = 0, K = 0;
     int sq = -1;
     int parts = 3;
@@ -95,6 +98,7 @@ struct gvt_handle {
     int stage1_engine = 0;          // gvt_stage1_engine for FP32 products
     int tc_pairs = GVT_TC_PAIRS_AUTO;   // gvt_tc_pairs: tile form of the tensor-core GEMM
     long long tc_stall_cycles = 0;      // > 0: test stall of the GEMMs' timeout path (gvt_set_tc_stall_test)
+    int stage_tiles = GVT_TILES_AUTO;   // gvt_stage_tiles: per-tile dense/sparse stages
     std::map<std::tuple<int, int64_t, int>, int> batch_tune;   // batched stage-1 tile choice
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;
@@ -144,6 +148,47 @@ struct Order {
 
 }  // namespace gvt
 
+namespace gvt {
+// Per-tile dense/sparse form of one stage of a Kronecker group (Zipf-like degrees make some tiles of
+// W, and of the sampled output grid, dense and most others sparse).  Ids are relabelled by
+// decreasing degree so that the dense tiles gather in one corner; dense tiles run on the
+// tensor-core GEMM, the rest on the SIMT stages.  Built on the host once per plan and
+// configuration; device arrays live in the plan's allocations.
+struct HybridS1 {                   // stage 1: S = B W with W's columns x, rows k
+    int ia = -1, ib = -1, parts = 0;
+    int64_t X = 0, K = 0, Y = 0;
+    int bn = 256;                   // x tile (the GEMM's N tile); k blocks are 64 wide
+    int64_t nx = 0, nk = 0;
+    int32_t* xperm = nullptr;       // x' -> x
+    int32_t* xrank = nullptr;       // x -> x'
+    int32_t* kperm = nullptr;       // k' -> k
+    int32_t* krank = nullptr;       // k -> k'
+    uint8_t* dense = nullptr;       // nx * nk tile flags
+    int32_t* kb_off = nullptr;      // nx + 1 offsets into kb_list
+    int32_t* kb_list = nullptr;     // dense k blocks of every x tile
+    int32_t *seg_r = nullptr, *bcol_r = nullptr, *perm_r = nullptr;   // remainder entries, by x
+    int64_t n_r = 0, n_dense_tiles = 0, n_dense_entries = 0;
+    int mode = 0;                   // 0: SIMT, 1: dense GEMM, 2: per tile
+    double cost[3] = {0, 0, 0};
+};
+struct HybridS2 {                   // stage 2: u_i = <A[a_i, :], S[s_i, :]> over the output pairs
+    int oa = -1, ob = -1, parts = 0;
+    int64_t MA = 0, YS = 0, X = 0;
+    int bm = 128, bn = 256;         // output tile of the GEMM C' = A' S'^T
+    int64_t na = 0, nb = 0;
+    int32_t* aperm = nullptr;       // a' -> a
+    int32_t* sperm = nullptr;       // s' -> s
+    int32_t* tiles = nullptr;       // dense output tiles, (m tile, n tile) pairs
+    int64_t n_tiles = 0;
+    int32_t *arow_d = nullptr, *srow_d = nullptr, *perm_d = nullptr;  // outputs in dense tiles, relabelled
+    int64_t n_d = 0;
+    int32_t *arow_r = nullptr, *srow_r = nullptr, *perm_r = nullptr;  // remainder outputs, by a
+    int64_t n_r = 0;
+    int mode = 0;
+    double cost[3] = {0, 0, 0};
+};
+}  // namespace gvt
+
 struct gvt_plan {
     gvt_handle* h = nullptr;
     int64_t m_rows = 0, m_cols = 0, q_rows = 0, q_cols = 0;
@@ -156,6 +201,8 @@ struct gvt_plan {
     gvt::Order in_by[2];    // [FIRST], [SECOND]
     gvt::Order out_by[2];
     std::vector<void*> allocs;
+    std::deque<gvt::HybridS1> hyb1;    // per-tile forms built so far (a deque: references stay valid)
+    std::deque<gvt::HybridS2> hyb2;
 };
 
 namespace gvt {
@@ -260,11 +307,25 @@ size_t dtype_size(int dt);
 inline int* handle_err_word(gvt_handle* h) { return static_cast<int*>(h->status.ptr) + 16; }
 // C[M x N] = row_scale[m] col_scale[n] (A B^T)[m, n] on the tensor cores; A, B both FP16 (f16) or
 // both BF16, K-major; the scales may be NULL; pair_mode is a gvt_tc_pairs value.
+// Sparse forms of the tensor-core GEMM (device arrays; one SM per tile, no split K):
+//  * block-sparse B: the CTA of N tile j (bn columns) runs over the k-blocks
+//    kb_list[kb_off[j] .. kb_off[j+1]) of each of the kb_parts K segments (kb_stride
+//    k-blocks apart); an N tile with an empty list stores zeros;
+//  * tile list: only the n_tiles output tiles tile_list[2b], tile_list[2b+1] = (m tile, n tile).
+struct TcSparse {
+    const int* kb_list = nullptr;
+    const int* kb_off = nullptr;
+    int kb_parts = 1;
+    int kb_stride = 0;
+    const int* tile_list = nullptr;
+    int64_t n_tiles = 0;
+    int bn = 256;
+};
 // stall_cycles > 0 (one-SM form only): the test stall of the timeout path (the GEMM's MMA thread
 // waits that many cycles on a barrier nothing arrives on; the result is then invalid).
 gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                    int64_t N, int64_t K, bool f16, const float* row_scale, const float* col_scale, int* err,
-                   cudaStream_t s, int pair_mode, long long stall_cycles = 0);
+                   cudaStream_t s, int pair_mode, long long stall_cycles = 0, const TcSparse* sparse = nullptr);
 // C[M x N] (FP32, ld ldc) = A[M x K] B[N x K]^T, A and B BF16 K-major (K % 64 == 0).
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                         int64_t N, int64_t K, int* err, cudaStream_t s, int pair_mode, long long stall_cycles = 0);
@@ -283,15 +344,32 @@ int64_t dense_kp(int64_t K);
 size_t dense_operand_bytes(int64_t rows, int64_t K, int parts);
 DenseOperand dense_operand_at(void* base, int64_t rows, int64_t K, int parts);
 size_t dense_w_scratch_bytes(int64_t X, int64_t K);
-// rows of a row-major FP32 matrix (entries squared if `square`), pattern_b: [hi|lo|hi] instead of [hi|hi|lo]
+// rows of a row-major FP32 matrix (entries squared if `square`), pattern_b: [hi|lo|hi] instead of [hi|hi|lo];
+// row r taken from source row rowperm[r] and entry k from column colperm[k] when given
 gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t cols, int square, bool f16,
-                            int pattern_b, const DenseOperand& dst, cudaStream_t s);
+                            int pattern_b, const DenseOperand& dst, cudaStream_t s, const int32_t* rowperm = nullptr,
+                            const int32_t* colperm = nullptr);
+// W^T in relabelled rows x' (original column xperm[x']) holding only the entries of one source that
+// fall in dense tiles (dense[(x' / bn) * nk + krank[bcol] / 64] != 0), at column krank[bcol], split
+gvt_status dense_densify_tiles(const S1Source& src, const int32_t* xperm, const int32_t* krank, const uint8_t* dense,
+                               int bn, int64_t nk, const float* v, int64_t X, bool f16, const DenseOperand& dst,
+                               cudaStream_t s);
+// S[y, x] += Sd[y, xrank[x]]
+gvt_status dense_merge_cols(float* S, int64_t lds, const float* Sd, int64_t ldsd, const int32_t* xrank, int64_t Y,
+                            int64_t X, cudaStream_t s);
 // W^T (X rows, [hi|lo|hi]) from the sources of a stage-1 group (keys[si][j] = column x of entry j)
 gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSources], int64_t n, const float* v,
                          int64_t X, bool f16, const DenseOperand& dst, float* wide_scratch, cudaStream_t s);
 // C[a.rows x b.rows] = a b^T with the FP16 row scales applied
 gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, float* C, int64_t ldc, int* err,
-                      cudaStream_t s, int pair_mode, long long stall_cycles = 0);
+                      cudaStream_t s, int pair_mode, long long stall_cycles = 0, const TcSparse* sparse = nullptr);
+
+// ---------------------------------------------------------------- per-tile dense/sparse stages
+// The per-tile form of stage 1 (x component ia, inner component ib, Y rows of S) or of stage 2
+// (A rows component oa, S rows component ob, inner length X) for `parts` 16-bit GEMM parts, with
+// the mode the cost model picks; built on first use and kept in the plan.
+gvt_status hybrid_stage1(gvt_plan* p, int ia, int ib, int64_t Y, int parts, cudaStream_t s, const HybridS1** out);
+gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cudaStream_t s, const HybridS2** out);
 
 // ---------------------------------------------------------------- pairwise driver
 // u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).

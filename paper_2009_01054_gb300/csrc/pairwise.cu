@@ -58,6 +58,10 @@ bool dense_pays(int64_t rows, int64_t cols, int64_t K, double simt_flops, int pa
     return t_dense < simt_flops / 4.5e12;
 }
 
+// Pairs below which the automatic engines keep the per-stage choice: the per-tile form's one-time
+// host build (a sort of the ids by degree, a pass over the pairs) pays off on large samples.
+constexpr int64_t kTilesMinPairs = int64_t(1) << 20;
+
 int64_t out_range(const gvt_plan* p, int c) { return c == GVT_FIRST ? p->m_rows : p->q_rows; }
 int64_t in_range(const gvt_plan* p, int c) { return c == GVT_FIRST ? p->m_cols : p->q_cols; }
 
@@ -230,8 +234,13 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     }
     const size_t off_one = one_elems > 0 ? ws.take(sizeof(T) * (size_t)one_elems) : 0;
     // ---- dense-stage decisions (same grouping as the execution loop below) and their workspace
+    // 0: SIMT, 1: dense GEMM, 2: per tile (dense tiles on the GEMM, the rest SIMT)
     std::vector<char> tc1(C.two.size(), 0), tc2(C.two.size(), 0);
     size_t slot_bytes = 0, w_bytes = 0, s_bytes = 0, c_bytes = 0, wide_bytes = 0;
+    int64_t sd_elems = 0;   // S' of a per-tile stage 1 (its dense part, relabelled columns)
+    // per-tile forms: the cost-model engines on large samples, or on request
+    const bool tiles_ok = chooses && sizeof(T) == 4 && h->stage_tiles != GVT_TILES_OFF &&
+                          (h->stage_tiles == GVT_TILES_ON || std::min(plan->n_in, n_out) >= kTilesMinPairs);
     if (engine != GVT_STAGE1_SIMT) {
         std::vector<bool> seen(C.two.size(), false);
         for (size_t gi = 0; gi < C.two.size(); ++gi) {
@@ -246,12 +255,19 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             if (is_dense(g.fb) && same_ib && Y > 0 && X > 0 && K > 0) {   // stage 1 needs a dense B only
                 const double entries = (double)g.recipe.size() * plan->n_in;
                 tc1[gi] = chooses ? dense_pays(Y, X, K, 2.0 * Y * entries, parts) : 1;
+                const int ia = g.recipe.begin()->first.first;
+                if (tiles_ok && g.recipe.size() == 1 && ia != ib && 4 * dense_kp(K) <= 160 * 1024) {
+                    const HybridS1* h1 = nullptr;
+                    GVT_CHECK(hybrid_stage1(plan, ia, ib, Y, parts, s, &h1));
+                    tc1[gi] = h->stage_tiles == GVT_TILES_ON ? 2 : (char)h1->mode;
+                }
             }
             if (tc1[gi]) {
                 slot_bytes = std::max(slot_bytes, dense_operand_bytes(Y, K, parts));
                 w_bytes = std::max(w_bytes, dense_operand_bytes(X, K, parts));
                 wide_bytes = std::max(wide_bytes, dense_w_scratch_bytes(X, K));
             }
+            if (tc1[gi] == 2) sd_elems = std::max(sd_elems, Y * round_up(X, 4));
             for (size_t gj = gi; gj < C.two.size(); ++gj) {
                 const TwoSided& g2 = C.two[gj];
                 if (seen[gj] || g2.fb != g.fb || g2.recipe != g.recipe || out_range(plan, g2.ob) != Y) continue;
@@ -259,6 +275,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 const int64_t mb = out_range(plan, g2.oa);
                 if (!f16 || !is_dense(g2.fa) || mb <= 0) continue;
                 tc2[gj] = chooses ? dense_pays(mb, Y, X, 2.0 * X * (double)n_out, parts) : 1;
+                if (tiles_ok && g2.oa != g2.ob) {
+                    const HybridS2* h2 = nullptr;
+                    GVT_CHECK(hybrid_stage2(plan, g2.oa, g2.ob, X, parts, s, &h2));
+                    tc2[gj] = h->stage_tiles == GVT_TILES_ON ? 2 : (char)h2->mode;
+                }
                 if (!tc2[gj]) continue;
                 slot_bytes = std::max(slot_bytes, dense_operand_bytes(mb, X, parts));
                 s_bytes = std::max(s_bytes, dense_operand_bytes(Y, X, parts));
@@ -272,6 +293,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     const size_t off_s2 = s_bytes ? ws.take(s_bytes) : 0;
     const size_t off_c2 = c_bytes ? ws.take(c_bytes) : 0;
     const size_t off_wide = wide_bytes ? ws.take(wide_bytes) : 0;
+    const size_t off_sd = sd_elems ? ws.take(sizeof(T) * (size_t)sd_elems) : 0;
     GVT_CHECK(ws.commit(s));
     char* base = ws.base();
 
@@ -302,6 +324,8 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     // stage 2) that need the same factor, square mode, extents and format.
     struct Slot {
         const void* ptr = nullptr;
+        const int32_t* rowperm = nullptr;
+        const int32_t* colperm = nullptr;
         int sq = -1, pattern = -1;
         int64_t rows = -1, K = -1;
         size_t off = 0;
@@ -310,11 +334,12 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     slots[0].off = off_slot0;
     slots[1].off = off_slot1;
     int64_t tick = 0;
-    auto factor_operand = [&](const gvt_matrix* F, int sq, int64_t rows, int64_t K, DenseOperand& out) -> gvt_status {
+    auto factor_operand = [&](const gvt_matrix* F, int sq, int64_t rows, int64_t K, DenseOperand& out,
+                              const int32_t* rowperm = nullptr, const int32_t* colperm = nullptr) -> gvt_status {
         if (h->factor_cache_depth > 0) {   // a solve holds the matrices fixed: keep splits across products
             for (auto& e : h->factor_cache)
                 if (e.valid && e.ptr == F->data && e.ld == F->ld && e.rows == rows && e.K == K && e.sq == sq &&
-                    e.f16 == f16 && e.parts == parts) {
+                    e.f16 == f16 && e.parts == parts && e.rowperm == rowperm && e.colperm == colperm) {
                     e.used = ++h->factor_cache_tick;
                     out = dense_operand_at(e.buf.ptr, rows, K, parts);
                     return GVT_OK;
@@ -325,8 +350,11 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             lru->valid = false;
             GVT_CHECK(lru->buf.reserve(dense_operand_bytes(rows, K, parts), s));
             out = dense_operand_at(lru->buf.ptr, rows, K, parts);
-            GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s));
+            GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s,
+                                       rowperm, colperm));
             lru->ptr = F->data;
+            lru->rowperm = rowperm;
+            lru->colperm = colperm;
             lru->ld = F->ld;
             lru->rows = rows;
             lru->K = K;
@@ -338,15 +366,19 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             return GVT_OK;
         }
         for (auto& sl : slots)
-            if (sl.ptr == F->data && sl.sq == sq && sl.rows == rows && sl.K == K && sl.pattern == 0) {
+            if (sl.ptr == F->data && sl.sq == sq && sl.rows == rows && sl.K == K && sl.pattern == 0 &&
+                sl.rowperm == rowperm && sl.colperm == colperm) {
                 sl.used = ++tick;
                 out = dense_operand_at(base + sl.off, rows, K, parts);
                 return GVT_OK;
             }
         Slot& sl = slots[0].used <= slots[1].used ? slots[0] : slots[1];
         out = dense_operand_at(base + sl.off, rows, K, parts);
-        GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s));
+        GVT_CHECK(dense_split_rows(static_cast<const float*>(F->data), F->ld, rows, K, sq, f16, 0, out, s, rowperm,
+                                   colperm));
         sl.ptr = F->data;
+        sl.rowperm = rowperm;
+        sl.colperm = colperm;
         sl.sq = sq;
         sl.rows = rows;
         sl.K = K;
@@ -374,7 +406,48 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         }
         const double E = (double)srcs.count * (double)plan->n_in;
         const double sz = (double)sizeof(T);
-        if (tc1[gi]) {
+        if (tc1[gi] == 2) {
+            // per tile: the sparse tiles' entries by the scatter-accumulate into S, the dense tiles on
+            // the block-sparse GEMM into S' (relabelled columns), then S += S' through the relabelling
+            const int ia = g.recipe.begin()->first.first, ib = g.recipe.begin()->first.second;
+            const int64_t K = in_range(plan, ib);
+            const HybridS1* h1 = nullptr;
+            GVT_CHECK(hybrid_stage1(plan, ia, ib, Y, parts, s, &h1));
+            const double fm = sq_mode(g.fb) ? 3.0 : 2.0;
+            StatScope st(h, s, GVT_STAT_STAGE1, fm * Y * E,
+                         sz * Y * (double)K + sz * Y * X + E * (8 + sz) + 4.0 * (X + 1));
+            const FactorView<T>& B = fv[base_matrix(g.fb, homo)];
+            S1Sources rem{};
+            rem.count = 1;
+            rem.src[0] = S1Source{h1->seg_r, h1->bcol_r, h1->perm_r, srcs.src[0].coef, 0};
+            {
+                const double fr = fm * Y * (double)h1->n_r;
+                const double br = sz * Y * (double)K + sz * Y * X + h1->n_r * (8 + sz) + 4.0 * (X + 1);
+                StatScope sk(h, s, GVT_STAT_SPARSE_STAGE1, fr, br);
+                GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), rem, v, S, lds, Y, X, s));
+            }
+            const gvt_matrix* Bm = mats[base_matrix(g.fb, homo)];
+            DenseOperand a1, b1 = dense_operand_at(base + off_w, X, K, parts);
+            GVT_CHECK(factor_operand(Bm, sq_mode(g.fb), Y, K, a1, nullptr, h1->kperm));
+            GVT_CHECK(dense_densify_tiles(srcs.src[0], h1->xperm, h1->krank, h1->dense, h1->bn, h1->nk,
+                                          reinterpret_cast<const float*>(v), X, f16, b1, s));
+            TcSparse sp;
+            sp.kb_list = h1->kb_list;
+            sp.kb_off = h1->kb_off;
+            sp.kb_parts = parts;
+            sp.kb_stride = (int)(dense_kp(K) / 64);
+            sp.bn = h1->bn;
+            T* Sd = reinterpret_cast<T*>(base + off_sd);
+            {
+                StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * Y * h1->bn * 64.0 * parts * (double)h1->n_dense_tiles,
+                             2.0 * parts * 64.0 * (double)h1->n_dense_tiles * (Y + h1->bn) + 4.0 * Y * X,
+                             fm * Y * (double)h1->n_dense_entries);
+                GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(Sd), lds, handle_err_word(h), s,
+                                     h->tc_pairs, h->tc_stall_cycles, &sp));
+            }
+            GVT_CHECK(dense_merge_cols(reinterpret_cast<float*>(S), lds, reinterpret_cast<const float*>(Sd), lds,
+                                       h1->xrank, Y, X, s));
+        } else if (tc1[gi]) {
             const int ib = g.recipe.begin()->first.second;
             const gvt_matrix* Bm = mats[base_matrix(g.fb, homo)];
             const int32_t* keys[kMaxSources] = {nullptr, nullptr, nullptr, nullptr};
@@ -427,6 +500,45 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             if (g2.fa == GVT_FACTOR_IDENTITY) {
                 StatScope st(h, s, GVT_STAT_STAGE2, (double)n_out, (double)n_out * (12 + 3 * sz));
                 GVT_CHECK(stage2_identity<T>(S, lds, X, outs, 1.0, u, s));
+            } else if (tc2[gj] == 2) {
+                // per tile: the dense output tiles on the tile-list GEMM C' = A' S'^T (rows relabelled)
+                // and read out of C'; the other outputs by the sampled gather-dot
+                const HybridS2* h2 = nullptr;
+                GVT_CHECK(hybrid_stage2(plan, g2.oa, g2.ob, X, parts, s, &h2));
+                const int64_t mb = out_range(plan, g2.oa);
+                const int64_t ldc2 = round_up(Y, 4);
+                const double fm = sq_mode(g2.fa) ? 3.0 : 2.0;
+                StatScope st(h, s, GVT_STAT_STAGE2, fm * X * n_out,
+                             sz * ((double)mb * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
+                const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
+                DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X, parts);
+                GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2, h2->aperm, nullptr));
+                GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s,
+                                           h2->sperm, nullptr));
+                s_split = false;   // s2 now holds the relabelled split
+                float* C2 = reinterpret_cast<float*>(base + off_c2);
+                TcSparse sp;
+                sp.tile_list = h2->tiles;
+                sp.n_tiles = h2->n_tiles;
+                sp.bn = h2->bn;
+                {
+                    const double kp = (double)dense_kp(X);
+                    StatScope sg(h, s, GVT_STAT_TC_GEMM, 2.0 * h2->bm * h2->bn * kp * parts * (double)h2->n_tiles,
+                                 2.0 * parts * kp * (double)h2->n_tiles * (h2->bm + h2->bn) +
+                                     4.0 * h2->bm * h2->bn * (double)h2->n_tiles,
+                                 fm * X * (double)h2->n_d);
+                    GVT_CHECK(dense_gemm(a2, s2, f16, C2, ldc2, handle_err_word(h), s, h->tc_pairs, h->tc_stall_cycles,
+                                         &sp));
+                }
+                c_ptr = nullptr;
+                GVT_CHECK(dense_gather(C2, ldc2, S2Outputs{h2->arow_d, h2->srow_d, h2->perm_d, h2->n_d},
+                                       reinterpret_cast<float*>(u), s));
+                const FactorView<T>& A = fv[base_matrix(g2.fa, homo)];
+                const double fr = fm * X * (double)h2->n_r;
+                const double br = sz * ((double)mb * X + (double)Y * X) + (double)h2->n_r * (12 + 2 * sz);
+                StatScope sk(h, s, GVT_STAT_SPARSE_STAGE2, fr, br);
+                GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X,
+                                           S2Outputs{h2->arow_r, h2->srow_r, h2->perm_r, h2->n_r}, 1.0, u, s));
             } else if (tc2[gj]) {
                 const int64_t mb = out_range(plan, g2.oa);
                 const int64_t ldc2 = round_up(Y, 4);

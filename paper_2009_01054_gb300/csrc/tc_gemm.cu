@@ -36,6 +36,12 @@
 // hop to every ring slot and measured half the speed.)
 // Epilogue: the folding warps stage the 128 x BN tile in the (then idle) ring
 // memory and store it row by row, 32 consecutive columns per warp instruction.
+// Two sparse forms (one-SM only, no split K), for the per-tile dense/sparse
+// stages: a block-sparse B, where the CTA of N tile j runs only over the
+// k-blocks kb_list[kb_off[j] .. kb_off[j+1]) (in each of the `parts` K
+// segments of a split operand, kb_stride k-blocks apart; an N tile with no
+// k-block stores zeros); and a tile list, where CTA b computes only output
+// tile tile_list[b] = (m tile, n tile).
 // Every wait on an mbarrier is bounded by a clock budget, and the waits of the
 // pipeline also end as soon as another thread of the CTA has timed out; on
 // expiry the thread records GVT_ERR_TIMEOUT in a device error word, the kernel
@@ -341,7 +347,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t ldc, int M, int N, int kb_total, int kb_per_split,
                int atomic_out, const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-               int* __restrict__ err, long long stall_cycles)
+               int* __restrict__ err, long long stall_cycles, const int* __restrict__ kb_list,
+               const int* __restrict__ kb_off, int kb_parts, int kb_stride, const int2* __restrict__ tile_list)
 {
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "UMMA N");
     static_assert(!PAIR || BN % 16 == 0, "UMMA N for M = 256");
@@ -365,12 +372,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     // 0..BN/2-1, rank 1 the rest
     const uint32_t rank = PAIR ? cluster_rank() : 0u;
     const bool leader = rank == 0;
-    const int m0 = PAIR ? (int)(blockIdx.x >> 1) * (2 * TC_BM) + (int)rank * TC_BM : (int)blockIdx.x * TC_BM;
-    const int n0 = blockIdx.y * BN;
+    int mt = PAIR ? (int)(blockIdx.x >> 1) * 2 + (int)rank : (int)blockIdx.x, nt = blockIdx.y;
+    if (!PAIR && tile_list) {
+        const int2 tl = tile_list[blockIdx.x];
+        mt = tl.x;
+        nt = tl.y;
+    }
+    const int m0 = mt * TC_BM;
+    const int n0 = nt * BN;
     const int nb0 = n0 + (int)rank * B_ROWS;   // first B row this CTA loads
+    // k-blocks of this CTA: a contiguous range (split K), or kb_parts copies of this N tile's list
+    const int kl0 = (!PAIR && kb_list) ? kb_off[nt] : 0;
+    const int kcount = (!PAIR && kb_list) ? kb_off[nt + 1] - kl0 : 0;
     const int kb0 = blockIdx.z * kb_per_split;
     const int kb1 = min(kb_total, kb0 + kb_per_split);
-    const int nkb = max(kb1 - kb0, 0);
+    const int nkb = (!PAIR && kb_list) ? kcount * kb_parts : max(kb1 - kb0, 0);
     const int nchunks = (nkb + TC_CHUNK - 1) / TC_CHUNK;
 
     if (threadIdx.x == 0) {
@@ -411,7 +427,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 }
                 if (*(volatile int*)&sh->timeout) break;
                 unsigned char* sa = tiles + st * STAGE_BYTES;
-                const int kx = (kb0 + i) * TC_BK;
+                const int kx = ((!PAIR && kb_list) ? (i / kcount) * kb_stride + kb_list[kl0 + i % kcount] : kb0 + i) *
+                               TC_BK;
                 if constexpr (PAIR) {
                     // the leader's slot completes when the loads of both CTAs landed
                     if (leader) mbar_expect_tx(&sh->full[st], 2 * STAGE_BYTES);
@@ -485,7 +502,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         float acc[HALF];
 #pragma unroll
         for (int e = 0; e < HALF; ++e) acc[e] = 0.f;
-        bool good = nkb > 0;
+        // (an N tile without k-blocks in the block-sparse form stores its zero sums)
+        bool good = nkb > 0 || (!PAIR && kb_list != nullptr);
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             if (!mbar_wait(&sh->acc_full[b], (c >> 1) & 1, &sh->timeout)) {
@@ -532,7 +550,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             for (int e = 0; e < HALF; ++e) stage[row * SLD + col0 + e] = acc[e];
         }
         asm volatile("bar.sync 1, %0;" ::"n"(TC_FOLD_WARPS * 32) : "memory");   // folding warps only
-        if (nkb > 0 && *(volatile int*)&sh->timeout == 0) {
+        if ((nkb > 0 || (!PAIR && kb_list != nullptr)) && *(volatile int*)&sh->timeout == 0) {
             const int ncols = min(BN, N - n0);
             for (int r = fw; r < TC_BM; r += TC_FOLD_WARPS) {
                 const int gm = m0 + r;
@@ -620,15 +638,21 @@ gvt_status make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K,
 
 template <int BN, bool F16, bool PAIR>
 gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M, int64_t N,
-                     int64_t K, const float* rs, const float* cs, int* err, long long stall, cudaStream_t s)
+                     int64_t K, const float* rs, const float* cs, int* err, long long stall, const TcSparse& sp,
+                     cudaStream_t s)
 {
     const int pairs = (int)((M + 2 * TC_BM - 1) / (2 * TC_BM));
-    const int gx = PAIR ? 2 * pairs : (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
+    int gx = PAIR ? 2 * pairs : (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
     const int kb_total = (int)(K / TC_BK);
+    if (sp.tile_list) {   // one CTA per listed output tile
+        gx = (int)sp.n_tiles;
+        gy = 1;
+    }
     const int tiles = gx * gy;
-    // split K only when the output tiles alone leave most SMs idle
+    // split K only when the output tiles alone leave most SMs idle (never in the sparse forms)
     int splits = tiles >= 100 ? 1 : (148 + tiles - 1) / tiles;
     splits = std::max(1, std::min(splits, kb_total / 8));
+    if (sp.kb_list || sp.tile_list) splits = 1;
     const int kb_per = (kb_total + splits - 1) / splits;
     splits = (kb_total + kb_per - 1) / kb_per;
     const int atomic_out = splits > 1 ? 1 : 0;
@@ -652,7 +676,8 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     cfg.attrs = attr;
     cfg.numAttrs = PAIR ? 1 : 0;
     GVT_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, C, ldc, (int)M, (int)N, kb_total, kb_per, atomic_out, rs, cs,
-                                err, stall));
+                                err, stall, sp.kb_list, sp.kb_off, sp.kb_parts, sp.kb_stride,
+                                reinterpret_cast<const int2*>(sp.tile_list)));
     GVT_LAUNCH_CHECK("tc_gemm");
     return GVT_OK;
 }
@@ -660,20 +685,21 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
 template <bool F16, bool PAIR>
 gvt_status launch_tc_bn(int BN, const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc, int64_t M,
                         int64_t N, int64_t K, const float* rs, const float* cs, int* err, long long stall,
-                        cudaStream_t s)
+                        const TcSparse& sp, cudaStream_t s)
 {
-    if (BN == 64) return launch_tc<64, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
-    if (BN == 128) return launch_tc<128, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
-    if (BN == 224) return launch_tc<224, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
-    return launch_tc<256, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, s);
+    if (BN == 64) return launch_tc<64, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, sp, s);
+    if (BN == 128) return launch_tc<128, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, sp, s);
+    if (BN == 224) return launch_tc<224, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, sp, s);
+    return launch_tc<256, F16, PAIR>(ma, mb, C, ldc, M, N, K, rs, cs, err, stall, sp, s);
 }
 
 }  // namespace
 
 gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                    int64_t N, int64_t K, bool f16, const float* row_scale, const float* col_scale, int* err,
-                   cudaStream_t s, int pair_mode, long long stall_cycles)
+                   cudaStream_t s, int pair_mode, long long stall_cycles, const TcSparse* sparse)
 {
+    const TcSparse sp = sparse ? *sparse : TcSparse{};
     if (M <= 0 || N <= 0) return GVT_OK;
     if (K <= 0 || K % TC_BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N ||
         ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M > INT32_MAX || N > INT32_MAX || K / TC_BK > INT32_MAX) {
@@ -688,7 +714,12 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
     GVT_CHECK(get_encode());
     // SM pairs only on request: on GB300 both forms reach the same rate on these shapes (the
     // pair form reads 30 % fewer operand bytes per SM, but the loads are not the bound)
-    const bool pair = pair_mode == GVT_TC_PAIRS_ON;
+    const bool pair = pair_mode == GVT_TC_PAIRS_ON && !sp.kb_list && !sp.tile_list;   // sparse forms: one SM
+    if (sp.kb_list && sp.tile_list) {
+        set_error("tc_gemm: a block-sparse B and a tile list cannot be combined");
+        return GVT_ERR_INVALID_ARG;
+    }
+    if (sp.tile_list && sp.n_tiles == 0) return GVT_OK;
     if (stall_cycles > 0 && pair) {
         set_error("tc_gemm: the test stall exists in the one-SM tile form only");
         return GVT_ERR_UNSUPPORTED;
@@ -704,16 +735,23 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
         const int64_t t256 = gx * ((N + 255) / 256), t224 = gx * ((N + 223) / 224);
         if (t256 < t224 && t224 <= 152) BN = 224;
     }
+    if (sp.kb_list || sp.tile_list) {   // the caller's tiling fixes the N tile
+        if (sp.bn != 64 && sp.bn != 128 && sp.bn != 224 && sp.bn != 256) {
+            set_error("tc_gemm: sparse forms need an N tile of 64, 128, 224 or 256");
+            return GVT_ERR_INVALID_ARG;
+        }
+        BN = sp.bn;
+    }
     CUtensorMap ma, mb;
     GVT_CHECK(make_map(&ma, A, M, K, lda, TC_BM, f16));
     GVT_CHECK(make_map(&mb, B, N, K, ldb, pair ? BN / 2 : BN, f16));
     const float* rs = row_scale;
     const float* cs = col_scale;
     if (f16)
-        return pair ? launch_tc_bn<true, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s)
-                    : launch_tc_bn<true, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s);
-    return pair ? launch_tc_bn<false, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s)
-                : launch_tc_bn<false, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, s);
+        return pair ? launch_tc_bn<true, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, sp, s)
+                    : launch_tc_bn<true, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, sp, s);
+    return pair ? launch_tc_bn<false, true>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, sp, s)
+                : launch_tc_bn<false, false>(BN, ma, mb, C, ldc, M, N, K, rs, cs, err, stall_cycles, sp, s);
 }
 
 gvt_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,

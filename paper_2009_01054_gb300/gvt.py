@@ -143,6 +143,7 @@ SIGNATURES = [
     ("gvt_check_device_errors", c_i32, [c_vp, c_vp]),
     ("gvt_tc_gemm_bf16", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]),
     ("gvt_set_tc_stall_test", c_i32, [c_vp, c_i64]),
+    ("gvt_set_stage_tiles", c_i32, [c_vp, c_i32]),
     ("gvt_matvec_static", c_i32, [c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
                                   _P(gvt_matrix), _P(gvt_matrix), c_vp, c_vp, c_i32, c_vp]),
 ]
@@ -427,6 +428,14 @@ def gvt_check_device_errors(h, stream):
 
 def gvt_tc_gemm_bf16(h, A, lda, B, ldb, C, ldc, M, N, K, stream):
     _call("gvt_tc_gemm_bf16", h, A, lda, B, ldb, C, ldc, M, N, K, stream)
+
+
+GVT_TILES_AUTO, GVT_TILES_OFF, GVT_TILES_ON = 0, 1, 2
+
+
+def gvt_set_stage_tiles(h, mode):
+    """Per-tile dense/sparse stages: GVT_TILES_AUTO (cost model, large plans), _OFF or _ON."""
+    _call("gvt_set_stage_tiles", h, int(mode))
 
 
 def gvt_set_tc_stall_test(h, cycles):
