@@ -434,6 +434,10 @@ class Products:
         for h in self.handles:
             self.gvt.gvt_set_stage1_engine(h.h, code)
 
+    def set_tiles(self, mode):
+        for h in self.handles:
+            self.gvt.gvt_set_stage_tiles(h.h, mode)
+
     def step(self, nstreams=None, after=None):
         gvt = self.gvt
         ns = self.S if nstreams is None else nstreams
@@ -554,6 +558,16 @@ def bench_products(args, gvt, torch, dev, name, p, K, W, ws, dist, local, flush,
         res["engines"] = {"simt_f32": {"ms_per_step": simt_ms, "value": ws * pts / (simt_ms / 1e3), "unit": UNIT},
                           args.engine: {"ms_per_step": step_ms_max, "value": value, "unit": UNIT}}
         pr.set_engine(engine_code)
+        if args.engine in ("auto", "tc16"):
+            # the same engine with the per-tile stages off: every stage wholly dense or wholly SIMT
+            pr.set_tiles(gvt.GVT_TILES_OFF)
+            for _ in range(2):
+                pr.step()
+            torch.cuda.synchronize()
+            off_ms = time_steps(torch, pr.step, max(3, min(K, 10)), flush, pr.stream)
+            res["engines"][args.engine + "_without_tiles"] = {"ms_per_step": off_ms,
+                                                              "value": ws * pts / (off_ms / 1e3), "unit": UNIT}
+            pr.set_tiles(gvt.GVT_TILES_AUTO)
     return pr, res
 
 
@@ -831,22 +845,22 @@ def bench_c5_precond(H, gvt, torch, dev, p, n_rhs=4, per_rhs=500, steps=400, lam
     rng = np.random.default_rng(11)
     ys = [torch.as_tensor(p.y, device=dev)] + [torch.as_tensor(rng.standard_normal(p.n), device=dev)
                                                for _ in range(n_rhs - 1)]
-    Rs, Es = [], []
+    # the pairs, column-major n x (n_rhs * per_rhs) in BF16: one buffer each, filled in place
+    Rrows = torch.empty((n_rhs * per_rhs, p.n), dtype=torch.bfloat16, device=dev)
+    Erows = torch.empty_like(Rrows)
     t0 = time.perf_counter()
     gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
     try:
-        for y in ys:
+        for k, y in enumerate(ys):
             a_star, st, info = gvt.krr_cg_solve(H, plan, "kronecker", M, N, y, lam, mode=gvt.GVT_SOLVE_MIXED_IR,
                                                 rel_tol=1e-8, check_every=2, max_iter=4000, inner_dtype=gvt.GVT_F16)
-            R, E = gvt.cg_record_pairs(H, plan, "kronecker", M32, N32, y, lam, a_star, list(range(per_rhs)),
-                                       store=torch.bfloat16)
-            Rs.append(R)
-            Es.append(E)
+            gvt.cg_record_pairs(H, plan, "kronecker", M32, N32, y, lam, a_star, list(range(per_rhs)),
+                                store=torch.bfloat16,
+                                out=(Rrows[k * per_rhs:(k + 1) * per_rhs], Erows[k * per_rhs:(k + 1) * per_rhs]))
         torch.cuda.synchronize()
         res["record_s"] = time.perf_counter() - t0
-        R = torch.cat(Rs, dim=1)
-        E = torch.cat(Es, dim=1)
-        del Rs, Es
+        res["pairs_gb_bf16"] = 2 * Rrows.numel() * 2 / 1e9
+        R, E = Rrows.t(), Erows.t()
         t0 = time.perf_counter()
         pc = gvt.Precond(H, plan, "kronecker", M, N, synth.mlp_init_params(0, out_scale=0.01))
         hist = pc.train(R, E, steps=steps, batch=16, lr=3e-3)
@@ -855,7 +869,7 @@ def bench_c5_precond(H, gvt, torch, dev, p, n_rhs=4, per_rhs=500, steps=400, lam
         res["loss_first5"] = float(np.mean(hist[:5]))
         res["loss_last20"] = float(np.mean(hist[-20:]))
         res["scale"] = pc.scale()
-        del R, E
+        del R, E, Rrows, Erows
         torch.cuda.empty_cache()
         y = ys[0]
         runs = {}

@@ -177,6 +177,128 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
     }
 }
 
+// ---- stage 1 from shared memory (FP32, K <= kS1SmemMaxK rows of B^T)
+// A block owns 16 rows y of S (all of B^T's K rows for them, 64 bytes each, sit in shared memory)
+// and a range of columns x.  Each warp takes columns in turn; in a column, groups of 4 lanes take
+// entries 8 at a time and each lane multiplies its entry's weight into 4 of the 16 rows (one
+// 16-byte shared-memory read per entry and lane), then the 8 groups' sums are reduced by shuffles.
+// Column sums are staged in shared memory and stored 64 columns at a time, row by row.  Every
+// B^T value is read from global memory once per (row tile, column split) instead of once per
+// entry, and the entries are read packed: (16-bit row index, weight) from one pass per product.
+constexpr int kS1SmemRows = 16;
+constexpr int kS1SmemMaxK = 3200;            // 200 KB of B^T rows
+constexpr int kS1SmemChunk = 64;              // columns staged per store
+
+// packed entries of one source: bcol as 16 bits, w = coef * v[perm]
+__global__ void pack_entries_kernel(const int32_t* __restrict__ bcol, const int32_t* __restrict__ perm, int64_t n,
+                                    const float* __restrict__ v, float coef, uint16_t* __restrict__ pb,
+                                    float* __restrict__ pw)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        pb[j] = (uint16_t)bcol[j];
+        pw[j] = coef * v[perm[j]];
+    }
+}
+
+struct S1Packed {
+    const int32_t* seg[kMaxSources];
+    const uint16_t* bcol[kMaxSources];
+    const float* w[kMaxSources];
+    int count;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+stage1_smem_kernel(const float* __restrict__ Bt, int64_t ldb, int Kdim, S1Packed pk, float* __restrict__ S,
+                   int64_t lds, int64_t Y, int64_t X, int64_t x_per_block)
+{
+    extern __shared__ float4 s1_smem[];
+    float4* Bs = s1_smem;                                                  // Kdim x 4 float4
+    float* stage = reinterpret_cast<float*>(s1_smem + (size_t)Kdim * 4);  // 16 x (64 + 1)
+    const int64_t y0 = (int64_t)blockIdx.x * kS1SmemRows;
+    const bool full = y0 + kS1SmemRows <= Y && (ldb % 4 == 0) && ((uintptr_t)Bt % 16 == 0);
+    for (int idx = threadIdx.x; idx < Kdim * 4; idx += blockDim.x) {
+        const int k = idx >> 2, q = idx & 3;
+        const float* src = Bt + (int64_t)k * ldb + y0 + q * 4;
+        float4 b;
+        if (full) {
+            b = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+            b.x = y0 + q * 4 + 0 < Y ? __ldg(src + 0) : 0.f;
+            b.y = y0 + q * 4 + 1 < Y ? __ldg(src + 1) : 0.f;
+            b.z = y0 + q * 4 + 2 < Y ? __ldg(src + 2) : 0.f;
+            b.w = y0 + q * 4 + 3 < Y ? __ldg(src + 3) : 0.f;
+        }
+        if (MODE == FM_SQUARE) {
+            b.x *= b.x;
+            b.y *= b.y;
+            b.z *= b.z;
+            b.w *= b.w;
+        }
+        Bs[idx] = b;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 2, q = lane & 3;   // entry slot 0..7, rows 4q..4q+3
+    const int64_t xb = (int64_t)blockIdx.y * x_per_block;
+    const int64_t xe = min(X, xb + x_per_block);
+    for (int64_t c0 = xb; c0 < xe; c0 += kS1SmemChunk) {
+        const int nc = (int)(xe - c0 < kS1SmemChunk ? xe - c0 : kS1SmemChunk);
+        for (int c = warp; c < nc; c += 8) {
+            const int64_t x = c0 + c;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+            for (int si = 0; si < kMaxSources; ++si) {
+                if (si >= pk.count) break;
+                const int32_t j0 = pk.seg[si][x], j1 = pk.seg[si][x + 1];
+                const uint16_t* pb = pk.bcol[si];
+                const float* pw = pk.w[si];
+                int32_t j = j0 + grp;
+                for (; j + 8 < j1; j += 16) {   // two entries per lane in flight
+                    const int k0 = pb[j], k1 = pb[j + 8];
+                    const float w0 = pw[j], w1 = pw[j + 8];
+                    const float4 b0 = Bs[k0 * 4 + q], b1 = Bs[k1 * 4 + q];
+                    a0 = fmaf(w0, b0.x, a0);
+                    a1 = fmaf(w0, b0.y, a1);
+                    a2 = fmaf(w0, b0.z, a2);
+                    a3 = fmaf(w0, b0.w, a3);
+                    a0 = fmaf(w1, b1.x, a0);
+                    a1 = fmaf(w1, b1.y, a1);
+                    a2 = fmaf(w1, b1.z, a2);
+                    a3 = fmaf(w1, b1.w, a3);
+                }
+                if (j < j1) {
+                    const float w0 = pw[j];
+                    const float4 b0 = Bs[pb[j] * 4 + q];
+                    a0 = fmaf(w0, b0.x, a0);
+                    a1 = fmaf(w0, b0.y, a1);
+                    a2 = fmaf(w0, b0.z, a2);
+                    a3 = fmaf(w0, b0.w, a3);
+                }
+            }
+#pragma unroll
+            for (int off = 4; off < 32; off <<= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+                a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+            }
+            if (grp == 0) {
+                stage[(q * 4 + 0) * (kS1SmemChunk + 1) + c] = a0;
+                stage[(q * 4 + 1) * (kS1SmemChunk + 1) + c] = a1;
+                stage[(q * 4 + 2) * (kS1SmemChunk + 1) + c] = a2;
+                stage[(q * 4 + 3) * (kS1SmemChunk + 1) + c] = a3;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kS1SmemRows * nc; e += blockDim.x) {
+            const int r = e / nc, c = e % nc;
+            if (y0 + r < Y) S[(y0 + r) * lds + c0 + c] = stage[r * (kS1SmemChunk + 1) + c];
+        }
+        __syncthreads();
+    }
+}
+
 template <class T>
 __global__ void stage1_identity_kernel(S1Sources srcs, const T* __restrict__ v, T* __restrict__ S,
                                        int64_t lds, int64_t Y, int64_t X)
@@ -621,11 +743,59 @@ static void launch_stage1(const T* Bt, int64_t ldb, int mode, const S1Sources& s
         stage1_sparse_kernel<T, FM_DENSE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
 }
 
+size_t stage1_pack_bytes(int count, int64_t n, int64_t K)
+{
+    if (K > kS1SmemMaxK || n <= 0) return 0;
+    return (size_t)count * (((size_t)n * 2 + 255) / 256 * 256 + ((size_t)n * 4 + 255) / 256 * 256);
+}
+
 template <class T>
 gvt_status stage1_sparse(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
-                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s)
+                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s, int64_t K, int64_t n_entries,
+                        void* pack)
 {
     if (Y <= 0 || X <= 0) return GVT_OK;
+    if (sizeof(T) == 4 && pack && K > 0 && K <= kS1SmemMaxK && n_entries > 0) {
+        // FP32 with every row of B^T for 16 rows y in shared memory
+        S1Packed pk{};
+        pk.count = srcs.count;
+        char* base = static_cast<char*>(pack);
+        const size_t bb = ((size_t)n_entries * 2 + 255) / 256 * 256, wb = ((size_t)n_entries * 4 + 255) / 256 * 256;
+        for (int si = 0; si < srcs.count; ++si) {
+            uint16_t* pb = reinterpret_cast<uint16_t*>(base + si * (bb + wb));
+            float* pw = reinterpret_cast<float*>(base + si * (bb + wb) + bb);
+            pack_entries_kernel<<<grid1d(n_entries, 256), 256, 0, s>>>(srcs.src[si].bcol, srcs.src[si].perm, n_entries,
+                                                                      reinterpret_cast<const float*>(v),
+                                                                      (float)srcs.src[si].coef, pb, pw);
+            pk.seg[si] = srcs.src[si].seg;
+            pk.bcol[si] = pb;
+            pk.w[si] = pw;
+        }
+        GVT_LAUNCHED(srcs.count, "stage1 pack");
+        const int64_t ytiles = (Y + kS1SmemRows - 1) / kS1SmemRows;
+        // column splits: about 4 blocks per SM in all (one block per SM at a time with a full K)
+        int64_t xs = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + ytiles - 1) / ytiles, (X + 63) / 64));
+        const int64_t xpb = (X + xs - 1) / xs;
+        xs = (X + xpb - 1) / xpb;
+        if (ytiles > 2147483647ll || xs > 65535) {
+            set_error("stage 1: too many rows or columns");
+            return GVT_ERR_UNSUPPORTED;
+        }
+        const size_t smem = (size_t)K * 64 + (size_t)kS1SmemRows * (kS1SmemChunk + 1) * 4;
+        const float* B32 = reinterpret_cast<const float*>(Bt);
+        float* S32 = reinterpret_cast<float*>(S);
+        if (mode == FM_SQUARE) {
+            GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(stage1_smem_kernel<FM_SQUARE>), (int)smem));
+            stage1_smem_kernel<FM_SQUARE><<<dim3((unsigned)ytiles, (unsigned)xs), 256, smem, s>>>(
+                B32, ldb, (int)K, pk, S32, lds, Y, X, xpb);
+        } else {
+            GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(stage1_smem_kernel<FM_DENSE>), (int)smem));
+            stage1_smem_kernel<FM_DENSE><<<dim3((unsigned)ytiles, (unsigned)xs), 256, smem, s>>>(
+                B32, ldb, (int)K, pk, S32, lds, Y, X, xpb);
+        }
+        GVT_LAUNCH_CHECK("stage1_smem");
+        return GVT_OK;
+    }
     const int64_t gy = (X + kS1Cols - 1) / kS1Cols;
     if (gy > 65535) {
         set_error("stage 1: too many columns");
@@ -853,7 +1023,7 @@ gvt_status tanimoto_kernel(const uint32_t* X, int64_t rx, const uint32_t* Y, int
 
 #define GVT_INST(T)                                                                                 \
     template gvt_status stage1_sparse<T>(const T*, int64_t, int, const S1Sources&, const T*, T*,      \
-                                        int64_t, int64_t, int64_t, cudaStream_t);                   \
+                                        int64_t, int64_t, int64_t, cudaStream_t, int64_t, int64_t, void*); \
     template gvt_status stage1_identity<T>(const S1Sources&, const T*, T*, int64_t, int64_t,        \
                                            int64_t, cudaStream_t);                                  \
     template gvt_status stage2_gather<T>(const T*, int64_t, int, const T*, int64_t, int64_t,          \

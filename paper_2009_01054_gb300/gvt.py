@@ -390,16 +390,22 @@ class Precond:
             pass
 
 
-def cg_record_pairs(handle, plan, kind, M, N, y, lam, a_star, iters, symmetric=True, stream=None, store=None):
+def cg_record_pairs(handle, plan, kind, M, N, y, lam, a_star, iters, symmetric=True, stream=None, store=None,
+                    out=None):
     """(R, E) n x len(iters): residuals and corrections a* - a_k of plain CG in the precision of M
     and N (FP64, or FP32 on the handle's engine), stored as `store` (torch.float32 by default, or
-    torch.bfloat16)."""
+    torch.bfloat16).  out = (R_rows, E_rows): len(iters) x n contiguous tensors to fill instead
+    (for example row slices of one large buffer, so that many recordings need no concatenation)."""
     import numpy as np
     torch = _torch()
     it = np.ascontiguousarray(iters, dtype=np.int64)
     store = store or torch.float32
-    R = torch.empty((len(it), plan.n_in), dtype=store, device="cuda")
-    E = torch.empty_like(R)
+    if out is not None:
+        R, E = out
+        assert R.shape == (len(it), plan.n_in) and E.shape == R.shape and R.is_contiguous() and E.is_contiguous()
+    else:
+        R = torch.empty((len(it), plan.n_in), dtype=store, device="cuda")
+        E = torch.empty_like(R)
     _call("gvt_cg_record_pairs", handle.h, plan.p, ctypes.byref(_desc(kind)), ctypes.byref(matrix(M, symmetric)),
           ctypes.byref(matrix(N, symmetric)) if N is not None else None, ptr(y), float(lam), ptr(a_star),
           it.ctypes.data_as(c_vp), len(it), dtype_code(M), ptr(R), ptr(E), dtype_code(R), stream_ptr(stream))

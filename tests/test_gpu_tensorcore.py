@@ -376,13 +376,14 @@ def test_single_pass_f16_stages_within_their_rounding_bound(H, kind):
     (N or M and W) and once more in stage 2 (A and S), so each term of u_i is off by at most about
     4u of its magnitude: |u_i - u*_i| <= 4u (|K||v|)_i plus FP32 accumulation.  These kernels have
     nonnegative formulas on Gaussian bases, so |K| = K and (|K||v|)_i is the oracle's product with
-    |v|.  The test asserts 8u (a factor 2 of margin) on a dense sample, where the cost model picks
+    |v|.  The test asserts 8u (a factor 2 of margin) on 300 sampled rows of a sample dense and
+    large enough (1000 x 600 or 1000 x 1000 objects, 30 % of the pairs) that the cost model picks
     the tensor cores (checked through the library's GEMM statistics)."""
     rng = np.random.default_rng(17)
-    m, q, dim = 300, (300 if kind in gvt.HOMOGENEOUS else 80), 12
+    m, q, dim = 1000, (1000 if kind in gvt.HOMOGENEOUS else 600), 12
     Xd = rng.standard_normal((m, dim))
     Xt = Xd if kind in gvt.HOMOGENEOUS else rng.standard_normal((q, dim))
-    n = int(0.4 * m * q)
+    n = int(0.3 * m * q)
     d, t = synth.random_pairs(rng, n, m, q)
     v = rng.standard_normal(n)
     g = 1.0 / dim
@@ -396,8 +397,10 @@ def test_single_pass_f16_stages_within_their_rounding_bound(H, kind):
     stats = gvt.gvt_stats_read(H.h)
     gvt.gvt_stats_enable(H.h, False)
     v64 = vv.double().cpu().numpy()
-    ref = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, v64)
-    mag = orc.pairwise_matvec(kind, Mo, No, d, t, d, t, np.abs(v64))
+    rows = np.sort(rng.choice(n, 300, replace=False))
+    ref = orc.pairwise_matvec(kind, Mo, No, d[rows], t[rows], d, t, v64)
+    mag = orc.pairwise_matvec(kind, Mo, No, d[rows], t[rows], d, t, np.abs(v64))
+    u = u[rows]
     err = float(np.max(np.abs(u - ref)) / np.max(mag))
     print("%s single-pass FP16 stages: error %.2e of max |K||v| (normwise %.2e), %d GEMM launches"
           % (kind, err, normwise(u, ref), stats["tc_gemm"]["launches"]))
