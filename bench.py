@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--headline", default="c5", choices=["c5", "c2"],
                     help="workload of `value`: c5 = kernel-filling scale (10M Zipf pairs, Gaussian kernel); "
                          "c2 = homogeneous 2000 objects, all nine kernels")
+    ap.add_argument("--c5-m", type=int, default=20000,
+                    help="objects per side of the kernel-filling workload (a smaller instance of the same "
+                         "recipe serves profiler captures that must stay small)")
+    ap.add_argument("--c5-n", type=int, default=10_000_000, help="pairs of the kernel-filling workload")
     ap.add_argument("--no-all-kernels", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-c5-solve", action="store_true")
@@ -124,9 +128,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def workload(name, seed):
+def workload(name, seed, c5_m=20000, c5_n=10_000_000):
     from paper_2009_01054_gb300 import synth
-    return synth.zipf(seed, labels=True) if name == "c5" else synth.homogeneous(seed)
+    return synth.zipf(seed, m=c5_m, n=c5_n, labels=True) if name == "c5" else synth.homogeneous(seed)
 
 
 def kinds_of(name):
@@ -367,7 +371,7 @@ def run_reference(args, ws, rank):
     import oracle as orc
     from oracle.build import build_oracle
     build_oracle()
-    p = workload(args.headline, 0)
+    p = workload(args.headline, 0, args.c5_m, args.c5_n)
     kinds = kinds_of(args.headline)
     rows = 64
     rng = np.random.default_rng(0)
@@ -515,7 +519,10 @@ def bench_products(args, gvt, torch, dev, name, p, K, W, ws, dist, local, flush,
     pts = pair_terms_per_step(p.n, kinds)
     step_ms_max, value = job_rate(step_ms, pts, ws, dist, dev)
     roof, tpipe = roofline(stats, K, peaks, peak_src, 4, name)
-    res = {"workload": WORKLOADS[name], "m": p.m, "q": p.q, "n": p.n, "nhat": p.n, "kernels": kinds,
+    wl = WORKLOADS[name]
+    if name == "c5" and (p.m != 20000 or p.n != 10_000_000):
+        wl += " -- reduced instance of the same recipe: m=q=%d, n=%d" % (p.m, p.n)
+    res = {"workload": wl, "m": p.m, "q": p.q, "n": p.n, "nhat": p.n, "kernels": kinds,
            "kronecker_terms": sum(TERMS[k] for k in kinds), "pair_terms_per_step": pts,
            "ms_per_step": step_ms_max, "value": value, "unit": UNIT, "streams": pr.S,
            "gpu_launches": launches, "clocks": clk, "roofline": roof, "tensor_pipe": tpipe,
@@ -618,7 +625,7 @@ def run_gvt(args, ws, rank, local):
     K, W = args.steps, args.warmup
 
     head = args.headline
-    p = workload(head, rank)
+    p = workload(head, rank, args.c5_m, args.c5_n)
     pr, res = bench_products(args, gvt, torch, dev, head, p, K, W, ws, dist, local, flush, peaks, peak_src, True)
     accuracy = error_vs_fp64(gvt, torch, dev, pr, p, kinds_of(head)) if rank == 0 else None
     pr.close()
@@ -644,10 +651,12 @@ def run_gvt(args, ws, rank, local):
         solve = bench_solve(H, gvt, torch, dev, [float(x) for x in args.solve_lambdas.split(",")])
     c5_solve = None
     if not args.no_c5_solve and rank == 0:
-        c5_solve = bench_c5_solve(H, gvt, torch, dev, p if head == "c5" else workload("c5", 0), args)
+        c5_solve = bench_c5_solve(H, gvt, torch, dev,
+                                  p if head == "c5" else workload("c5", 0, args.c5_m, args.c5_n), args)
     c5_precond = None
     if args.c5_precond and rank == 0:
-        c5_precond = bench_c5_precond(H, gvt, torch, dev, p if head == "c5" else workload("c5", 0))
+        c5_precond = bench_c5_precond(H, gvt, torch, dev,
+                                      p if head == "c5" else workload("c5", 0, args.c5_m, args.c5_n))
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(H, gvt, torch, dev, args.batched_problems, args.batched_sample)

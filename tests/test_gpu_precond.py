@@ -165,16 +165,17 @@ def test_forward_apply_and_gradient_match_oracle(H, dtype):
 
 def test_fp32_recorded_bf16_stored_pairs_match_and_train(H):
     """Pairs recorded by FP32 CG on FP32 kernel matrices and stored in BF16 agree with the FP64 CG's
-    FP32-stored pairs: the first residual (y itself) to BF16 rounding, the later ones within 5 %
-    (FP32 CG's iterates drift from FP64 CG's as rounding differences grow over the iterations:
-    1.1 % by the eighth); and they train the BF16 network (the loss falls)."""
+    FP32-stored pairs over the first iterations: the first residual (y itself) to BF16 rounding, the
+    next ones within 2 % (FP32 CG's iterates then drift from FP64 CG's as rounding differences grow,
+    as CG's do: 0.4 % by the eighth iteration, 58 % by the tenth on this problem); and they train the
+    BF16 network (the loss falls)."""
     P = setup(H, n=3000)
     lam = 1e-1
     y = torch.as_tensor(P["y"], device=DEV)
     a_star, st, _ = gvt.krr_cg_solve(H, P["plan"], "kronecker", P["M"], P["N"], y, lam, rel_tol=1e-10,
                                      max_iter=20000)
     assert st == 0
-    iters = list(range(0, 24, 2))
+    iters = list(range(0, 10, 2))
     R64, E64 = gvt.cg_record_pairs(H, P["plan"], "kronecker", P["M"], P["N"], y, lam, a_star, iters)
     Rb, Eb = gvt.cg_record_pairs(H, P["plan"], "kronecker", P["M"].float(), P["N"].float(), y, lam, a_star, iters,
                                  store=torch.bfloat16)
@@ -183,10 +184,10 @@ def test_fp32_recorded_bf16_stored_pairs_match_and_train(H):
         er = float(torch.norm(Rb[:, k].double() - R64[:, k].double()) / torch.norm(R64[:, k].double()))
         ee = float(torch.norm(Eb[:, k].double() - E64[:, k].double()) / torch.norm(E64[:, k].double()))
         print("iteration %d: residual %.1e, correction %.1e apart" % (iters[k], er, ee))
-        tol = 2 * 2.0 ** -9 if k == 0 else 5e-2
+        tol = 2 * 2.0 ** -9 if k == 0 else 2e-2
         assert er <= tol and ee <= tol, (k, er, ee)
     pc = gvt.Precond(H, P["plan"], "kronecker", P["M"], P["N"], lp.init_params(0, out_scale=0.01))
-    hist = pc.train(Rb, Eb, steps=200, batch=6, lr=3e-3)
+    hist = pc.train(Rb, Eb, steps=200, batch=5, lr=3e-3)
     print("BF16-stored pairs: loss %.3f -> %.3f" % (np.mean(hist[:5]), np.mean(hist[-10:])))
     assert np.mean(hist[-10:]) < 0.95 * np.mean(hist[:5])
     pc.close()
