@@ -657,6 +657,7 @@ def run_gvt(args, ws, rank, local):
     if args.c5_precond and rank == 0:
         c5_precond = bench_c5_precond(H, gvt, torch, dev,
                                       p if head == "c5" else workload("c5", 0, args.c5_m, args.c5_n))
+    sparse_hbm = bench_sparse_hbm(gvt, torch, dev, peaks) if rank == 0 and not args.no_all_kernels else None
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(H, gvt, torch, dev, args.batched_problems, args.batched_sample)
@@ -693,7 +694,7 @@ def run_gvt(args, ws, rank, local):
                "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
                "engine": args.engine, "engines": res.get("engines"),
                "error_vs_fp64": accuracy, "tensor_stage1_gemm": tc_gemm, "solve": solve,
-               "c5_solve": c5_solve, "c5_precond": c5_precond, "batched": batched}
+               "c5_solve": c5_solve, "c5_precond": c5_precond, "sparse_hbm": sparse_hbm, "batched": batched}
         out.update(others)
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -798,16 +799,19 @@ def bench_c5_solve(H, gvt, torch, dev, p, args):
     gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_AUTO)
     try:
         runs1 = {}
-        for name, inner, note in (("mixed_ir_f16x1", gvt.GVT_F16,
-                                   "FP32 CG on single-pass FP16 tensor-core stages where dense"),
-                                  ("mixed_ir_f16x3", gvt.GVT_F32,
-                                   "FP32 CG, automatic engine (FP16x3 tensor-core stages where dense)")):
+        for name, inner, itol, note in (
+                ("mixed_ir_f16x1", gvt.GVT_F16, 1e-3, "FP32 CG on single-pass FP16 tensor-core stages where dense"),
+                ("mixed_ir_f16x1_inner_tol_1e-2", gvt.GVT_F16, 1e-2,
+                 "the same, each inner solve stopped at 1e-2 (the single-pass operator's own error limits "
+                 "what one refinement can gain)"),
+                ("mixed_ir_f16x3", gvt.GVT_F32, 1e-3,
+                 "FP32 CG, automatic engine (FP16x3 tensor-core stages where dense)")):
             (a, st_, info, hist), wall = timed_solve(torch, lambda: gvt.krr_cg_solve(
                 H, plan, "kronecker", M, N, y, 1.0, mode=gvt.GVT_SOLVE_MIXED_IR, check_every=2, max_iter=1500,
-                history=64, inner_dtype=inner))
+                history=64, inner_dtype=inner, inner_tol=itol))
             rr = {"ms": wall, "status": gvt.STATUS_NAMES[st_], "iterations": int(info.iterations),
                   "refinements": int(info.refinements), "rel_residual": info.rel_residual, "history": hist,
-                  "inner": note}
+                  "inner": note, "inner_tol": itol}
             runs1[name] = rr
         res["runs"]["lambda=1"] = runs1
         if args.c5_fp64_cg:
@@ -900,6 +904,45 @@ def bench_c5_precond(H, gvt, torch, dev, p, n_rhs=4, per_rhs=500, steps=400, lam
     del M, N, M32, N32
     torch.cuda.empty_cache()
     return res
+
+
+def bench_sparse_hbm(gvt, torch, dev, peaks, reps=10):
+    """The sparse SIMT stages where HBM binds: a heterodimer-like density (0.2 %) on a
+    kernel-filling-sized id space, homogeneous m = q = 20000, 64-d, 800k ordered pairs, the
+    Kronecker kernel in FP32 on the SIMT engine.  Per stage kernel: the algorithmic bytes of
+    SURVEY-defined minimum traffic (factor and S once, the entries once) per launch over the
+    launch's time, against the measured HBM bandwidth (`hbm_frac`), and the bytes the kernel
+    streams (one factor row per entry, 4 Y bytes; two rows per sampled dot) at that time."""
+    from paper_2009_01054_gb300 import synth
+    p = synth.homogeneous(0, m=20000, dim=64, n=800_000)
+    H = gvt.Handle()
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=dev), gamma=p.gamma, dtype=torch.float32)
+    plan = gvt.Plan(H, (p.m, p.m), (p.m, p.m), p.d, p.t)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=dev)
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    for _ in range(2):
+        gvt.pairwise_kernel_matvec(plan, "kronecker", M, M, v)
+    torch.cuda.synchronize()
+    gvt.gvt_stats_enable(H.h, True)
+    for _ in range(reps):
+        gvt.pairwise_kernel_matvec(plan, "kronecker", M, M, v)
+    torch.cuda.synchronize()
+    st = gvt.gvt_stats_read(H.h)
+    gvt.gvt_stats_enable(H.h, False)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"workload": "homogeneous m=q=20000, 64-d, 800k uniform ordered pairs (0.2 %, heterodimer-like), "
+                       "Kronecker kernel, FP32 SIMT stages", "hbm_peak_gbs": hbm}
+    for k, stream_bytes in (("sparse_stage1", 4.0 * p.m * p.n), ("sparse_stage2", 2 * 4.0 * p.m * p.n)):
+        r = st[k]
+        ms = r["ms"] / max(r["launches"], 1)
+        ab = r["bytes"] / max(r["launches"], 1)
+        out[k] = {"ms_per_launch": ms, "algorithmic_gbs": ab / (ms / 1e3) / 1e9,
+                  "hbm_frac": ab / (ms / 1e3) / 1e9 / hbm,
+                  "useful_tflops": r["useful_flops"] / max(r["launches"], 1) / (ms / 1e3) / 1e12,
+                  "streamed_gbs": stream_bytes / (ms / 1e3) / 1e9}
+    plan.close()
+    H.close()
+    return out
 
 
 def bench_batched(H, gvt, torch, dev, n_probs, sample=32):

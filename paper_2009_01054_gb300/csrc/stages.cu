@@ -187,7 +187,7 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
 // Column sums are staged in shared memory and stored row by row.  Every B^T value is read from
 // global memory once per (row tile, column split) instead of once per entry.
 constexpr int kS1SmemRows = 16;
-constexpr int kS1SmemMaxK = 3200;            // 200 KB of B^T rows
+constexpr int kS1SmemMaxK = 3200;            // 200 KB of B^T rows (with 16 KB of entries: 217 KB)
 constexpr int kS1SmemWarps = 16;             // columns per chunk
 constexpr int kS1SmemPiece = 2048;           // entries staged at a time (16 KB)
 
@@ -240,39 +240,82 @@ stage1_smem_kernel(const float* __restrict__ Bt, int64_t ldb, int Kdim, S1Packed
     const int grp = lane >> 2, q = lane & 3;   // entry slot 0..7, rows 4q..4q+3
     const int64_t xb = (int64_t)blockIdx.y * x_per_block;
     const int64_t xe = min(X, xb + x_per_block);
+    // One source: the next chunk's entries are loaded into registers while the current chunk
+    // computes (each thread holds up to kPre of them), then written to shared memory.
+    constexpr int kThreads = kS1SmemWarps * 32;
+    constexpr int kPre = kS1SmemPiece / kThreads;
+    const bool single = pk.count == 1;
+    const int32_t* seg0 = pk.seg[0];
+    const int2* ent0 = pk.ent[0];
+    int2 pre[kPre];
+    auto chunk_fits = [&](int64_t c) {
+        const int64_t ce = min(xe, c + kS1SmemWarps);
+        return single && c < xe && seg0[ce] - seg0[c] <= kS1SmemPiece;
+    };
+    auto prefetch = [&](int64_t c) {
+        const int64_t ce = min(xe, c + kS1SmemWarps);
+        const int32_t lo = seg0[c], hi = seg0[ce];
+#pragma unroll
+        for (int r = 0; r < kPre; ++r) {
+            const int32_t e = lo + (int32_t)threadIdx.x + r * kThreads;
+            pre[r] = e < hi ? __ldg(ent0 + e) : make_int2(0, 0);
+        }
+    };
+    auto commit = [&]() {
+#pragma unroll
+        for (int r = 0; r < kPre; ++r) ents[threadIdx.x + r * kThreads] = pre[r];
+    };
+    bool have = chunk_fits(xb);   // ents holds the current chunk's entries
+    if (have) {
+        prefetch(xb);
+        commit();
+    }
+    __syncthreads();   // Bs and the first chunk's entries are in place
     for (int64_t c0 = xb; c0 < xe; c0 += kS1SmemWarps) {
         const int nc = (int)(xe - c0 < kS1SmemWarps ? xe - c0 : kS1SmemWarps);
         const int64_t x = c0 + warp;
+        const bool next_fits = chunk_fits(c0 + kS1SmemWarps);
+        if (next_fits) prefetch(c0 + kS1SmemWarps);
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        auto accumulate = [&](int32_t lo, int32_t hi) {   // entries [lo, hi) of ents
+            int32_t j = lo + grp;
+            for (; j + 24 < hi; j += 32) {   // four entries per lane in flight
+                const int2 e0 = ents[j], e1 = ents[j + 8], e2 = ents[j + 16], e3 = ents[j + 24];
+                const float4 b0 = Bs[e0.x * 4 + q], b1 = Bs[e1.x * 4 + q];
+                const float4 b2 = Bs[e2.x * 4 + q], b3 = Bs[e3.x * 4 + q];
+                const float w0 = __int_as_float(e0.y), w1 = __int_as_float(e1.y);
+                const float w2 = __int_as_float(e2.y), w3 = __int_as_float(e3.y);
+                a0 = fmaf(w0, b0.x, a0); a1 = fmaf(w0, b0.y, a1); a2 = fmaf(w0, b0.z, a2); a3 = fmaf(w0, b0.w, a3);
+                a0 = fmaf(w1, b1.x, a0); a1 = fmaf(w1, b1.y, a1); a2 = fmaf(w1, b1.z, a2); a3 = fmaf(w1, b1.w, a3);
+                a0 = fmaf(w2, b2.x, a0); a1 = fmaf(w2, b2.y, a1); a2 = fmaf(w2, b2.z, a2); a3 = fmaf(w2, b2.w, a3);
+                a0 = fmaf(w3, b3.x, a0); a1 = fmaf(w3, b3.y, a1); a2 = fmaf(w3, b3.z, a2); a3 = fmaf(w3, b3.w, a3);
+            }
+            for (; j < hi; j += 8) {
+                const int2 e0 = ents[j];
+                const float4 b0 = Bs[e0.x * 4 + q];
+                const float w0 = __int_as_float(e0.y);
+                a0 = fmaf(w0, b0.x, a0); a1 = fmaf(w0, b0.y, a1); a2 = fmaf(w0, b0.z, a2); a3 = fmaf(w0, b0.w, a3);
+            }
+        };
+        if (have) {
+            if (warp < nc) {
+                const int32_t base = seg0[c0];
+                accumulate(seg0[x] - base, seg0[x + 1] - base);
+            }
+        } else {
+            // several sources or a chunk of more than kS1SmemPiece entries: pieces, synchronously
 #pragma unroll 1
-        for (int si = 0; si < pk.count; ++si) {
-            const int32_t* seg = pk.seg[si];
-            const int32_t jlo = seg[c0], jhi = seg[c0 + nc];
-            const int32_t mylo = warp < nc ? seg[x] : 0, myhi = warp < nc ? seg[x + 1] : 0;
-            for (int32_t p0 = jlo; p0 < jhi; p0 += kS1SmemPiece) {
-                const int32_t p1 = min(jhi, p0 + kS1SmemPiece);
-                __syncthreads();   // the previous piece is consumed (and Bs is complete)
-                for (int32_t e = p0 + (int32_t)threadIdx.x; e < p1; e += (int32_t)blockDim.x)
-                    ents[e - p0] = __ldg(pk.ent[si] + e);
-                __syncthreads();
-                const int32_t lo = max(mylo, p0) - p0, hi = min(myhi, p1) - p0;
-                int32_t j = lo + grp;
-                for (; j + 24 < hi; j += 32) {   // four entries per lane in flight
-                    const int2 e0 = ents[j], e1 = ents[j + 8], e2 = ents[j + 16], e3 = ents[j + 24];
-                    const float4 b0 = Bs[e0.x * 4 + q], b1 = Bs[e1.x * 4 + q];
-                    const float4 b2 = Bs[e2.x * 4 + q], b3 = Bs[e3.x * 4 + q];
-                    const float w0 = __int_as_float(e0.y), w1 = __int_as_float(e1.y);
-                    const float w2 = __int_as_float(e2.y), w3 = __int_as_float(e3.y);
-                    a0 = fmaf(w0, b0.x, a0); a1 = fmaf(w0, b0.y, a1); a2 = fmaf(w0, b0.z, a2); a3 = fmaf(w0, b0.w, a3);
-                    a0 = fmaf(w1, b1.x, a0); a1 = fmaf(w1, b1.y, a1); a2 = fmaf(w1, b1.z, a2); a3 = fmaf(w1, b1.w, a3);
-                    a0 = fmaf(w2, b2.x, a0); a1 = fmaf(w2, b2.y, a1); a2 = fmaf(w2, b2.z, a2); a3 = fmaf(w2, b2.w, a3);
-                    a0 = fmaf(w3, b3.x, a0); a1 = fmaf(w3, b3.y, a1); a2 = fmaf(w3, b3.z, a2); a3 = fmaf(w3, b3.w, a3);
-                }
-                for (; j < hi; j += 8) {
-                    const int2 e0 = ents[j];
-                    const float4 b0 = Bs[e0.x * 4 + q];
-                    const float w0 = __int_as_float(e0.y);
-                    a0 = fmaf(w0, b0.x, a0); a1 = fmaf(w0, b0.y, a1); a2 = fmaf(w0, b0.z, a2); a3 = fmaf(w0, b0.w, a3);
+            for (int si = 0; si < pk.count; ++si) {
+                const int32_t* seg = pk.seg[si];
+                const int32_t jlo = seg[c0], jhi = seg[c0 + nc];
+                const int32_t mylo = warp < nc ? seg[x] : 0, myhi = warp < nc ? seg[x + 1] : 0;
+                for (int32_t p0 = jlo; p0 < jhi; p0 += kS1SmemPiece) {
+                    const int32_t p1 = min(jhi, p0 + kS1SmemPiece);
+                    __syncthreads();   // the previous piece is consumed
+                    for (int32_t e = p0 + (int32_t)threadIdx.x; e < p1; e += (int32_t)blockDim.x)
+                        ents[e - p0] = __ldg(pk.ent[si] + e);
+                    __syncthreads();
+                    accumulate(max(mylo, p0) - p0, min(myhi, p1) - p0);
                 }
             }
         }
@@ -283,13 +326,15 @@ stage1_smem_kernel(const float* __restrict__ Bt, int64_t ldb, int Kdim, S1Packed
             a2 += __shfl_xor_sync(0xffffffffu, a2, off);
             a3 += __shfl_xor_sync(0xffffffffu, a3, off);
         }
-        __syncthreads();   // every warp is past the last piece and the previous chunk's store
+        __syncthreads();   // every warp is done with ents and with the previous chunk's store
         if (grp == 0 && warp < nc) {
             stage[(q * 4 + 0) * (kS1SmemWarps + 1) + warp] = a0;
             stage[(q * 4 + 1) * (kS1SmemWarps + 1) + warp] = a1;
             stage[(q * 4 + 2) * (kS1SmemWarps + 1) + warp] = a2;
             stage[(q * 4 + 3) * (kS1SmemWarps + 1) + warp] = a3;
         }
+        if (next_fits) commit();
+        have = next_fits;
         __syncthreads();
         for (int e = threadIdx.x; e < kS1SmemRows * nc; e += blockDim.x) {
             const int r = e / nc, c = e % nc;
