@@ -54,6 +54,26 @@ StatScope::~StatScope()
     h->recs.push_back(StatRec{kind, e0, e1, flops, bytes, useful});
 }
 
+gvt_status aux_fork(gvt_handle* h, cudaStream_t s, cudaStream_t* aux)
+{
+    if (!h->aux) {
+        GVT_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        GVT_CUDA(cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming));
+        GVT_CUDA(cudaEventCreateWithFlags(&h->aux_join, cudaEventDisableTiming));
+    }
+    GVT_CUDA(cudaEventRecord(h->aux_fork, s));
+    GVT_CUDA(cudaStreamWaitEvent(h->aux, h->aux_fork, 0));
+    *aux = h->aux;
+    return GVT_OK;
+}
+
+gvt_status aux_join(gvt_handle* h, cudaStream_t s)
+{
+    GVT_CUDA(cudaEventRecord(h->aux_join, h->aux));
+    GVT_CUDA(cudaStreamWaitEvent(s, h->aux_join, 0));
+    return GVT_OK;
+}
+
 gvt_status cuda_fail(cudaError_t e, const char* what)
 {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -263,6 +283,9 @@ gvt_status gvt_destroy(gvt_handle* h)
     h->status.release();
     for (auto& e : h->factor_cache) e.buf.release();
     if (h->host_scalars) cudaFreeHost(h->host_scalars);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->aux_fork) cudaEventDestroy(h->aux_fork);
+    if (h->aux_join) cudaEventDestroy(h->aux_join);
     delete h;
     return GVT_OK;
 }

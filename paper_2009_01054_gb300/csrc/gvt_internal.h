@@ -99,6 +99,10 @@ struct gvt_handle {
     int tc_pairs = GVT_TC_PAIRS_AUTO;   // gvt_tc_pairs: tile form of the tensor-core GEMM
     long long tc_stall_cycles = 0;      // > 0: test stall of the GEMMs' timeout path (gvt_set_tc_stall_test)
     int stage_tiles = GVT_TILES_AUTO;   // gvt_stage_tiles: per-tile dense/sparse stages
+    // a second stream on which a per-tile stage's sparse part runs beside its GEMM (created on first
+    // use), with the events that fork it from and join it to the caller's stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
     std::map<std::tuple<int, int64_t, int>, int> batch_tune;   // batched stage-1 tile choice
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;
@@ -108,6 +112,11 @@ struct gvt_handle {
 };
 
 namespace gvt {
+// The handle's auxiliary stream, forked from s: work queued on it after this call runs after
+// everything queued on s so far.  aux_join(h, s) makes s wait for everything queued on it.
+gvt_status aux_fork(gvt_handle* h, cudaStream_t s, cudaStream_t* aux);
+gvt_status aux_join(gvt_handle* h, cudaStream_t s);
+
 // While alive, the dense engines reuse split copies of kernel matrices across products (the
 // caller guarantees the matrices do not change); the copies are dropped when the last scope ends.
 struct FactorCacheScope {

@@ -428,11 +428,15 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             S1Sources rem{};
             rem.count = 1;
             rem.src[0] = S1Source{h1->seg_r, h1->bcol_r, h1->perm_r, srcs.src[0].coef, 0};
+            // the sparse part (streams factor rows from HBM) runs on the auxiliary stream beside the
+            // GEMM (tensor cores); they write S and S', joined before the merge
+            cudaStream_t sa = nullptr;
+            GVT_CHECK(aux_fork(h, s, &sa));
             {
                 const double fr = fm * Y * (double)h1->n_r;
                 const double br = sz * Y * (double)K + sz * Y * X + h1->n_r * (8 + sz) + 4.0 * (X + 1);
-                StatScope sk(h, s, GVT_STAT_SPARSE_STAGE1, fr, br);
-                GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), rem, v, S, lds, Y, X, s,
+                StatScope sk(h, sa, GVT_STAT_SPARSE_STAGE1, fr, br);
+                GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), rem, v, S, lds, Y, X, sa,
                                            mats[base_matrix(g.fb, homo)]->cols, h1->n_r,
                                            pack_bytes ? base + off_pack : nullptr));
             }
@@ -455,6 +459,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 GVT_CHECK(dense_gemm(a1, b1, f16, reinterpret_cast<float*>(Sd), lds, handle_err_word(h), s,
                                      h->tc_pairs, h->tc_stall_cycles, &sp));
             }
+            GVT_CHECK(aux_join(h, s));
             GVT_CHECK(dense_merge_cols(reinterpret_cast<float*>(S), lds, reinterpret_cast<const float*>(Sd), lds,
                                        h1->xrank, Y, X, s));
         } else if (tc1[gi]) {
@@ -522,6 +527,18 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 const double fm = sq_mode(g2.fa) ? 3.0 : 2.0;
                 StatScope st(h, s, GVT_STAT_STAGE2, fm * X * n_out,
                              sz * ((double)mb * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
+                // the remainder's sampled dots (HBM-bound) on the auxiliary stream beside the tile-list
+                // GEMM; they add into disjoint outputs of u
+                cudaStream_t sa = nullptr;
+                GVT_CHECK(aux_fork(h, s, &sa));
+                {
+                    const FactorView<T>& A = fv[base_matrix(g2.fa, homo)];
+                    const double fr = fm * X * (double)h2->n_r;
+                    const double br = sz * ((double)mb * X + (double)Y * X) + (double)h2->n_r * (12 + 2 * sz);
+                    StatScope sk(h, sa, GVT_STAT_SPARSE_STAGE2, fr, br);
+                    GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X,
+                                               S2Outputs{h2->arow_r, h2->srow_r, h2->perm_r, h2->n_r}, 1.0, u, sa));
+                }
                 const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
                 DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X, parts);
                 GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2, h2->aperm, nullptr));
@@ -545,12 +562,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 c_ptr = nullptr;
                 GVT_CHECK(dense_gather(C2, ldc2, S2Outputs{h2->arow_d, h2->srow_d, h2->perm_d, h2->n_d},
                                        reinterpret_cast<float*>(u), s));
-                const FactorView<T>& A = fv[base_matrix(g2.fa, homo)];
-                const double fr = fm * X * (double)h2->n_r;
-                const double br = sz * ((double)mb * X + (double)Y * X) + (double)h2->n_r * (12 + 2 * sz);
-                StatScope sk(h, s, GVT_STAT_SPARSE_STAGE2, fr, br);
-                GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X,
-                                           S2Outputs{h2->arow_r, h2->srow_r, h2->perm_r, h2->n_r}, 1.0, u, s));
+                GVT_CHECK(aux_join(h, s));
             } else if (tc2[gj]) {
                 const int64_t mb = out_range(plan, g2.oa);
                 const int64_t ldc2 = round_up(Y, 4);
