@@ -253,13 +253,9 @@ struct S1Sources {
 
 // S[y, x] = sum_src coef * sum_{j in seg_src[x]} Bt[bcol_j, y] * v[perm_j]   (y < Y, x < X)
 // Bt is B transposed: Bt[t*ldb + y] = B[y, t].  mode squares B's entries.
-// FP32 with K <= 3200 rows of B^T and a pack workspace of stage1_pack_bytes(count, n_entries, K)
-// bytes: B^T staged in shared memory, entries packed once per call (n_entries: the sources' length)
 template <class T>
 gvt_status stage1_sparse(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
-                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s, int64_t K = 0,
-                        int64_t n_entries = 0, void* pack = nullptr);
-size_t stage1_pack_bytes(int count, int64_t n, int64_t K);
+                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s);
 // B = identity: S[y, x] = sum_src coef * sum_{j in seg_src[x], bcol_j == y} v[perm_j]
 // (S must be zeroed by the caller; entries with bcol >= Y are skipped).
 template <class T>

@@ -197,13 +197,17 @@ gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cuda
     const double thr = tile_t / out_t;
     std::vector<uint8_t> dense(cnt.size(), 0);
     std::vector<int32_t> tiles;
-    for (int64_t nt = 0; nt < H.nb; ++nt)            // m tiles fastest: neighbouring CTAs share B
-        for (int64_t mt = 0; mt < H.na; ++mt)
-            if ((double)cnt[(size_t)(mt * H.nb + nt)] > thr) {
-                dense[(size_t)(mt * H.nb + nt)] = 1;
-                tiles.push_back((int32_t)mt);
-                tiles.push_back((int32_t)nt);
-            }
+    // groups of 16 m tiles, m tile fastest within a group: the CTAs resident at one time share a
+    // few A strips and B strips in L2 (the GEMM's own grid order)
+    constexpr int64_t kGroupM = 16;
+    for (int64_t g0 = 0; g0 < H.na; g0 += kGroupM)
+        for (int64_t nt = 0; nt < H.nb; ++nt)
+            for (int64_t mt = g0; mt < std::min(H.na, g0 + kGroupM); ++mt)
+                if ((double)cnt[(size_t)(mt * H.nb + nt)] > thr) {
+                    dense[(size_t)(mt * H.nb + nt)] = 1;
+                    tiles.push_back((int32_t)mt);
+                    tiles.push_back((int32_t)nt);
+                }
     H.n_tiles = (int64_t)tiles.size() / 2;
     std::vector<int32_t> arow_d, srow_d, perm_d, arow_r, srow_r, perm_r;
     for (int64_t i = 0; i < n; ++i) {

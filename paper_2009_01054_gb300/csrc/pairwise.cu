@@ -294,14 +294,6 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
     const size_t off_c2 = c_bytes ? ws.take(c_bytes) : 0;
     const size_t off_wide = wide_bytes ? ws.take(wide_bytes) : 0;
     const size_t off_sd = sd_elems ? ws.take(sizeof(T) * (size_t)sd_elems) : 0;
-    // packed entries of the shared-memory stage-1 kernel (FP32 SIMT groups with a short B^T)
-    size_t pack_bytes = 0;
-    if (sizeof(T) == 4)
-        for (size_t gi = 0; gi < C.two.size(); ++gi)
-            if (tc1[gi] != 1 && is_dense(C.two[gi].fb))
-                pack_bytes = std::max(pack_bytes, stage1_pack_bytes((int)C.two[gi].recipe.size(), plan->n_in,
-                                                                    mats[base_matrix(C.two[gi].fb, homo)]->cols));
-    const size_t off_pack = pack_bytes ? ws.take(pack_bytes) : 0;
     GVT_CHECK(ws.commit(s));
     char* base = ws.base();
 
@@ -436,9 +428,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 const double fr = fm * Y * (double)h1->n_r;
                 const double br = sz * Y * (double)K + sz * Y * X + h1->n_r * (8 + sz) + 4.0 * (X + 1);
                 StatScope sk(h, sa, GVT_STAT_SPARSE_STAGE1, fr, br);
-                GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), rem, v, S, lds, Y, X, sa,
-                                           mats[base_matrix(g.fb, homo)]->cols, h1->n_r,
-                                           pack_bytes ? base + off_pack : nullptr));
+                GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), rem, v, S, lds, Y, X, sa));
             }
             const gvt_matrix* Bm = mats[base_matrix(g.fb, homo)];
             DenseOperand a1, b1 = dense_operand_at(base + off_w, X, K, parts);
@@ -495,9 +485,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
             const double b1 = sz * Y * bcols + sz * Y * X + E * (8 + sz) + srcs.count * 4.0 * (X + 1);
             StatScope st(h, s, GVT_STAT_STAGE1, f1, b1);
             StatScope sk(h, s, GVT_STAT_SPARSE_STAGE1, f1, b1);
-            GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), srcs, v, S, lds, Y, X, s,
-                                       mats[base_matrix(g.fb, homo)]->cols, plan->n_in,
-                                       pack_bytes ? base + off_pack : nullptr));
+            GVT_CHECK(stage1_sparse<T>(B.Bt, B.ldbt, sq_mode(g.fb), srcs, v, S, lds, Y, X, s));
         }
         // every group that reads this S (same B factor, out_b range and recipe); on the dense
         // engine S is split once, and a group whose stage-2 GEMM equals the previous one (same

@@ -177,172 +177,6 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
     }
 }
 
-// ---- stage 1 from shared memory (FP32, K <= kS1SmemMaxK rows of B^T)
-// A block owns 16 rows y of S -- all K rows of B^T for them sit in shared memory, 64 bytes each --
-// and a range of columns x, taken 16 at a time (one column per warp).  The entries of the 16
-// columns are packed once per product as (row k, weight coef * v) and copied into shared memory
-// by the whole block with coalesced loads, at most kS1SmemPiece at a time.  In its column a
-// warp's 8 groups of 4 lanes take entries 8 apart; each lane multiplies its entry's weight into
-// 4 of the 16 rows (one 16-byte shared-memory read), and the groups' sums are reduced by shuffles.
-// Column sums are staged in shared memory and stored row by row.  Every B^T value is read from
-// global memory once per (row tile, column split) instead of once per entry.
-constexpr int kS1SmemRows = 16;
-constexpr int kS1SmemMaxK = 3200;            // 200 KB of B^T rows (with 16 KB of entries: 217 KB)
-constexpr int kS1SmemWarps = 16;             // columns per chunk
-constexpr int kS1SmemPiece = 2048;           // entries staged at a time (16 KB)
-
-// packed entries of one source: (bcol, coef * v[perm]) as one 8-byte record
-__global__ void pack_entries_kernel(const int32_t* __restrict__ bcol, const int32_t* __restrict__ perm, int64_t n,
-                                    const float* __restrict__ v, float coef, int2* __restrict__ pe)
-{
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        pe[j] = make_int2(bcol[j], __float_as_int(coef * v[perm[j]]));
-}
-
-struct S1Packed {
-    const int32_t* seg[kMaxSources];
-    const int2* ent[kMaxSources];
-    int count;
-};
-
-template <int MODE>
-__global__ void __launch_bounds__(kS1SmemWarps * 32, 1)
-stage1_smem_kernel(const float* __restrict__ Bt, int64_t ldb, int Kdim, S1Packed pk, float* __restrict__ S,
-                   int64_t lds, int64_t Y, int64_t X, int64_t x_per_block)
-{
-    extern __shared__ float4 s1_smem[];
-    float4* Bs = s1_smem;                                                   // Kdim x 4 float4
-    int2* ents = reinterpret_cast<int2*>(s1_smem + (size_t)Kdim * 4);        // kS1SmemPiece records
-    float* stage = reinterpret_cast<float*>(ents + kS1SmemPiece);           // 16 x (16 + 1)
-    const int64_t y0 = (int64_t)blockIdx.x * kS1SmemRows;
-    const bool full = y0 + kS1SmemRows <= Y && (ldb % 4 == 0) && ((uintptr_t)Bt % 16 == 0);
-    for (int idx = threadIdx.x; idx < Kdim * 4; idx += blockDim.x) {
-        const int k = idx >> 2, q = idx & 3;
-        const float* src = Bt + (int64_t)k * ldb + y0 + q * 4;
-        float4 b;
-        if (full) {
-            b = __ldg(reinterpret_cast<const float4*>(src));
-        } else {
-            b.x = y0 + q * 4 + 0 < Y ? __ldg(src + 0) : 0.f;
-            b.y = y0 + q * 4 + 1 < Y ? __ldg(src + 1) : 0.f;
-            b.z = y0 + q * 4 + 2 < Y ? __ldg(src + 2) : 0.f;
-            b.w = y0 + q * 4 + 3 < Y ? __ldg(src + 3) : 0.f;
-        }
-        if (MODE == FM_SQUARE) {
-            b.x *= b.x;
-            b.y *= b.y;
-            b.z *= b.z;
-            b.w *= b.w;
-        }
-        Bs[idx] = b;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane >> 2, q = lane & 3;   // entry slot 0..7, rows 4q..4q+3
-    const int64_t xb = (int64_t)blockIdx.y * x_per_block;
-    const int64_t xe = min(X, xb + x_per_block);
-    // One source: the next chunk's entries are loaded into registers while the current chunk
-    // computes (each thread holds up to kPre of them), then written to shared memory.
-    constexpr int kThreads = kS1SmemWarps * 32;
-    constexpr int kPre = kS1SmemPiece / kThreads;
-    const bool single = pk.count == 1;
-    const int32_t* seg0 = pk.seg[0];
-    const int2* ent0 = pk.ent[0];
-    int2 pre[kPre];
-    auto chunk_fits = [&](int64_t c) {
-        const int64_t ce = min(xe, c + kS1SmemWarps);
-        return single && c < xe && seg0[ce] - seg0[c] <= kS1SmemPiece;
-    };
-    auto prefetch = [&](int64_t c) {
-        const int64_t ce = min(xe, c + kS1SmemWarps);
-        const int32_t lo = seg0[c], hi = seg0[ce];
-#pragma unroll
-        for (int r = 0; r < kPre; ++r) {
-            const int32_t e = lo + (int32_t)threadIdx.x + r * kThreads;
-            pre[r] = e < hi ? __ldg(ent0 + e) : make_int2(0, 0);
-        }
-    };
-    auto commit = [&]() {
-#pragma unroll
-        for (int r = 0; r < kPre; ++r) ents[threadIdx.x + r * kThreads] = pre[r];
-    };
-    bool have = chunk_fits(xb);   // ents holds the current chunk's entries
-    if (have) {
-        prefetch(xb);
-        commit();
-    }
-    __syncthreads();   // Bs and the first chunk's entries are in place
-    for (int64_t c0 = xb; c0 < xe; c0 += kS1SmemWarps) {
-        const int nc = (int)(xe - c0 < kS1SmemWarps ? xe - c0 : kS1SmemWarps);
-        const int64_t x = c0 + warp;
-        const bool next_fits = chunk_fits(c0 + kS1SmemWarps);
-        if (next_fits) prefetch(c0 + kS1SmemWarps);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        auto accumulate = [&](int32_t lo, int32_t hi) {   // entries [lo, hi) of ents
-            int32_t j = lo + grp;
-            for (; j + 24 < hi; j += 32) {   // four entries per lane in flight
-                const int2 e0 = ents[j], e1 = ents[j + 8], e2 = ents[j + 16], e3 = ents[j + 24];
-                const float4 b0 = Bs[e0.x * 4 + q], b1 = Bs[e1.x * 4 + q];
-                const float4 b2 = Bs[e2.x * 4 + q], b3 = Bs[e3.x * 4 + q];
-                const float w0 = __int_as_float(e0.y), w1 = __int_as_float(e1.y);
-                const float w2 = __int_as_float(e2.y), w3 = __int_as_float(e3.y);
-                a0 = fmaf(w0, b0.x, a0); a1 = fmaf(w0, b0.y, a1); a2 = fmaf(w0, b0.z, a2); a3 = fmaf(w0, b0.w, a3);
-                a0 = fmaf(w1, b1.x, a0); a1 = fmaf(w1, b1.y, a1); a2 = fmaf(w1, b1.z, a2); a3 = fmaf(w1, b1.w, a3);
-                a0 = fmaf(w2, b2.x, a0); a1 = fmaf(w2, b2.y, a1); a2 = fmaf(w2, b2.z, a2); a3 = fmaf(w2, b2.w, a3);
-                a0 = fmaf(w3, b3.x, a0); a1 = fmaf(w3, b3.y, a1); a2 = fmaf(w3, b3.z, a2); a3 = fmaf(w3, b3.w, a3);
-            }
-            for (; j < hi; j += 8) {
-                const int2 e0 = ents[j];
-                const float4 b0 = Bs[e0.x * 4 + q];
-                const float w0 = __int_as_float(e0.y);
-                a0 = fmaf(w0, b0.x, a0); a1 = fmaf(w0, b0.y, a1); a2 = fmaf(w0, b0.z, a2); a3 = fmaf(w0, b0.w, a3);
-            }
-        };
-        if (have) {
-            if (warp < nc) {
-                const int32_t base = seg0[c0];
-                accumulate(seg0[x] - base, seg0[x + 1] - base);
-            }
-        } else {
-            // several sources or a chunk of more than kS1SmemPiece entries: pieces, synchronously
-#pragma unroll 1
-            for (int si = 0; si < pk.count; ++si) {
-                const int32_t* seg = pk.seg[si];
-                const int32_t jlo = seg[c0], jhi = seg[c0 + nc];
-                const int32_t mylo = warp < nc ? seg[x] : 0, myhi = warp < nc ? seg[x + 1] : 0;
-                for (int32_t p0 = jlo; p0 < jhi; p0 += kS1SmemPiece) {
-                    const int32_t p1 = min(jhi, p0 + kS1SmemPiece);
-                    __syncthreads();   // the previous piece is consumed
-                    for (int32_t e = p0 + (int32_t)threadIdx.x; e < p1; e += (int32_t)blockDim.x)
-                        ents[e - p0] = __ldg(pk.ent[si] + e);
-                    __syncthreads();
-                    accumulate(max(mylo, p0) - p0, min(myhi, p1) - p0);
-                }
-            }
-        }
-#pragma unroll
-        for (int off = 4; off < 32; off <<= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, off);
-            a3 += __shfl_xor_sync(0xffffffffu, a3, off);
-        }
-        __syncthreads();   // every warp is done with ents and with the previous chunk's store
-        if (grp == 0 && warp < nc) {
-            stage[(q * 4 + 0) * (kS1SmemWarps + 1) + warp] = a0;
-            stage[(q * 4 + 1) * (kS1SmemWarps + 1) + warp] = a1;
-            stage[(q * 4 + 2) * (kS1SmemWarps + 1) + warp] = a2;
-            stage[(q * 4 + 3) * (kS1SmemWarps + 1) + warp] = a3;
-        }
-        if (next_fits) commit();
-        have = next_fits;
-        __syncthreads();
-        for (int e = threadIdx.x; e < kS1SmemRows * nc; e += blockDim.x) {
-            const int r = e / nc, c = e % nc;
-            if (y0 + r < Y) S[(y0 + r) * lds + c0 + c] = stage[r * (kS1SmemWarps + 1) + c];
-        }
-    }
-}
-
 template <class T>
 __global__ void stage1_identity_kernel(S1Sources srcs, const T* __restrict__ v, T* __restrict__ S,
                                        int64_t lds, int64_t Y, int64_t X)
@@ -787,60 +621,11 @@ static void launch_stage1(const T* Bt, int64_t ldb, int mode, const S1Sources& s
         stage1_sparse_kernel<T, FM_DENSE, NT, RPT><<<grid, NT, 0, s>>>(Bt, ldb, srcs, v, S, lds, Y, X);
 }
 
-size_t stage1_pack_bytes(int count, int64_t n, int64_t K)
-{
-    if (K > kS1SmemMaxK || n <= 0) return 0;
-    return (size_t)count * (((size_t)n * 8 + 255) / 256 * 256);
-}
-
 template <class T>
 gvt_status stage1_sparse(const T* Bt, int64_t ldb, int mode, const S1Sources& srcs, const T* v,
-                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s, int64_t K, int64_t n_entries,
-                        void* pack)
+                        T* S, int64_t lds, int64_t Y, int64_t X, cudaStream_t s)
 {
     if (Y <= 0 || X <= 0) return GVT_OK;
-    if (sizeof(T) == 4 && pack && K > 0 && K <= kS1SmemMaxK && n_entries > 0) {
-        // FP32 with every row of B^T for 16 rows y in shared memory
-        S1Packed pk{};
-        pk.count = srcs.count;
-        char* base = static_cast<char*>(pack);
-        const size_t eb = ((size_t)n_entries * 8 + 255) / 256 * 256;
-        for (int si = 0; si < srcs.count; ++si) {
-            int2* pe = reinterpret_cast<int2*>(base + si * eb);
-            pack_entries_kernel<<<grid1d(n_entries, 256), 256, 0, s>>>(srcs.src[si].bcol, srcs.src[si].perm, n_entries,
-                                                                      reinterpret_cast<const float*>(v),
-                                                                      (float)srcs.src[si].coef, pe);
-            pk.seg[si] = srcs.src[si].seg;
-            pk.ent[si] = pe;
-        }
-        GVT_LAUNCHED(srcs.count, "stage1 pack");
-        const int64_t ytiles = (Y + kS1SmemRows - 1) / kS1SmemRows;
-        // column splits: about 3 blocks per SM in all (one block of 16 warps per SM at a time)
-        int64_t xs = std::max<int64_t>(1, std::min<int64_t>((3 * 152 + ytiles - 1) / ytiles,
-                                                            (X + kS1SmemWarps - 1) / kS1SmemWarps));
-        const int64_t xpb = (X + xs - 1) / xs;
-        xs = (X + xpb - 1) / xpb;
-        if (ytiles > 2147483647ll || xs > 65535) {
-            set_error("stage 1: too many rows or columns");
-            return GVT_ERR_UNSUPPORTED;
-        }
-        const size_t smem = (size_t)K * 64 + (size_t)kS1SmemPiece * 8 +
-                            (size_t)kS1SmemRows * (kS1SmemWarps + 1) * 4;
-        const float* B32 = reinterpret_cast<const float*>(Bt);
-        float* S32 = reinterpret_cast<float*>(S);
-        const dim3 grid((unsigned)ytiles, (unsigned)xs);
-        if (mode == FM_SQUARE) {
-            GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(stage1_smem_kernel<FM_SQUARE>), (int)smem));
-            stage1_smem_kernel<FM_SQUARE><<<grid, kS1SmemWarps * 32, smem, s>>>(B32, ldb, (int)K, pk, S32, lds, Y, X,
-                                                                                xpb);
-        } else {
-            GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(stage1_smem_kernel<FM_DENSE>), (int)smem));
-            stage1_smem_kernel<FM_DENSE><<<grid, kS1SmemWarps * 32, smem, s>>>(B32, ldb, (int)K, pk, S32, lds, Y, X,
-                                                                               xpb);
-        }
-        GVT_LAUNCH_CHECK("stage1_smem");
-        return GVT_OK;
-    }
     const int64_t gy = (X + kS1Cols - 1) / kS1Cols;
     if (gy > 65535) {
         set_error("stage 1: too many columns");
@@ -1068,7 +853,7 @@ gvt_status tanimoto_kernel(const uint32_t* X, int64_t rx, const uint32_t* Y, int
 
 #define GVT_INST(T)                                                                                 \
     template gvt_status stage1_sparse<T>(const T*, int64_t, int, const S1Sources&, const T*, T*,      \
-                                        int64_t, int64_t, int64_t, cudaStream_t, int64_t, int64_t, void*); \
+                                        int64_t, int64_t, int64_t, cudaStream_t);                     \
     template gvt_status stage1_identity<T>(const S1Sources&, const T*, T*, int64_t, int64_t,        \
                                            int64_t, cudaStream_t);                                  \
     template gvt_status stage2_gather<T>(const T*, int64_t, int, const T*, int64_t, int64_t,          \

@@ -42,6 +42,9 @@
 // segments of a split operand, kb_stride k-blocks apart; an N tile with no
 // k-block stores zeros); and a tile list, where CTA b computes only output
 // tile tile_list[b] = (m tile, n tile).
+// CTA order (one-SM grid form): groups of TC_GROUP_M m tiles, m tile fastest
+// within a group, so that the CTAs resident at one time share operand strips
+// in L2; the caller orders a tile list the same way.
 // Every wait on an mbarrier is bounded by a clock budget, and the waits of the
 // pipeline also end as soon as another thread of the CTA has timed out; on
 // expiry the thread records GVT_ERR_TIMEOUT in a device error word, the kernel
@@ -66,6 +69,10 @@ constexpr size_t TC_SMEM_LIMIT = 227 * 1024;
 constexpr int TC_THREADS = 320;           // producer warp, MMA warp, 8 folding warps
 constexpr int TC_FOLD_WARPS = 8;
 constexpr int TC_CHUNK = 8;               // k-blocks (8 x 64 = 512 of K) per accumulation chunk
+// m tiles per group of the CTA order: a wave of 152 CTAs then covers 16 A strips of 128 rows and
+// about 9 B strips of 256 rows (the two operands' bytes per wave about equal), instead of 152 A
+// strips and one B strip
+constexpr int TC_GROUP_M = 16;
 constexpr long long TC_TIMEOUT_CYCLES = 4000000000ll;   // about 2 s at 2 GHz
 constexpr long long TC_DRAIN_CYCLES = 20000000ll;       // about 10 ms
 
@@ -377,6 +384,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const int2 tl = tile_list[blockIdx.x];
         mt = tl.x;
         nt = tl.y;
+    } else if (!PAIR) {
+        // grouped order: consecutive CTAs take TC_GROUP_M m tiles (fastest) by as many n tiles as
+        // a wave holds, so that the CTAs resident at one time share their A and B strips in L2
+        const int64_t pid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        const int64_t per_group = (int64_t)TC_GROUP_M * gridDim.y;
+        const int64_t g = pid / per_group;
+        const int64_t first = g * TC_GROUP_M;
+        const int64_t gsz = min((int64_t)gridDim.x - first, (int64_t)TC_GROUP_M);
+        const int64_t r = pid - g * per_group;
+        mt = (int)(first + r % gsz);
+        nt = (int)(r / gsz);
     }
     const int m0 = mt * TC_BM;
     const int n0 = nt * BN;
