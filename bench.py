@@ -962,20 +962,33 @@ def bench_batched(H, gvt, torch, dev, n_probs, sample=32):
         probs.append(dict(M=M, N=N, d=torch.as_tensor(p.d, device=dev), t=torch.as_tensor(p.t, device=dev),
                           y=torch.as_tensor(p.y, device=dev)))
     total_pairs = sum(p.n for p in ps)
-    # first call includes the autotuner; time the second (tuned, cached) call
-    gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6)
-    (A, st, info, rr), batched_ms = timed_solve(torch, lambda: gvt.krr_solve_batched(H, probs, lambdas, rel_tol=1e-6))
+
+    def solve_on(engine, problems):
+        gvt.gvt_set_stage1_engine(H.h, engine)
+        try:
+            # first call includes the autotuner; time the second (tuned, cached) call
+            gvt.krr_solve_batched(H, problems, lambdas, rel_tol=1e-6)
+            return timed_solve(torch, lambda: gvt.krr_solve_batched(H, problems, lambdas, rel_tol=1e-6))
+        finally:
+            gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+
+    (A, st, info, rr), batched_ms = solve_on(gvt.GVT_STAGES_AUTO, probs)
+    (_, st_s, info_s, rr_s), simt_ms = solve_on(gvt.GVT_STAGE1_SIMT, probs)
     worst = max(max(r) for r in rr)
     out = {"workload": "%d problems, m,q ~ U{32..512}, density ~ U[5%%,60%%], 32-d, %d lambdas logspace(-4,0), "
                        "%d pairs total, %d systems" % (len(ps), len(lambdas), total_pairs, len(ps) * len(lambdas)),
+           "engine": "auto: tensor-core stages (FP16x3, grouped GEMMs) for the problems the cost model picks, "
+                     "SIMT stages for the others",
            "batched_ms": batched_ms, "status": gvt.STATUS_NAMES[st], "inner_iterations": int(info.iterations),
-           "refinements": int(info.refinements), "max_rel_residual": worst, "data_generation_s": gen_s}
+           "refinements": int(info.refinements), "max_rel_residual": worst, "data_generation_s": gen_s,
+           "simt_engine": {"batched_ms": simt_ms, "status": gvt.STATUS_NAMES[st_s],
+                           "inner_iterations": int(info_s.iterations), "refinements": int(info_s.refinements),
+                           "max_rel_residual": max(max(r) for r in rr_s)}}
     if sample > 0:
         step = max(1, len(ps) // sample)
         sel = list(range(0, len(ps), step))[:sample]
         sub = [probs[b] for b in sel]
-        gvt.krr_solve_batched(H, sub, lambdas, rel_tol=1e-6)
-        (A2, st2, info2, rr2), sub_ms = timed_solve(torch, lambda: gvt.krr_solve_batched(H, sub, lambdas, rel_tol=1e-6))
+        (A2, st2, info2, rr2), sub_ms = solve_on(gvt.GVT_STAGES_AUTO, sub)
         per = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -620,7 +620,7 @@ gvt_status gvt_cg_record_pairs(gvt_handle* h, gvt_plan* plan, const gvt_desc* de
 
 /* ------------------------------------------------------------ batched solves */
 
-/* One problem of a batched solve.  All pointers are device memory. */
+/* One problem of a batched solve or product.  All pointers are device memory. */
 typedef struct gvt_problem {
     int64_t m, q, n;          /* drugs, targets, training pairs; m * kc <= 25600 where kc is
                                  n_lambda rounded up to 4 (8, 16), q <= 65535 */
@@ -628,8 +628,9 @@ typedef struct gvt_problem {
     const double* N;          /* q x q FP64 target kernel, row-major (ld = q), symmetric */
     const int32_t* d;         /* n drug ids in [0, m) */
     const int32_t* t;         /* n target ids in [0, q) */
-    const double* y;          /* n labels */
-    double* a;                /* out: n x n_lambda dual coefficients, column c at a + c * n */
+    const double* y;          /* n labels (solve only; may be NULL for the product) */
+    double* a;                /* out: n x n_lambda dual coefficients, column c at a + c * n (solve
+                                 only) */
 } gvt_problem;
 
 /*
@@ -646,10 +647,37 @@ typedef struct gvt_problem {
  * the handle.  n_lambda in [1, 16].  rel_residuals (host, may be NULL)
  * receives the final FP64 relative residual of system (b, c) at
  * [b * n_lambda + c].  Synchronises `stream`.
+ * The FP32 operator follows the handle's engine (gvt_set_stage1_engine):
+ *  GVT_STAGE1_SIMT, GVT_STAGE1_TC_BF16X3 : SIMT stages for every problem.
+ *  GVT_STAGES_AUTO, GVT_STAGES_TC_F16X1  : a problem whose K' (q and m rounded up to 64) is at most
+ *      1536 runs both stages as tcgen05 GEMMs on FP16 hi/lo splits (FP32-class products) when a
+ *      cost model at measured GB300 rates favours it: stage 1 S_b = N_b Vd_b^T with the lambda
+ *      columns of the densified pair vectors as rows of Vd_b, stage 2 C_b = M_b S_b'^T with the
+ *      (target, lambda) rows of S_b, and the sampled entries read out of C_b (multi-RHS: the
+ *      kc columns share every left tile).  All such problems run in one grouped launch per stage,
+ *      beside the SIMT stages of the others.  Needs the split operands and outputs in at most half
+ *      of the free device memory, else every problem stays on the SIMT stages.
+ *  GVT_STAGES_TC_F16X3 : as AUTO, but every problem that fits runs on the tensor cores.
+ * The FP64 operator of the outer residuals always runs the SIMT stages.  Returns GVT_ERR_TIMEOUT
+ * when a bounded wait of a tensor-core stage expired.
  */
 gvt_status gvt_krr_cg_solve_batched(gvt_handle* h, const gvt_problem* probs, int64_t n_probs,
                                     const double* lambdas, int64_t n_lambda, const gvt_solve_opts* opts,
                                     double* rel_residuals, gvt_solve_info* info, void* stream);
+
+/*
+ * The FP32 operator of the batched solve on its own (Theorem 1 per problem, several vectors at
+ * once): for every problem b and column c < n_cols,
+ *   w_b[:, c] = R_b (M_b kron N_b) R_b^T v_b[:, c] + shifts[c] v_b[:, c].
+ * v[b], w[b] (host arrays of device pointers): FP32, n_b x n_cols column-major (column c at
+ * + c * n_b); may be NULL for a problem with n_b = 0.  shifts (host, finite; 0 for the plain
+ * product).  The problems' y and a are not used.  n_cols in [1, 16].  Engines as for
+ * gvt_krr_cg_solve_batched.  Prepares the batch on every call (packing, pair sorts, splits):
+ * the solve amortises that set-up, this call does not.  Synchronises `stream`; GVT_ERR_TIMEOUT
+ * as for the solve.
+ */
+gvt_status gvt_matvec_batched(gvt_handle* h, const gvt_problem* probs, int64_t n_probs, const double* shifts,
+                              int64_t n_cols, const float* const* v, float* const* w, void* stream);
 
 /* ------------------------------------------------------------ instrumentation */
 

@@ -321,6 +321,13 @@ inline int* handle_err_word(gvt_handle* h) { return static_cast<int*>(h->status.
 //    kb_list[kb_off[j] .. kb_off[j+1]) of each of the kb_parts K segments (kb_stride
 //    k-blocks apart); an N tile with an empty list stores zeros;
 //  * tile list: only the n_tiles output tiles tile_list[2b], tile_list[2b+1] = (m tile, n tile).
+// One output tile of a grouped launch: rows a_row.. of A and b_row.. of B (128 and bn of them;
+// rows past m_valid / n_valid are computed but not stored) over k-blocks 0 .. nkb-1, stored at
+// C + c_off with row stride ldc; row and column scales indexed by A and B row.
+struct TcGroupTile {
+    int32_t a_row, b_row, nkb, m_valid, n_valid, pad;
+    int64_t c_off, ldc;
+};
 struct TcSparse {
     const int* kb_list = nullptr;
     const int* kb_off = nullptr;
@@ -329,6 +336,7 @@ struct TcSparse {
     const int* tile_list = nullptr;
     int64_t n_tiles = 0;
     int bn = 256;
+    const TcGroupTile* group = nullptr;   // grouped tiles (n_tiles of them), instead of the lists
 };
 // stall_cycles > 0 (one-SM form only): the test stall of the timeout path (the GEMM's MMA thread
 // waits that many cycles on a barrier nothing arrives on; the result is then invalid).

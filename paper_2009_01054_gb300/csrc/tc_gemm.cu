@@ -42,6 +42,10 @@
 // segments of a split operand, kb_stride k-blocks apart; an N tile with no
 // k-block stores zeros); and a tile list, where CTA b computes only output
 // tile tile_list[b] = (m tile, n tile).
+// Grouped tiles (one-SM, for many small independent GEMMs in one launch): CTA b
+// reads its record group[b] -- first A row, first B row, k-block count, valid
+// rows and columns, and the output's offset and row stride -- and computes one
+// 128 x BN tile over k-blocks 0 .. nkb-1 of its rows.
 // CTA order (one-SM grid form): groups of TC_GROUP_M m tiles, m tile fastest
 // within a group, so that the CTAs resident at one time share operand strips
 // in L2; the caller orders a tile list the same way.
@@ -355,7 +359,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                float* __restrict__ C, int64_t ldc, int M, int N, int kb_total, int kb_per_split,
                int atomic_out, const float* __restrict__ row_scale, const float* __restrict__ col_scale,
                int* __restrict__ err, long long stall_cycles, const int* __restrict__ kb_list,
-               const int* __restrict__ kb_off, int kb_parts, int kb_stride, const int2* __restrict__ tile_list)
+               const int* __restrict__ kb_off, int kb_parts, int kb_stride, const int2* __restrict__ tile_list,
+               const TcGroupTile* __restrict__ group)
 {
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "UMMA N");
     static_assert(!PAIR || BN % 16 == 0, "UMMA N for M = 256");
@@ -384,6 +389,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const int2 tl = tile_list[blockIdx.x];
         mt = tl.x;
         nt = tl.y;
+    } else if (!PAIR && group) {
+        mt = nt = 0;
     } else if (!PAIR) {
         // grouped order: consecutive CTAs take TC_GROUP_M m tiles (fastest) by as many n tiles as
         // a wave holds, so that the CTAs resident at one time share their A and B strips in L2
@@ -396,14 +403,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         mt = (int)(first + r % gsz);
         nt = (int)(r / gsz);
     }
-    const int m0 = mt * TC_BM;
-    const int n0 = nt * BN;
+    // grouped tiles: A rows, B rows, k-blocks and output placement come from the tile's record
+    const TcGroupTile gt = (!PAIR && group) ? group[blockIdx.x] : TcGroupTile{};
+    const bool grouped = !PAIR && group != nullptr;
+    const int m0 = grouped ? gt.a_row : mt * TC_BM;
+    const int n0 = grouped ? gt.b_row : nt * BN;
     const int nb0 = n0 + (int)rank * B_ROWS;   // first B row this CTA loads
     // k-blocks of this CTA: a contiguous range (split K), or kb_parts copies of this N tile's list
     const int kl0 = (!PAIR && kb_list) ? kb_off[nt] : 0;
     const int kcount = (!PAIR && kb_list) ? kb_off[nt + 1] - kl0 : 0;
-    const int kb0 = blockIdx.z * kb_per_split;
-    const int kb1 = min(kb_total, kb0 + kb_per_split);
+    const int kb0 = grouped ? 0 : blockIdx.z * kb_per_split;
+    const int kb1 = grouped ? gt.nkb : min(kb_total, kb0 + kb_per_split);
     const int nkb = (!PAIR && kb_list) ? kcount * kb_parts : max(kb1 - kb0, 0);
     const int nchunks = (nkb + TC_CHUNK - 1) / TC_CHUNK;
 
@@ -569,12 +579,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         }
         asm volatile("bar.sync 1, %0;" ::"n"(TC_FOLD_WARPS * 32) : "memory");   // folding warps only
         if ((nkb > 0 || (!PAIR && kb_list != nullptr)) && *(volatile int*)&sh->timeout == 0) {
-            const int ncols = min(BN, N - n0);
-            for (int r = fw; r < TC_BM; r += TC_FOLD_WARPS) {
+            const int ncols = grouped ? min(BN, gt.n_valid) : min(BN, N - n0);
+            const int nrows = grouped ? min(TC_BM, gt.m_valid) : min(TC_BM, M - m0);
+            float* cbase = grouped ? C + gt.c_off : C + (int64_t)m0 * ldc + n0;
+            const int64_t ldo = grouped ? gt.ldc : ldc;
+            for (int r = fw; r < nrows; r += TC_FOLD_WARPS) {
                 const int gm = m0 + r;
-                if (gm >= M) break;
                 const float rs = row_scale ? row_scale[gm] : 1.f;
-                float* crow = C + (int64_t)gm * ldc + n0;
+                float* crow = cbase + (int64_t)r * ldo;
                 for (int cc = lane; cc < ncols; cc += 32) {
                     float f = stage[r * SLD + cc] * rs;
                     if (col_scale) f *= col_scale[n0 + cc];
@@ -662,7 +674,7 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     const int pairs = (int)((M + 2 * TC_BM - 1) / (2 * TC_BM));
     int gx = PAIR ? 2 * pairs : (int)((M + TC_BM - 1) / TC_BM), gy = (int)((N + BN - 1) / BN);
     const int kb_total = (int)(K / TC_BK);
-    if (sp.tile_list) {   // one CTA per listed output tile
+    if (sp.tile_list || sp.group) {   // one CTA per listed output tile
         gx = (int)sp.n_tiles;
         gy = 1;
     }
@@ -670,7 +682,7 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     // split K only when the output tiles alone leave most SMs idle (never in the sparse forms)
     int splits = tiles >= 100 ? 1 : (148 + tiles - 1) / tiles;
     splits = std::max(1, std::min(splits, kb_total / 8));
-    if (sp.kb_list || sp.tile_list) splits = 1;
+    if (sp.kb_list || sp.tile_list || sp.group) splits = 1;
     const int kb_per = (kb_total + splits - 1) / splits;
     splits = (kb_total + kb_per - 1) / kb_per;
     const int atomic_out = splits > 1 ? 1 : 0;
@@ -695,7 +707,7 @@ gvt_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int
     cfg.numAttrs = PAIR ? 1 : 0;
     GVT_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, C, ldc, (int)M, (int)N, kb_total, kb_per, atomic_out, rs, cs,
                                 err, stall, sp.kb_list, sp.kb_off, sp.kb_parts, sp.kb_stride,
-                                reinterpret_cast<const int2*>(sp.tile_list)));
+                                reinterpret_cast<const int2*>(sp.tile_list), sp.group));
     GVT_LAUNCH_CHECK("tc_gemm");
     return GVT_OK;
 }
@@ -719,20 +731,27 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
 {
     const TcSparse sp = sparse ? *sparse : TcSparse{};
     if (M <= 0 || N <= 0) return GVT_OK;
-    if (K <= 0 || K % TC_BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N ||
-        ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M > INT32_MAX || N > INT32_MAX || K / TC_BK > INT32_MAX) {
+    const bool grouped = sp.group != nullptr;
+    if (K <= 0 || K % TC_BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K ||
+        (!grouped && ldc < N) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M > INT32_MAX || N > INT32_MAX ||
+        K / TC_BK > INT32_MAX) {
         set_error("tc_gemm: K must be a positive multiple of 64, lda/ldb multiples of 8, "
                   "A and B 16-byte aligned");
         return GVT_ERR_INVALID_ARG;
     }
-    if ((M + TC_BM - 1) / TC_BM > 2147483647ll || (N + 63) / 64 > 65535) {
+    if (grouped && (sp.kb_list || sp.tile_list || sp.n_tiles > INT32_MAX)) {
+        set_error("tc_gemm: grouped tiles take no k-block or tile list, and at most 2^31 - 1 tiles");
+        return GVT_ERR_INVALID_ARG;
+    }
+    if (grouped && sp.n_tiles == 0) return GVT_OK;
+    if ((M + TC_BM - 1) / TC_BM > 2147483647ll || (!grouped && (N + 63) / 64 > 65535)) {
         set_error("tc_gemm: matrix too large");
         return GVT_ERR_UNSUPPORTED;
     }
     GVT_CHECK(get_encode());
     // SM pairs only on request: on GB300 both forms reach the same rate on these shapes (the
     // pair form reads 30 % fewer operand bytes per SM, but the loads are not the bound)
-    const bool pair = pair_mode == GVT_TC_PAIRS_ON && !sp.kb_list && !sp.tile_list;   // sparse forms: one SM
+    const bool pair = pair_mode == GVT_TC_PAIRS_ON && !sp.kb_list && !sp.tile_list && !grouped;   // one SM
     if (sp.kb_list && sp.tile_list) {
         set_error("tc_gemm: a block-sparse B and a tile list cannot be combined");
         return GVT_ERR_INVALID_ARG;
@@ -753,7 +772,7 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
         const int64_t t256 = gx * ((N + 255) / 256), t224 = gx * ((N + 223) / 224);
         if (t256 < t224 && t224 <= 152) BN = 224;
     }
-    if (sp.kb_list || sp.tile_list) {   // the caller's tiling fixes the N tile
+    if (sp.kb_list || sp.tile_list || grouped) {   // the caller's tiling fixes the N tile
         if (sp.bn != 64 && sp.bn != 128 && sp.bn != 224 && sp.bn != 256) {
             set_error("tc_gemm: sparse forms need an N tile of 64, 128, 224 or 256");
             return GVT_ERR_INVALID_ARG;

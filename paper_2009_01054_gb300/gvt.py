@@ -122,6 +122,7 @@ SIGNATURES = [
                                  c_vp, c_dbl, c_vp, _P(gvt_solve_opts), _P(gvt_solve_info), c_vp]),
     ("gvt_krr_cg_solve_batched", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, _P(gvt_solve_opts), c_vp,
                                          _P(gvt_solve_info), c_vp]),
+    ("gvt_matvec_batched", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
     ("gvt_set_stage1_engine", c_i32, [c_vp, c_i32]),
     ("gvt_set_tc_pairs", c_i32, [c_vp, c_i32]),
     ("gvt_factor_cache_begin", c_i32, [c_vp]),
@@ -273,6 +274,41 @@ def gvt_krr_cg_solve_batched(h, probs, lambdas, opts, stream):
         raise GvtError(st, "gvt_krr_cg_solve_batched", last_error())
     res = [[rr[b * len(lambdas) + c] for c in range(len(lambdas))] for b in range(len(probs))]
     return st, info, res
+
+
+def gvt_matvec_batched(h, probs, shifts, v_ptrs, w_ptrs, stream):
+    """probs: list of gvt_problem; v_ptrs / w_ptrs: device pointers per problem (FP32, n x n_cols
+    column-major); raises on a non-zero status."""
+    arr = (gvt_problem * len(probs))(*probs)
+    sh = (c_dbl * len(shifts))(*shifts)
+    vin = (c_vp * len(probs))(*[c_vp(x) for x in v_ptrs])
+    wout = (c_vp * len(probs))(*[c_vp(x) for x in w_ptrs])
+    _call("gvt_matvec_batched", h, ctypes.cast(arr, c_vp), len(probs), ctypes.cast(sh, c_vp), len(shifts),
+          ctypes.cast(vin, c_vp), ctypes.cast(wout, c_vp), stream)
+
+
+def matvec_batched(handle, problems, vectors, shifts=None, stream=None):
+    """The batched FP32 operator: for every problem (dict with CUDA tensors M, N (FP64), d, t
+    (int32)) and every column c of its vectors (n x n_cols FP32 tensor),
+    w[:, c] = R (M kron N) R^T v[:, c] + shifts[c] v[:, c].  Returns the list of w (n x n_cols)."""
+    torch = _torch()
+    keep, probs, vin, outs = [], [], [], []
+    for p, v in zip(problems, vectors):
+        d = p["d"].to(torch.int32).contiguous()
+        t = p["t"].to(torch.int32).contiguous()
+        M = p["M"].to(torch.float64).contiguous()
+        N = p["N"].to(torch.float64).contiguous()
+        vt = v.to(torch.float32).t().contiguous()          # n_cols x n: column c at + c * n
+        w = torch.empty_like(vt)
+        keep += [d, t, M, N, vt]
+        vin.append(vt.data_ptr())
+        outs.append(w)
+        probs.append(gvt_problem(M.shape[0], N.shape[0], d.numel(), c_vp(M.data_ptr()), c_vp(N.data_ptr()),
+                                 c_vp(d.data_ptr()), c_vp(t.data_ptr()), None, None))
+    n_cols = vectors[0].shape[1]
+    shifts = [0.0] * n_cols if shifts is None else list(shifts)
+    gvt_matvec_batched(handle.h, probs, shifts, vin, [w.data_ptr() for w in outs], stream_ptr(stream))
+    return [w.t() for w in outs]
 
 
 def krr_solve_batched(handle, problems, lambdas, rel_tol=1e-6, inner_tol=1e-3, max_iter=20000,
