@@ -95,6 +95,7 @@ def parse():
                          "off = one SM per 128-row tile; on = SM pairs (256-row tiles, tcgen05 cta_group::2)")
     ap.add_argument("--solve-lambdas", default="1e-4,1e-2,1")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-sparse-hbm", action="store_true")
     ap.add_argument("--no-headline", action="store_true",
                     help="skip the headline product (profiling runs of the other sections); the line then "
                          "carries no value")
@@ -665,7 +666,7 @@ def run_gvt(args, ws, rank, local):
         c5_precond = bench_c5_precond(H, gvt, torch, dev,
                                       p if head == "c5" and p is not None else
                                       workload("c5", 0, args.c5_m, args.c5_n))
-    sparse_hbm = bench_sparse_hbm(gvt, torch, dev, peaks) if rank == 0 and not args.no_all_kernels else None
+    sparse_hbm = bench_sparse_hbm(gvt, torch, dev, peaks) if rank == 0 and not args.no_sparse_hbm else None
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(H, gvt, torch, dev, args.batched_problems, args.batched_sample)

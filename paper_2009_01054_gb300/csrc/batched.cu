@@ -611,29 +611,38 @@ __global__ void __launch_bounds__(32 * kTcSplitRows)
 b_tc_split_kernel(const int2* __restrict__ items, const BSplit* __restrict__ sets, const float* __restrict__ src,
                   uint4* __restrict__ dst, int64_t pitch_u4, float* __restrict__ inv_scale, int pattern_b)
 {
+    __shared__ float scale[kTcSplitRows];
     const int2 it = items[blockIdx.x];
     const BSplit S = sets[it.x];
-    const int r = it.y + (int)(threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= S.rows) return;
-    const float* row = src + S.src_off + (int64_t)r * S.ld;
-    float m = 0.f;
-    for (int k = lane; k < S.cols; k += 32) m = fmaxf(m, fabsf(row[k]));
+    const int nr = min(kTcSplitRows, S.rows - it.y);   // rows of this block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < nr) {   // row scales, a warp per row
+        const int64_t r = it.y + warp;
+        const float* row = src + S.src_off + r * S.ld;
+        float m = 0.f;
+        for (int k = lane; k < S.cols; k += 32) m = fmaxf(m, fabsf(row[k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    float sc, inv;
-    row_scale(m, sc, inv);
-    const int64_t drow = S.dst_row + r;
-    if (lane == 0) inv_scale[drow] = inv;
-    uint4* d = dst + drow * pitch_u4;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        float sc, inv;
+        row_scale(m, sc, inv);
+        if (lane == 0) {
+            scale[warp] = sc;
+            inv_scale[S.dst_row + r] = inv;
+        }
+    }
+    __syncthreads();
+    // the splits, every thread on consecutive 8-value groups of the block's rows (coalesced stores)
     const int per_row = S.kp / 8;
-    for (int q = lane; q < per_row; q += 32) {
+    for (int e = threadIdx.x; e < nr * per_row; e += blockDim.x) {
+        const int rr = e / per_row, q = e % per_row;
+        const int64_t r = it.y + rr;
+        const float* row = src + S.src_off + r * S.ld;
         float xs[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) xs[e] = q * 8 + e < S.cols ? row[q * 8 + e] : 0.f;
+        for (int k = 0; k < 8; ++k) xs[k] = q * 8 + k < S.cols ? row[q * 8 + k] : 0.f;
         uint4 hi, lo;
-        split8_f16(xs, sc, hi, lo);
-        store3(d, q, per_row, pattern_b, kTcParts, hi, lo);
+        split8_f16(xs, scale[rr], hi, lo);
+        store3(dst + (S.dst_row + r) * pitch_u4, q, per_row, pattern_b, kTcParts, hi, lo);
     }
 }
 
@@ -646,12 +655,13 @@ b_tc_densify_kernel(const int2* __restrict__ items, const BTc* __restrict__ tcp,
                     const int32_t* __restrict__ perm, const float* __restrict__ V, int kc,
                     uint4* __restrict__ dst, int64_t pitch_u4, float* __restrict__ inv_scale)
 {
-    extern __shared__ float vrow[];   // kc x kp1
+    extern __shared__ float4 vrow4[];   // kc x kp1 floats
+    float* vrow = reinterpret_cast<float*>(vrow4);
     const int2 it = items[blockIdx.x];
     const BTc T = tcp[it.x];
     const BProb P = probs[T.b];
     const int x = it.y, kp = T.kp1;
-    for (int e = threadIdx.x; e < kc * kp; e += blockDim.x) vrow[e] = 0.f;
+    for (int e = threadIdx.x; e < kc * kp / 4; e += blockDim.x) vrow4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int32_t* sg = seg + P.seg_off;
     const int j0 = sg[x], nj = sg[x + 1] - j0;
@@ -661,9 +671,9 @@ b_tc_densify_kernel(const int2* __restrict__ items, const BTc* __restrict__ tcp,
         atomicAdd(&vrow[c * kp + tcol[g]], V[(P.n_off + perm[g]) * kc + c]);
     }
     __syncthreads();
+    __shared__ float scale[KC_MAX];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_row = kp / 8;
-    for (int c = warp; c < kc; c += 8) {
+    for (int c = warp; c < kc; c += 8) {   // row scales, a warp per row
         const float* vr = vrow + c * kp;
         float m = 0.f;
         for (int k = lane; k < kp; k += 32) m = fmaxf(m, fabsf(vr[k]));
@@ -671,17 +681,22 @@ b_tc_densify_kernel(const int2* __restrict__ items, const BTc* __restrict__ tcp,
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         float sc, inv;
         row_scale(m, sc, inv);
-        const int64_t drow = T.b1_row + (int64_t)c * P.m + x;
-        if (lane == 0) inv_scale[drow] = inv;
-        uint4* d = dst + drow * pitch_u4;
-        for (int q = lane; q < per_row; q += 32) {
-            float xs[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) xs[e] = vr[q * 8 + e];
-            uint4 hi, lo;
-            split8_f16(xs, sc, hi, lo);
-            store3(d, q, per_row, 1, kTcParts, hi, lo);
+        if (lane == 0) {
+            scale[c] = sc;
+            inv_scale[T.b1_row + (int64_t)c * P.m + x] = inv;
         }
+    }
+    __syncthreads();
+    // the splits, every thread on consecutive 8-value groups of the kc rows (coalesced stores)
+    const int per_row = kp / 8;
+    for (int e = threadIdx.x; e < kc * per_row; e += blockDim.x) {
+        const int c = e / per_row, q = e % per_row;
+        const float4* src = reinterpret_cast<const float4*>(vrow + c * kp + q * 8);
+        const float4 a = src[0], b = src[1];
+        const float xs[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint4 hi, lo;
+        split8_f16(xs, scale[c], hi, lo);
+        store3(dst + (T.b1_row + (int64_t)c * P.m + x) * pitch_u4, q, per_row, 1, kTcParts, hi, lo);
     }
 }
 

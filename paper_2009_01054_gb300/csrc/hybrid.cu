@@ -20,10 +20,10 @@
 // The break-even counts and the choice between SIMT, dense and per-tile come from
 // a cost model with rates measured on GB300 at the kernel-filling scale (20000 x
 // 20000 ids, 10M pairs): the FP16x3 GEMM executes 1.3e15 flop/s; a sparse stage-1
-// entry of the per-tile remainder streams its factor row (4 Y bytes) at about
-// 6.7e12 B/s and a sampled dot its two rows (about 5 X bytes, the A row shared by
-// neighbouring outputs) at about 7.4e12 B/s (the remainder's rows belong to
-// low-degree ids and rarely stay in L2).
+// entry of the per-tile remainder takes its factor row (4 Y bytes, in 1024-row
+// slices that stay in L2 during a pass) at about 1.0e13 B/s, and a sampled dot its
+// two rows (about 5 X bytes, the A row shared by neighbouring outputs) at about
+// 6.2e12 B/s (the remainder's rows belong to low-degree ids and rarely stay in L2).
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -34,8 +34,8 @@ namespace gvt {
 namespace {
 
 constexpr double kTcRate = 1.3e15;        // executed flop/s of the split GEMM
-constexpr double kStage1Bw = 6.7e12;      // bytes/s of a sparse stage-1 entry's row stream
-constexpr double kStage2Bw = 7.4e12;      // bytes/s of a sampled dot's row streams
+constexpr double kStage1Bw = 1.0e13;      // bytes/s of a sparse stage-1 entry's row stream
+constexpr double kStage2Bw = 6.2e12;      // bytes/s of a sampled dot's row streams
 constexpr double kPassBw = 4e12;          // split, densify and merge passes
 constexpr double kFixed = 8e-6;           // per dense stage (launches, ring fill, epilogue)
 
