@@ -36,12 +36,12 @@
 // hop to every ring slot and measured half the speed.)
 // Epilogue: the folding warps stage the 128 x BN tile in the (then idle) ring
 // memory and store it row by row, 32 consecutive columns per warp instruction.
-// Two sparse forms (one-SM only, no split K), for the per-tile dense/sparse
-// stages: a block-sparse B, where the CTA of N tile j runs only over the
+// Two sparse forms (no split K), for the per-tile dense/sparse stages: a
+// block-sparse B (also in the SM-pair form), where the CTA of N tile j runs only over the
 // k-blocks kb_list[kb_off[j] .. kb_off[j+1]) (in each of the `parts` K
 // segments of a split operand, kb_stride k-blocks apart; an N tile with no
 // k-block stores zeros); and a tile list, where CTA b computes only output
-// tile tile_list[b] = (m tile, n tile).
+// tile tile_list[b] = (m tile, n tile) (one SM).
 // Grouped tiles (one-SM, for many small independent GEMMs in one launch): CTA b
 // reads its record group[b] -- first A row, first B row, k-block count, valid
 // rows and columns, and the output's offset and row stride -- and computes one
@@ -391,16 +391,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         nt = tl.y;
     } else if (!PAIR && group) {
         mt = nt = 0;
-    } else if (!PAIR) {
-        // grouped order: consecutive CTAs take TC_GROUP_M m tiles (fastest) by as many n tiles as
-        // a wave holds, so that the CTAs resident at one time share their A and B strips in L2
-        const int64_t pid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-        const int64_t per_group = (int64_t)TC_GROUP_M * gridDim.y;
+    } else {
+        // grouped order: consecutive CTAs (clusters, in the SM-pair form) take TC_GROUP_M m tiles
+        // (fastest) by as many n tiles as a wave holds, so that the CTAs resident at one time share
+        // their A and B strips in L2; both CTAs of a pair get the same 256-row tile
+        const int64_t ux = PAIR ? gridDim.x / 2 : gridDim.x;   // units along m: tiles or pairs
+        const int64_t gm = PAIR ? TC_GROUP_M / 2 : TC_GROUP_M;
+        const int64_t pid = (int64_t)blockIdx.y * ux + (PAIR ? blockIdx.x >> 1 : blockIdx.x);
+        const int64_t per_group = gm * gridDim.y;
         const int64_t g = pid / per_group;
-        const int64_t first = g * TC_GROUP_M;
-        const int64_t gsz = min((int64_t)gridDim.x - first, (int64_t)TC_GROUP_M);
+        const int64_t first = g * gm;
+        const int64_t gsz = min(ux - first, gm);
         const int64_t r = pid - g * per_group;
-        mt = (int)(first + r % gsz);
+        const int unit = (int)(first + r % gsz);
+        mt = PAIR ? unit * 2 + (int)rank : unit;
         nt = (int)(r / gsz);
     }
     // grouped tiles: A rows, B rows, k-blocks and output placement come from the tile's record
@@ -410,11 +414,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int n0 = grouped ? gt.b_row : nt * BN;
     const int nb0 = n0 + (int)rank * B_ROWS;   // first B row this CTA loads
     // k-blocks of this CTA: a contiguous range (split K), or kb_parts copies of this N tile's list
-    const int kl0 = (!PAIR && kb_list) ? kb_off[nt] : 0;
-    const int kcount = (!PAIR && kb_list) ? kb_off[nt + 1] - kl0 : 0;
+    const int kl0 = kb_list ? kb_off[nt] : 0;
+    const int kcount = kb_list ? kb_off[nt + 1] - kl0 : 0;
     const int kb0 = grouped ? 0 : blockIdx.z * kb_per_split;
     const int kb1 = grouped ? gt.nkb : min(kb_total, kb0 + kb_per_split);
-    const int nkb = (!PAIR && kb_list) ? kcount * kb_parts : max(kb1 - kb0, 0);
+    const int nkb = kb_list ? kcount * kb_parts : max(kb1 - kb0, 0);
     const int nchunks = (nkb + TC_CHUNK - 1) / TC_CHUNK;
 
     if (threadIdx.x == 0) {
@@ -455,8 +459,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 }
                 if (*(volatile int*)&sh->timeout) break;
                 unsigned char* sa = tiles + st * STAGE_BYTES;
-                const int kx = ((!PAIR && kb_list) ? (i / kcount) * kb_stride + kb_list[kl0 + i % kcount] : kb0 + i) *
-                               TC_BK;
+                const int kx = (kb_list ? (i / kcount) * kb_stride + kb_list[kl0 + i % kcount] : kb0 + i) * TC_BK;
                 if constexpr (PAIR) {
                     // the leader's slot completes when the loads of both CTAs landed
                     if (leader) mbar_expect_tx(&sh->full[st], 2 * STAGE_BYTES);
@@ -509,11 +512,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 if (ok) umma_commit<PAIR>(&sh->acc_full[b]);
             }
             sh->consumed = i;
-            if constexpr (PAIR) {
+            if (PAIR && i > 0) {
                 // the peer's shared memory and TMEM stay in use until these MMAs complete
                 umma_commit_local_pair(&sh->mma_done);
                 if (!mbar_wait(&sh->mma_done, 0)) atomicExch(&sh->timeout, 1);
-            } else if (i > 0) {
+            } else if (!PAIR && i > 0) {
                 // TMEM is freed at the end: every MMA issued must have completed by then, also
                 // when a timeout left its accumulator unread
                 umma_commit<false>(&sh->mma_done);
@@ -531,7 +534,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
         for (int e = 0; e < HALF; ++e) acc[e] = 0.f;
         // (an N tile without k-blocks in the block-sparse form stores its zero sums)
-        bool good = nkb > 0 || (!PAIR && kb_list != nullptr);
+        bool good = nkb > 0 || kb_list != nullptr;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             if (!mbar_wait(&sh->acc_full[b], (c >> 1) & 1, &sh->timeout)) {
@@ -578,7 +581,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             for (int e = 0; e < HALF; ++e) stage[row * SLD + col0 + e] = acc[e];
         }
         asm volatile("bar.sync 1, %0;" ::"n"(TC_FOLD_WARPS * 32) : "memory");   // folding warps only
-        if ((nkb > 0 || (!PAIR && kb_list != nullptr)) && *(volatile int*)&sh->timeout == 0) {
+        if ((nkb > 0 || kb_list != nullptr) && *(volatile int*)&sh->timeout == 0) {
             const int ncols = grouped ? min(BN, gt.n_valid) : min(BN, N - n0);
             const int nrows = grouped ? min(TC_BM, gt.m_valid) : min(TC_BM, M - m0);
             float* cbase = grouped ? C + gt.c_off : C + (int64_t)m0 * ldc + n0;
@@ -751,7 +754,9 @@ gvt_status tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float
     GVT_CHECK(get_encode());
     // SM pairs only on request: on GB300 both forms reach the same rate on these shapes (the
     // pair form reads 30 % fewer operand bytes per SM, but the loads are not the bound)
-    const bool pair = pair_mode == GVT_TC_PAIRS_ON && !sp.kb_list && !sp.tile_list && !grouped;   // one SM
+    // SM pairs on request, also for a block-sparse B (both CTAs of a pair share the N tile and
+    // its k-block list); tile lists and grouped tiles run on one SM
+    const bool pair = pair_mode == GVT_TC_PAIRS_ON && !sp.tile_list && !grouped;
     if (sp.kb_list && sp.tile_list) {
         set_error("tc_gemm: a block-sparse B and a tile list cannot be combined");
         return GVT_ERR_INVALID_ARG;

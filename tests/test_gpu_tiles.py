@@ -134,3 +134,28 @@ def test_per_tile_in_a_mixed_solve(H, zp):
     print("oracle estimate of the residual on 200 rows: %.2e" % est)
     assert est <= 2e-6
     plan.close()
+
+
+def test_per_tile_sm_pairs_match_one_sm(H, zp):
+    """The block-sparse stage-1 GEMM in the SM-pair form (two CTAs per 256-row tile sharing the N
+    tile's k-block list, some lists empty): the per-tile product equals the oracle within the FP32
+    tolerance and the one-SM form's product to FP32 rounding."""
+    p = zp
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=DEV), gamma=p.gamma, dtype=torch.float32)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=DEV), gamma=p.gamma, dtype=torch.float32)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=DEV)
+    u1, _ = _product(H, plan, M, N, v, gvt.GVT_STAGES_AUTO, gvt.GVT_TILES_ON)
+    gvt.gvt_set_tc_pairs(H.h, gvt.GVT_TC_PAIRS_ON)
+    try:
+        u2, st = _product(H, plan, M, N, v, gvt.GVT_STAGES_AUTO, gvt.GVT_TILES_ON)
+    finally:
+        gvt.gvt_set_tc_pairs(H.h, gvt.GVT_TC_PAIRS_AUTO)
+    rows = np.sort(np.random.default_rng(8).choice(p.n, 300, replace=False))
+    ref, _ = _rows_ref(p, rows, v.double().cpu().numpy())
+    err = float(np.max(np.abs(u2[rows] - ref)) / np.max(np.abs(ref)))
+    diff = float(np.max(np.abs(u2 - u1)) / np.max(np.abs(u1)))
+    print("per tile on SM pairs: error %.2e, difference to one SM %.2e" % (err, diff))
+    assert st["tc_gemm"]["launches"] == 2
+    assert err <= 1e-5 and diff <= 2e-6
+    plan.close()
