@@ -435,6 +435,12 @@ gvt_status gvt_solve_opts_default(gvt_solve_opts* o);
  * into the handle's workspace.  Synchronises `stream`.  On
  * GVT_ERR_NOT_CONVERGED / GVT_ERR_BREAKDOWN `a` holds the last iterate and
  * `info` (may be NULL) is filled in.
+ * The CG iterations run on a stream the handle owns, after everything queued
+ * on `stream` and before anything queued on it later.  Without a
+ * preconditioner and with statistics off, blocks of check_every iterations
+ * are captured once into a CUDA graph after the first block and replayed
+ * (the product must not change its device buffers in between, which holds
+ * within one solve); the results are those of the eager loop.
  */
 gvt_status gvt_krr_cg_solve(gvt_handle* h, gvt_plan* plan, const gvt_desc* desc,
                             const gvt_matrix* M, const gvt_matrix* N,

@@ -17,6 +17,7 @@ std::atomic<long long> g_launches{0};
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long gvt_launch_count_internal() { return g_launches.load(std::memory_order_relaxed); }
 
 StatScope::StatScope(gvt_handle* h_, cudaStream_t s_, int kind_, double flops_, double bytes_, double useful_)
     : h(h_), s(s_), kind(kind_), flops(flops_), bytes(bytes_), useful(useful_ < 0.0 ? flops_ : useful_)
@@ -286,6 +287,9 @@ gvt_status gvt_destroy(gvt_handle* h)
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux_fork) cudaEventDestroy(h->aux_fork);
     if (h->aux_join) cudaEventDestroy(h->aux_join);
+    if (h->cg_stream) cudaStreamDestroy(h->cg_stream);
+    if (h->cg_fork) cudaEventDestroy(h->cg_fork);
+    if (h->cg_join) cudaEventDestroy(h->cg_join);
     delete h;
     return GVT_OK;
 }

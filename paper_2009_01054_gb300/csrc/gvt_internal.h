@@ -35,6 +35,7 @@ gvt_status ensure_smem_attr(const void* func, int bytes);
 
 // Count `n` kernel launches made just before and check their launch status.
 void count_launches(int n);
+long long gvt_launch_count_internal();
 #define GVT_LAUNCHED(n, what)                                              \
     do {                                                                   \
         ::gvt::count_launches(n);                                          \
@@ -103,6 +104,8 @@ struct gvt_handle {
     // use), with the events that fork it from and join it to the caller's stream
     cudaStream_t aux = nullptr;
     cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
+    cudaStream_t cg_stream = nullptr;   // CG iterations (captured into graphs in steady state)
+    cudaEvent_t cg_fork = nullptr, cg_join = nullptr;
     std::map<std::tuple<int, int64_t, int>, int> batch_tune;   // batched stage-1 tile choice
     std::vector<gvt::StatRec> recs;
     std::vector<cudaEvent_t> event_pool;

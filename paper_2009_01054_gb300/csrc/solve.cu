@@ -219,7 +219,7 @@ template <class T, class TA>
 gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, const gvt_matrix* N,
                   const T* b, double bnorm, double lam, TA* x, T* r, T* p, T* w, double* part, double* sc,
                   double* hsc, double tol, int64_t max_iter, int check_every, int64_t* iters, double* rel,
-                  cudaStream_t s, gvt_precond* P = nullptr, T* z = nullptr, const History* hist = nullptr)
+                  cudaStream_t s_caller, gvt_precond* P = nullptr, T* z = nullptr, const History* hist = nullptr)
 {
     const int64_t n = plan->n_in;
     *iters = 0;
@@ -228,6 +228,31 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
         *rel = 0.0;
         return GVT_OK;
     }
+    // The iterations run on the handle's CG stream (a capture cannot start on the legacy default
+    // stream), after everything queued on the caller's stream so far; on every return the caller's
+    // stream waits for them.
+    cudaStream_t s = s_caller;
+    gvt_handle* h = plan->h;
+    if (h) {
+        if (!h->cg_stream) {
+            GVT_CUDA(cudaStreamCreateWithFlags(&h->cg_stream, cudaStreamNonBlocking));
+            GVT_CUDA(cudaEventCreateWithFlags(&h->cg_fork, cudaEventDisableTiming));
+            GVT_CUDA(cudaEventCreateWithFlags(&h->cg_join, cudaEventDisableTiming));
+        }
+        GVT_CUDA(cudaEventRecord(h->cg_fork, s_caller));
+        GVT_CUDA(cudaStreamWaitEvent(h->cg_stream, h->cg_fork, 0));
+        s = h->cg_stream;
+    }
+    struct JoinGuard {
+        gvt_handle* h;
+        cudaStream_t caller;
+        ~JoinGuard()
+        {
+            if (!h) return;
+            cudaEventRecord(h->cg_join, h->cg_stream);
+            cudaStreamWaitEvent(caller, h->cg_join, 0);
+        }
+    } join_guard{h, s_caller};
     copy_kernel<T><<<vgrid(n), 256, 0, s>>>(r, b, n);
     dot_kernel<T, T><<<kRedBlocks, kRedThreads, 0, s>>>(r, r, n, part);
     finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 2);
@@ -272,17 +297,43 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
         if (hist) hist->add(ring_it[slot], *rel);
         return *rel <= tol ? 1 : 0;
     };
-    int64_t it = 0;
-    while (it < max_iter) {
+    // Steady-state iterations of plain CG replay from a CUDA graph: after the first block of
+    // check_every iterations (the workspace grown, per-tile forms and split factors built), one
+    // block is captured and replayed while at least check_every iterations remain.  A product that
+    // cannot be captured (or statistics, whose events are read per launch) keeps the loop eager.
+    auto cg_iteration = [&]() -> gvt_status {
         GVT_CHECK(pairwise_apply<T>(plan, desc, M, N, p, w, s));
         shift_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lam, n, part);
-        if (!P) {
-            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
-            update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
-            finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
-            pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
-            GVT_LAUNCHED(5, "cg iteration");
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 0);
+        update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
+        finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 1);
+        pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, r, n, sc);
+        GVT_LAUNCHED(5, "cg iteration");
+        return GVT_OK;
+    };
+    struct GraphGuard {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        ~GraphGuard()
+        {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+        }
+    } graph;
+    bool try_graph = !P && !(plan->h && plan->h->stats_on);
+    long long graph_launches = 0;   // kernels in one replayed block
+    int64_t it = 0;
+    while (it < max_iter) {
+        if (graph.e && it % check_every == 0 && it + check_every <= max_iter) {
+            GVT_CUDA(cudaGraphLaunch(graph.e, s));
+            count_launches((int)graph_launches);
+            it += check_every;
+        } else if (!P) {
+            GVT_CHECK(cg_iteration());
+            ++it;
         } else {
+            GVT_CHECK(pairwise_apply<T>(plan, desc, M, N, p, w, s));
+            shift_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, s>>>(w, p, lam, n, part);
             finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 5);
             update_kernel<T, TA><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, n, sc, part);
             finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 6);
@@ -294,8 +345,8 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
             finalize_kernel<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sc, 8);
             pupdate_kernel<T><<<vgrid(n), 256, 0, s>>>(p, z, n, sc);
             GVT_LAUNCHED(5, "fcg iteration");
+            ++it;
         }
-        ++it;
         if (it % check_every == 0 || it == max_iter) {
             const int slot = next_slot;
             next_slot ^= 1;
@@ -327,6 +378,26 @@ gvt_status cg_run(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix* M, con
                 }
             }
             pending = slot;
+        }
+        if (try_graph && it == check_every) {
+            try_graph = false;
+            const long long before = gvt_launch_count_internal();
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                gvt_status gst = GVT_OK;
+                for (int k = 0; k < check_every && gst == GVT_OK; ++k) gst = cg_iteration();
+                cudaGraph_t g = nullptr;
+                const cudaError_t ce = cudaStreamEndCapture(s, &g);
+                if (gst == GVT_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&graph.e, g, 0) == cudaSuccess) {
+                    graph.g = g;
+                } else {
+                    if (g) cudaGraphDestroy(g);
+                    graph.e = nullptr;
+                }
+            }
+            cudaGetLastError();   // a capture that failed leaves the loop eager
+            // the captured kernels ran nowhere yet: they are counted when a block replays
+            graph_launches = gvt_launch_count_internal() - before;
+            count_launches(-(int)graph_launches);
         }
     }
     *iters = it;
