@@ -10,7 +10,10 @@
 //   beta = rr' / rr                               (one block)
 //   p = r + beta p
 // Dot products reduce in FP64 in a fixed order (per-block partials, then one
-// block), so a run is bitwise reproducible.
+// block), so a run is bitwise reproducible.  The iterations run on a stream the
+// handle owns, joined to the caller's by events; in steady state blocks of
+// iterations replay from a CUDA graph (the launches of small problems are then
+// no longer separated by the host's launch gaps).
 #include <cuda_bf16.h>
 
 #include <chrono>
