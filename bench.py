@@ -583,6 +583,25 @@ def bench_products(args, gvt, torch, dev, name, p, K, W, ws, dist, local, flush,
             res["engines"][args.engine + "_without_tiles"] = {"ms_per_step": off_ms,
                                                               "value": ws * pts / (off_ms / 1e3), "unit": UNIT}
             pr.set_tiles(gvt.GVT_TILES_AUTO)
+        if args.engine == "auto":
+            # the single-pass FP16 stages: the inner operator of the mixed-precision solves (its
+            # products carry 2^-11 relative errors, which the FP64 refinement removes)
+            pr.set_engine(gvt.GVT_STAGES_TC_F16X1)
+            for _ in range(2):
+                pr.step()
+            torch.cuda.synchronize()
+            k1 = max(3, min(K, 10))
+            f1_ms = time_steps(torch, pr.step, k1, flush, pr.stream)
+            gvt.gvt_stats_enable(H.h, True)
+            for _ in range(k1):
+                flush.zero_()
+                pr.step(nstreams=1)
+            torch.cuda.synchronize()
+            st1 = gvt.gvt_stats_read(H.h)
+            gvt.gvt_stats_enable(H.h, False)
+            res["engines"]["f16x1"] = {"ms_per_step": f1_ms, "value": ws * pts / (f1_ms / 1e3), "unit": UNIT,
+                                       "stages": stage_summary(st1, k1)}
+            pr.set_engine(engine_code)
     return pr, res
 
 

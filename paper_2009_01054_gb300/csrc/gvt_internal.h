@@ -184,7 +184,7 @@ struct HybridS1 {                   // stage 1: S = B W with W's columns x, rows
     double cost[3] = {0, 0, 0};
 };
 struct HybridS2 {                   // stage 2: u_i = <A[a_i, :], S[s_i, :]> over the output pairs
-    int oa = -1, ob = -1, parts = 0;
+    int oa = -1, ob = -1, parts = 0, eb = 4;
     int64_t MA = 0, YS = 0, X = 0;
     int bm = 128, bn = 256;         // output tile of the GEMM C' = A' S'^T
     int64_t na = 0, nb = 0;
@@ -195,6 +195,7 @@ struct HybridS2 {                   // stage 2: u_i = <A[a_i, :], S[s_i, :]> ove
     int32_t *arow_d = nullptr, *srow_d = nullptr, *perm_d = nullptr;  // outputs in dense tiles, relabelled
     int64_t n_d = 0;
     int32_t *arow_r = nullptr, *srow_r = nullptr, *perm_r = nullptr;  // remainder outputs, by a
+    int32_t *arow_rl = nullptr, *srow_rl = nullptr;   // the remainder's rows relabelled (a', s')
     int64_t n_r = 0;
     int mode = 0;
     double cost[3] = {0, 0, 0};
@@ -277,6 +278,11 @@ struct S2Outputs {
 template <class T>
 gvt_status stage2_gather(const T* A, int64_t lda, int mode, const T* S, int64_t lds, int64_t X,
                         const S2Outputs& outs, double coef, T* u, cudaStream_t s);
+// The same over FP16 rows of A and S scaled by powers of two (inverses ascale, sscale per row),
+// dots accumulated in FP32; X, lda and lds multiples of 8, both bases 16-byte aligned.
+gvt_status stage2_gather_f16(const void* A, int64_t lda, const float* ascale, const void* S, int64_t lds,
+                             const float* sscale, int64_t X, const S2Outputs& outs, double coef, float* u,
+                             cudaStream_t s);
 // u[perm_i] += C[arow_i, srow_i] (the dense stage 2's sampled read-out)
 gvt_status dense_gather(const float* C, int64_t ldc, const S2Outputs& outs, float* u, cudaStream_t s);
 // A = identity: u[perm_i] += coef * S[srow_i, arow_i] (arow_i < X)
@@ -387,9 +393,11 @@ gvt_status dense_gemm(const DenseOperand& a, const DenseOperand& b, bool f16, fl
 // ---------------------------------------------------------------- per-tile dense/sparse stages
 // The per-tile form of stage 1 (x component ia, inner component ib, Y rows of S) or of stage 2
 // (A rows component oa, S rows component ob, inner length X) for `parts` 16-bit GEMM parts, with
-// the mode the cost model picks; built on first use and kept in the plan.
+// the mode the cost model picks; built on first use and kept in the plan.  Stage 2's sparse
+// remainder reads `eb` bytes per row entry (4: FP32; 2: the FP16 operands of the single pass).
 gvt_status hybrid_stage1(gvt_plan* p, int ia, int ib, int64_t Y, int parts, cudaStream_t s, const HybridS1** out);
-gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cudaStream_t s, const HybridS2** out);
+gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, int eb, cudaStream_t s,
+                         const HybridS2** out);
 
 // ---------------------------------------------------------------- pairwise driver
 // u = R_out K_desc R_in^T v for one column (all pointers device; T = float/double).

@@ -24,6 +24,10 @@
 // slices that stay in L2 during a pass) at about 1.0e13 B/s, and a sampled dot its
 // two rows (about 5 X bytes, the A row shared by neighbouring outputs) at about
 // 6.2e12 B/s (the remainder's rows belong to low-degree ids and rarely stay in L2).
+// On the single pass stage 2's remainder reads the GEMM's FP16 operands instead (half
+// the bytes, at the same rate), and the model counts their bytes.  Stage 1's remainder
+// stays on FP32 factor rows: its time is set by the entries, not by their bytes
+// (measured: FP16 rows made it slower).
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -160,10 +164,11 @@ gvt_status hybrid_stage1(gvt_plan* p, int ia, int ib, int64_t Y, int parts, cuda
     return GVT_OK;
 }
 
-gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cudaStream_t s, const HybridS2** out)
+gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, int eb, cudaStream_t s,
+                         const HybridS2** out)
 {
     for (auto& h : p->hyb2)
-        if (h.oa == oa && h.ob == ob && h.X == X && h.parts == parts) {
+        if (h.oa == oa && h.ob == ob && h.X == X && h.parts == parts && h.eb == eb) {
             *out = &h;
             return GVT_OK;
         }
@@ -173,6 +178,7 @@ gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cuda
     H.ob = ob;
     H.X = X;
     H.parts = parts;
+    H.eb = eb;
     const Order& oA = p->out_by[oa];
     const Order& oS = p->out_by[ob];
     H.MA = oA.K;
@@ -193,7 +199,7 @@ gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cuda
     for (int64_t i = 0; i < n; ++i) cnt[(size_t)((arank[arow[i]] / H.bm) * H.nb + srank[srow[i]] / H.bn)]++;
     const double kp = (double)((X + 63) / 64 * 64);
     const double tile_t = 2.0 * H.bm * H.bn * kp * parts / kTcRate;
-    const double out_t = 5.0 * X / kStage2Bw;
+    const double out_t = 1.25 * eb * X / kStage2Bw;   // the S row and a share of the A row
     const double thr = tile_t / out_t;
     std::vector<uint8_t> dense(cnt.size(), 0);
     std::vector<int32_t> tiles;
@@ -209,7 +215,7 @@ gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cuda
                     tiles.push_back((int32_t)nt);
                 }
     H.n_tiles = (int64_t)tiles.size() / 2;
-    std::vector<int32_t> arow_d, srow_d, perm_d, arow_r, srow_r, perm_r;
+    std::vector<int32_t> arow_d, srow_d, perm_d, arow_r, srow_r, perm_r, arow_rl, srow_rl;
     for (int64_t i = 0; i < n; ++i) {
         const int32_t a = arank[arow[i]], b = srank[srow[i]];
         if (dense[(size_t)((a / H.bm) * H.nb + b / H.bn)]) {
@@ -220,6 +226,8 @@ gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cuda
             arow_r.push_back(arow[i]);
             srow_r.push_back(srow[i]);
             perm_r.push_back(perm[i]);
+            arow_rl.push_back(a);
+            srow_rl.push_back(b);
         }
     }
     H.n_d = (int64_t)arow_d.size();
@@ -238,6 +246,8 @@ gvt_status hybrid_stage2(gvt_plan* p, int oa, int ob, int64_t X, int parts, cuda
     GVT_CHECK(to_device(p, arow_r, &H.arow_r));
     GVT_CHECK(to_device(p, srow_r, &H.srow_r));
     GVT_CHECK(to_device(p, perm_r, &H.perm_r));
+    GVT_CHECK(to_device(p, arow_rl, &H.arow_rl));
+    GVT_CHECK(to_device(p, srow_rl, &H.srow_rl));
     p->hyb2.push_back(H);
     *out = &p->hyb2.back();
     return GVT_OK;

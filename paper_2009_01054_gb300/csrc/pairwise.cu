@@ -277,7 +277,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 tc2[gj] = chooses ? dense_pays(mb, Y, X, 2.0 * X * (double)n_out, parts) : 1;
                 if (tiles_ok && g2.oa != g2.ob) {
                     const HybridS2* h2 = nullptr;
-                    GVT_CHECK(hybrid_stage2(plan, g2.oa, g2.ob, X, parts, s, &h2));
+                    GVT_CHECK(hybrid_stage2(plan, g2.oa, g2.ob, X, parts, parts == 1 ? 2 : 4, s, &h2));
                     tc2[gj] = h->stage_tiles == GVT_TILES_ON ? 2 : (char)h2->mode;
                 }
                 if (!tc2[gj]) continue;
@@ -509,12 +509,24 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 // per tile: the dense output tiles on the tile-list GEMM C' = A' S'^T (rows relabelled)
                 // and read out of C'; the other outputs by the sampled gather-dot
                 const HybridS2* h2 = nullptr;
-                GVT_CHECK(hybrid_stage2(plan, g2.oa, g2.ob, X, parts, s, &h2));
+                GVT_CHECK(hybrid_stage2(plan, g2.oa, g2.ob, X, parts, parts == 1 ? 2 : 4, s, &h2));
                 const int64_t mb = out_range(plan, g2.oa);
                 const int64_t ldc2 = round_up(Y, 4);
                 const double fm = sq_mode(g2.fa) ? 3.0 : 2.0;
                 StatScope st(h, s, GVT_STAT_STAGE2, fm * X * n_out,
                              sz * ((double)mb * X + (double)Y * X) + (double)n_out * (12 + 2 * sz));
+                const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
+                DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X, parts);
+                // single pass: the remainder's dots read the GEMM's own FP16 operands (A' and S', rows
+                // relabelled and scaled by powers of two), so the splits come first
+                const bool rem16 = h2->eb == 2 && h2->n_r > 0;
+                auto split_operands = [&]() -> gvt_status {
+                    GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2, h2->aperm, nullptr));
+                    GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s,
+                                               h2->sperm, nullptr));
+                    return GVT_OK;
+                };
+                if (rem16) GVT_CHECK(split_operands());
                 // the remainder's sampled dots (HBM-bound) on the auxiliary stream beside the tile-list
                 // GEMM; they add into disjoint outputs of u
                 cudaStream_t sa = nullptr;
@@ -522,16 +534,19 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 {
                     const FactorView<T>& A = fv[base_matrix(g2.fa, homo)];
                     const double fr = fm * X * (double)h2->n_r;
-                    const double br = sz * ((double)mb * X + (double)Y * X) + (double)h2->n_r * (12 + 2 * sz);
+                    const double zb = rem16 ? 2.0 : sz;
+                    const double br = zb * ((double)mb * X + (double)Y * X) + (double)h2->n_r * (12 + 2 * sz);
                     StatScope sk(h, sa, GVT_STAT_SPARSE_STAGE2, fr, br);
-                    GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X,
-                                               S2Outputs{h2->arow_r, h2->srow_r, h2->perm_r, h2->n_r}, 1.0, u, sa));
+                    if (rem16)
+                        GVT_CHECK(stage2_gather_f16(a2.data, a2.kp, a2.inv_scale, s2.data, s2.kp, s2.inv_scale, a2.kp,
+                                                    S2Outputs{h2->arow_rl, h2->srow_rl, h2->perm_r, h2->n_r}, 1.0,
+                                                    reinterpret_cast<float*>(u), sa));
+                    else
+                        GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X,
+                                                   S2Outputs{h2->arow_r, h2->srow_r, h2->perm_r, h2->n_r}, 1.0, u,
+                                                   sa));
                 }
-                const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
-                DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X, parts);
-                GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2, h2->aperm, nullptr));
-                GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s,
-                                           h2->sperm, nullptr));
+                if (!rem16) GVT_CHECK(split_operands());
                 s_split = false;   // s2 now holds the relabelled split
                 float* C2 = reinterpret_cast<float*>(base + off_c2);
                 TcSparse sp;

@@ -12,6 +12,7 @@
 // per output pair, outputs sorted by arow so that consecutive warps share the
 // A row in L1; 16-byte vector loads of both rows.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -33,6 +34,29 @@ template <> struct Vec<double> {
     __device__ static void split(const double2& q, double* o) { o[0] = q.x; o[1] = q.y; }
     __device__ static double2 make(const double* o) { return make_double2(o[0], o[1]); }
 };
+
+// 16-byte loads of a stored type TB widened to the arithmetic type T (FP16 storage: the
+// single-pass operands of the dense stages, rows scaled by powers of two, read in FP32)
+template <class TB, class T> struct Ld;
+template <> struct Ld<float, float> : Vec<float> {};
+template <> struct Ld<double, double> : Vec<double> {};
+template <> struct Ld<__half, float> {
+    using type = uint4;
+    static constexpr int N = 8;
+    __device__ static void split(const uint4& q, float* o)
+    {
+        const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(h[e]);
+            o[2 * e] = f.x;
+            o[2 * e + 1] = f.y;
+        }
+    }
+};
+__device__ __forceinline__ float ld1(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ld1(const double* p) { return __ldg(p); }
 
 __host__ __device__ inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -216,14 +240,17 @@ constexpr int kS2Group = 4;      // outputs per warp, processed together
 // Three blocks per SM (at most 80 registers a thread, a few spilled): the kernel waits on its row
 // loads, and 24 warps per SM hide that latency better than the 16 that 114 registers allowed
 // (measured: 9.05 -> 7.67 ms for the kernel-filling remainder, 11.1 -> 9.5 ms at 0.2 % density).
-template <class T, int MODE>
+// FP16 storage (TB = __half): A and S rows scaled by powers of two, whose inverses (ascale,
+// sscale, one per row) multiply each finished dot.
+template <class T, class TB, int MODE>
 __global__ void __launch_bounds__(kS2Threads, 3)
-stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ S, int64_t lds,
+stage2_gather_kernel(const TB* __restrict__ A, int64_t lda, const float* __restrict__ ascale,
+                    const TB* __restrict__ S, int64_t lds, const float* __restrict__ sscale,
                     int64_t X, S2Outputs outs, T coef, T* __restrict__ u)
 {
-    constexpr int VEC = Vec<T>::N;
+    constexpr int VEC = Ld<TB, T>::N;
     constexpr int G = kS2Group;
-    using VT = typename Vec<T>::type;
+    using VT = typename Ld<TB, T>::type;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (kS2Threads / 32);
     const bool vec_ok = (lda % VEC == 0) && (lds % VEC == 0) && aligned16(A) && aligned16(S);
@@ -240,8 +267,8 @@ stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__
         }
         const int32_t ar0 = __shfl_sync(0xffffffffu, ar, 0);
         const bool same = __all_sync(0xffffffffu, lane >= ng || ar == ar0);
-        const T* arow[G];
-        const T* srow[G];
+        const TB* arow[G];
+        const TB* srow[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             // groups shorter than G repeat their last output; only real ones are written
@@ -255,9 +282,9 @@ stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__
         if (same) {
             for (int64_t x = (int64_t)lane * VEC; x < xv; x += 32 * VEC) {
                 T a[VEC], sv[G][VEC];
-                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(arow[0] + x)), a);
+                Ld<TB, T>::split(__ldg(reinterpret_cast<const VT*>(arow[0] + x)), a);
 #pragma unroll
-                for (int g = 0; g < G; ++g) Vec<T>::split(__ldg(reinterpret_cast<const VT*>(srow[g] + x)), sv[g]);
+                for (int g = 0; g < G; ++g) Ld<TB, T>::split(__ldg(reinterpret_cast<const VT*>(srow[g] + x)), sv[g]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     const T ak = MODE == FM_SQUARE ? a[k] * a[k] : a[k];
@@ -270,8 +297,8 @@ stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__
                 T a[G][VEC], sv[G][VEC];
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
-                    Vec<T>::split(__ldg(reinterpret_cast<const VT*>(arow[g] + x)), a[g]);
-                    Vec<T>::split(__ldg(reinterpret_cast<const VT*>(srow[g] + x)), sv[g]);
+                    Ld<TB, T>::split(__ldg(reinterpret_cast<const VT*>(arow[g] + x)), a[g]);
+                    Ld<TB, T>::split(__ldg(reinterpret_cast<const VT*>(srow[g] + x)), sv[g]);
                 }
 #pragma unroll
                 for (int g = 0; g < G; ++g)
@@ -285,8 +312,9 @@ stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__
         for (int64_t x = xv + lane; x < X; x += 32) {
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                const T ak = MODE == FM_SQUARE ? arow[g][x] * arow[g][x] : arow[g][x];
-                acc[g] = fma(ak, srow[g][x], acc[g]);
+                const T av = (T)ld1(arow[g] + x);
+                const T ak = MODE == FM_SQUARE ? av * av : av;
+                acc[g] = fma(ak, (T)ld1(srow[g] + x), acc[g]);
             }
         }
 #pragma unroll
@@ -298,6 +326,7 @@ stage2_gather_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__
 #pragma unroll
             for (int g = 1; g < G; ++g)
                 if (lane == g) mine = acc[g];
+            if (ascale) mine *= (T)ascale[ar] * (T)sscale[sr];
             u[pm] += coef * mine;
         }
     }
@@ -671,10 +700,25 @@ gvt_status stage2_gather(const T* A, int64_t lda, int mode, const T* S, int64_t 
     const int64_t groups = (outs.n + kS2Group - 1) / kS2Group;
     const int64_t g = std::min<int64_t>((groups + (kS2Threads / 32) - 1) / (kS2Threads / 32), 152 * 64);
     if (mode == FM_SQUARE)
-        stage2_gather_kernel<T, FM_SQUARE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
+        stage2_gather_kernel<T, T, FM_SQUARE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, nullptr, S, lds, nullptr, X,
+                                                                                 outs, (T)coef, u);
     else
-        stage2_gather_kernel<T, FM_DENSE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, S, lds, X, outs, (T)coef, u);
+        stage2_gather_kernel<T, T, FM_DENSE><<<(unsigned)g, kS2Threads, 0, s>>>(A, lda, nullptr, S, lds, nullptr, X,
+                                                                                outs, (T)coef, u);
     GVT_LAUNCH_CHECK("stage2_gather");
+    return GVT_OK;
+}
+
+gvt_status stage2_gather_f16(const void* A, int64_t lda, const float* ascale, const void* S, int64_t lds,
+                             const float* sscale, int64_t X, const S2Outputs& outs, double coef, float* u,
+                             cudaStream_t s)
+{
+    if (outs.n <= 0) return GVT_OK;
+    const int64_t groups = (outs.n + kS2Group - 1) / kS2Group;
+    const int64_t g = std::min<int64_t>((groups + (kS2Threads / 32) - 1) / (kS2Threads / 32), 152 * 64);
+    stage2_gather_kernel<float, __half, FM_DENSE><<<(unsigned)g, kS2Threads, 0, s>>>(
+        static_cast<const __half*>(A), lda, ascale, static_cast<const __half*>(S), lds, sscale, X, outs, (float)coef, u);
+    GVT_LAUNCH_CHECK("stage2_gather_f16");
     return GVT_OK;
 }
 

@@ -159,3 +159,51 @@ def test_per_tile_sm_pairs_match_one_sm(H, zp):
     assert st["tc_gemm"]["launches"] == 2
     assert err <= 1e-5 and diff <= 2e-6
     plan.close()
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_per_tile_single_pass_squared_factors(H, zp, symmetric):
+    """One term with squared factors, (M o M) x (N o N), on the single-pass per-tile stages, with
+    the kernel matrices passed as symmetric or not (stage 1 then works on B itself or on a
+    transposed copy).  Stage 2's sparse remainder reads the dense stages' FP16 operands (entries
+    squared before rounding, rows relabelled and scaled by powers of two); the product stays
+    within the single-pass bound of the oracle's, 4u of the term magnitudes (u = 2^-11)."""
+    p = zp
+    M = gvt.gaussian_kernel(H, torch.as_tensor(p.Xd, device=DEV), gamma=p.gamma, dtype=torch.float32)
+    N = gvt.gaussian_kernel(H, torch.as_tensor(p.Xt, device=DEV), gamma=p.gamma, dtype=torch.float32)
+    plan = gvt.Plan(H, (p.m, p.m), (p.q, p.q), p.d, p.t)
+    v = torch.as_tensor(p.v, dtype=torch.float32, device=DEV)
+    d = gvt.gvt_desc()
+    d.kind, d.n_terms, d.homogeneous = -1, 1, 0
+    t = d.terms[0]
+    t.coef = 1.0
+    t.factor_a, t.factor_b = gvt.GVT_FACTOR_M_SQ, gvt.GVT_FACTOR_N_SQ
+    t.out_a, t.out_b, t.in_a, t.in_b = gvt.GVT_FIRST, gvt.GVT_SECOND, gvt.GVT_FIRST, gvt.GVT_SECOND
+    gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGES_TC_F16X1)
+    gvt.gvt_set_stage_tiles(H.h, gvt.GVT_TILES_ON)
+    gvt.gvt_stats_enable(H.h, True)
+    try:
+        u = gvt.pairwise_kernel_matvec(plan, d, M, N, v, symmetric=symmetric).double().cpu().numpy()
+        gvt.gvt_check_device_errors(H.h, gvt.stream_ptr())
+        st = gvt.gvt_stats_read(H.h)
+    finally:
+        gvt.gvt_stats_enable(H.h, False)
+        gvt.gvt_set_stage_tiles(H.h, gvt.GVT_TILES_AUTO)
+        gvt.gvt_set_stage1_engine(H.h, gvt.GVT_STAGE1_SIMT)
+    rows = np.sort(np.random.default_rng(9).choice(p.n, 300, replace=False))
+    ud, id_ = np.unique(p.d[rows], return_inverse=True)
+    ut, it_ = np.unique(p.t[rows], return_inverse=True)
+    Mo = orc.gaussian_kernel(p.Xd[ud], p.Xd, gamma=p.gamma) ** 2
+    No = orc.gaussian_kernel(p.Xt[ut], p.Xt, gamma=p.gamma) ** 2
+    vv = v.double().cpu().numpy()
+    ia, it = id_.astype(np.int32), it_.astype(np.int32)
+    ref = orc.pairwise_matvec("kronecker", Mo, No, ia, it, p.d, p.t, vv)
+    mag = orc.pairwise_matvec("kronecker", Mo, No, ia, it, p.d, p.t, np.abs(vv))
+    err_m = float(np.max(np.abs(u[rows] - ref)) / np.max(mag))
+    print("squared factors, single pass per tile (symmetric %s): %.2e of max |K||v|; sparse stage 1 %d, "
+          "sparse stage 2 %d launches" % (symmetric, err_m, st["sparse_stage1"]["launches"],
+                                          st["sparse_stage2"]["launches"]))
+    assert st["tc_gemm"]["launches"] == 2
+    assert st["sparse_stage1"]["launches"] == 1 and st["sparse_stage2"]["launches"] == 1
+    assert err_m <= 4 * 2.0 ** -11
+    plan.close()
