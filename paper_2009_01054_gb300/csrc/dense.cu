@@ -35,7 +35,13 @@ using split16::store3;
 
 constexpr int kSplitThreads = 256;
 constexpr int64_t kRowSmemMax = 160 * 1024;   // widest W^T row (bytes) densified in shared memory
+// Row passes that gather through a column permutation stage the row in shared memory first: a
+// gather straight from global memory reads a 32-byte sector per 4-byte value.  1024 threads a
+// block and rows of up to 100 KB keep two blocks (64 warps) on an SM.
+constexpr int kPermThreads = 1024;
+constexpr int64_t kPermRowMax = 100 * 1024;
 
+// largest of v over the block (red: one slot per warp)
 __device__ __forceinline__ float block_max(float v, float* red)
 {
 #pragma unroll
@@ -164,6 +170,92 @@ __global__ void merge_cols_kernel(float* __restrict__ S, int64_t lds, const floa
         float* srow = S + y * lds;
         const float* drow = Sd + y * ldsd;
         for (int64_t x = threadIdx.x; x < X; x += blockDim.x) srow[x] += __ldg(drow + xrank[x]);
+    }
+}
+
+// The same with the row of Sd staged in shared memory (4 X bytes), one row per pass of a block.
+__global__ void __launch_bounds__(kPermThreads)
+merge_cols_smem_kernel(float* __restrict__ S, int64_t lds, const float* __restrict__ Sd, int64_t ldsd,
+                       const int32_t* __restrict__ xrank, int64_t Y, int64_t X)
+{
+    extern __shared__ float drow_s[];
+    const bool vec = (lds % 4 == 0) && (ldsd % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(Sd) & 15) == 0) && ((reinterpret_cast<uintptr_t>(xrank) & 15) == 0);
+    const int64_t xv = vec ? X / 4 * 4 : 0;
+    for (int64_t y = blockIdx.x; y < Y; y += gridDim.x) {
+        const float* drow = Sd + y * ldsd;
+        float* srow = S + y * lds;
+        __syncthreads();   // the previous row's gathers are done
+        for (int64_t x = (int64_t)threadIdx.x * 4; x < xv; x += 4 * blockDim.x)
+            *reinterpret_cast<float4*>(drow_s + x) = __ldg(reinterpret_cast<const float4*>(drow + x));
+        for (int64_t x = xv + threadIdx.x; x < X; x += blockDim.x) drow_s[x] = __ldg(drow + x);
+        __syncthreads();
+        for (int64_t x = (int64_t)threadIdx.x * 4; x < xv; x += 4 * blockDim.x) {
+            const int4 r = __ldg(reinterpret_cast<const int4*>(xrank + x));
+            float4 v = *reinterpret_cast<const float4*>(srow + x);
+            v.x += drow_s[r.x];
+            v.y += drow_s[r.y];
+            v.z += drow_s[r.z];
+            v.w += drow_s[r.w];
+            *reinterpret_cast<float4*>(srow + x) = v;
+        }
+        for (int64_t x = xv + threadIdx.x; x < X; x += blockDim.x) srow[x] += drow_s[xrank[x]];
+    }
+}
+
+// split_rows_kernel for a column permutation: the source row (cols values) is staged in shared
+// memory, its largest magnitude taken on the way, then split through colperm from there.
+template <bool F16>
+__global__ void __launch_bounds__(kPermThreads)
+split_rows_perm_kernel(const float* __restrict__ src, int64_t ld, int64_t cols, int square, int pattern_b,
+                       uint4* __restrict__ dst, float* __restrict__ inv_scale, int64_t kp, int parts,
+                       const int32_t* __restrict__ rowperm, const int32_t* __restrict__ colperm)
+{
+    extern __shared__ float row_s[];
+    __shared__ float red[kPermThreads / 32];
+    const int64_t r = blockIdx.x;
+    const float* row = src + (rowperm ? (int64_t)rowperm[r] : r) * ld;
+    float m = 0.f;
+    const bool vec = ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
+    const int64_t cv = vec ? cols / 4 * 4 : 0;
+    for (int64_t k = (int64_t)threadIdx.x * 4; k < cv; k += 4 * blockDim.x) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(row + k));
+        if (square) {
+            a.x *= a.x;
+            a.y *= a.y;
+            a.z *= a.z;
+            a.w *= a.w;
+        }
+        *reinterpret_cast<float4*>(row_s + k) = a;
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+    }
+    for (int64_t k = cv + threadIdx.x; k < cols; k += blockDim.x) {
+        float a = __ldg(row + k);
+        if (square) a *= a;
+        row_s[k] = a;
+        m = fmaxf(m, fabsf(a));
+    }
+    float s = 1.f;
+    if (F16) {
+        float inv;
+        row_scale(block_max(m, red), s, inv);   // (its barriers also publish row_s)
+        if (threadIdx.x == 0) inv_scale[r] = inv;
+    } else {
+        __syncthreads();
+    }
+    const int64_t per_row = kp / 8;
+    uint4* d = dst + r * parts * per_row;
+    for (int64_t q = threadIdx.x; q < per_row; q += blockDim.x) {
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t k = q * 8 + e;
+            x[e] = k < cols ? row_s[colperm[k]] : 0.f;
+        }
+        uint4 hi, lo;
+        if (F16) split8_f16(x, s, hi, lo);
+        else split8_bf16(x, hi, lo);
+        store3(d, q, per_row, pattern_b, parts, hi, lo);
     }
 }
 
@@ -304,7 +396,18 @@ gvt_status dense_split_rows(const float* src, int64_t ld, int64_t rows, int64_t 
         return GVT_ERR_UNSUPPORTED;
     }
     uint4* d = static_cast<uint4*>(dst.data);
-    if (f16)
+    const int64_t perm_smem = 4 * ((cols + 3) / 4 * 4);
+    if (colperm && perm_smem <= kPermRowMax) {
+        const void* fn = f16 ? reinterpret_cast<const void*>(split_rows_perm_kernel<true>)
+                             : reinterpret_cast<const void*>(split_rows_perm_kernel<false>);
+        if (perm_smem > 48 * 1024) GVT_CHECK(ensure_smem_attr(fn, (int)perm_smem));
+        if (f16)
+            split_rows_perm_kernel<true><<<(unsigned)rows, kPermThreads, (size_t)perm_smem, s>>>(
+                src, ld, cols, square, pattern_b, d, dst.inv_scale, dst.kp, dst.parts, rowperm, colperm);
+        else
+            split_rows_perm_kernel<false><<<(unsigned)rows, kPermThreads, (size_t)perm_smem, s>>>(
+                src, ld, cols, square, pattern_b, d, dst.inv_scale, dst.kp, dst.parts, rowperm, colperm);
+    } else if (f16)
         split_rows_kernel<true><<<(unsigned)rows, kSplitThreads, 0, s>>>(src, ld, cols, square, pattern_b, d,
                                                                          dst.inv_scale, dst.kp, dst.parts, rowperm,
                                                                          colperm);
@@ -388,7 +491,15 @@ gvt_status dense_merge_cols(float* S, int64_t lds, const float* Sd, int64_t ldsd
                             int64_t X, cudaStream_t s)
 {
     if (Y <= 0 || X <= 0) return GVT_OK;
-    merge_cols_kernel<<<(unsigned)std::min<int64_t>(Y, 152 * 8), 256, 0, s>>>(S, lds, Sd, ldsd, xrank, Y, X);
+    const int64_t smem = 4 * ((X + 3) / 4 * 4);
+    if (smem <= kPermRowMax) {
+        if (smem > 48 * 1024)
+            GVT_CHECK(ensure_smem_attr(reinterpret_cast<const void*>(merge_cols_smem_kernel), (int)smem));
+        merge_cols_smem_kernel<<<(unsigned)std::min<int64_t>(Y, 152 * 2), kPermThreads, (size_t)smem, s>>>(
+            S, lds, Sd, ldsd, xrank, Y, X);
+    } else {
+        merge_cols_kernel<<<(unsigned)std::min<int64_t>(Y, 152 * 8), 256, 0, s>>>(S, lds, Sd, ldsd, xrank, Y, X);
+    }
     GVT_LAUNCH_CHECK("merge dense part of S");
     return GVT_OK;
 }
