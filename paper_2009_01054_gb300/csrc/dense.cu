@@ -203,6 +203,86 @@ merge_cols_smem_kernel(float* __restrict__ S, int64_t lds, const float* __restri
     }
 }
 
+// The merge fused with the split of S that follows it: block r takes row y = rowperm[r] (r without
+// rowperm), stages Sd's row y in shared memory, forms S[y, x] + Sd[y, xrank[x]], writes it back
+// to S (for the consumers of S in FP32) and splits it as dst row r.  A thread keeps its values of
+// the merged row in registers between the two passes: groups of 8, at most kMergeGroups a thread
+// (kp <= 8 * kMergeGroups * kPermThreads).
+constexpr int kMergeGroups = 4;
+template <bool F16>
+__global__ void __launch_bounds__(kPermThreads)
+merge_split_rows_kernel(float* __restrict__ S, int64_t lds, const float* __restrict__ Sd, int64_t ldsd,
+                        const int32_t* __restrict__ xrank, int64_t X, int pattern_b, uint4* __restrict__ dst,
+                        float* __restrict__ inv_scale, int64_t kp, int parts, const int32_t* __restrict__ rowperm)
+{
+    extern __shared__ float drow_s[];
+    __shared__ float red[kPermThreads / 32];
+    const int64_t r = blockIdx.x;
+    const int64_t y = rowperm ? (int64_t)rowperm[r] : r;
+    float* srow = S + y * lds;
+    const float* drow = Sd + y * ldsd;
+    const bool vec = (lds % 4 == 0) && (ldsd % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(Sd) & 15) == 0);
+    const int64_t xv = vec ? X / 4 * 4 : 0;
+    for (int64_t x = (int64_t)threadIdx.x * 4; x < xv; x += 4 * blockDim.x)
+        *reinterpret_cast<float4*>(drow_s + x) = __ldg(reinterpret_cast<const float4*>(drow + x));
+    for (int64_t x = xv + threadIdx.x; x < X; x += blockDim.x) drow_s[x] = __ldg(drow + x);
+    __syncthreads();
+    const int64_t per_row = kp / 8;
+    float val[kMergeGroups][8];
+    float m = 0.f;
+#pragma unroll
+    for (int g = 0; g < kMergeGroups; ++g) {
+        const int64_t q = threadIdx.x + (int64_t)g * blockDim.x;
+        const int64_t x0 = q * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) val[g][e] = 0.f;
+        if (q >= per_row || x0 >= X) continue;
+        if (vec && x0 + 8 <= X) {
+            float4 a = *reinterpret_cast<const float4*>(srow + x0);
+            float4 b = *reinterpret_cast<const float4*>(srow + x0 + 4);
+            a.x += drow_s[xrank[x0]];
+            a.y += drow_s[xrank[x0 + 1]];
+            a.z += drow_s[xrank[x0 + 2]];
+            a.w += drow_s[xrank[x0 + 3]];
+            b.x += drow_s[xrank[x0 + 4]];
+            b.y += drow_s[xrank[x0 + 5]];
+            b.z += drow_s[xrank[x0 + 6]];
+            b.w += drow_s[xrank[x0 + 7]];
+            *reinterpret_cast<float4*>(srow + x0) = a;
+            *reinterpret_cast<float4*>(srow + x0 + 4) = b;
+            val[g][0] = a.x; val[g][1] = a.y; val[g][2] = a.z; val[g][3] = a.w;
+            val[g][4] = b.x; val[g][5] = b.y; val[g][6] = b.z; val[g][7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (x0 + e < X) {
+                    const float v = srow[x0 + e] + drow_s[xrank[x0 + e]];
+                    srow[x0 + e] = v;
+                    val[g][e] = v;
+                }
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(val[g][e]));
+    }
+    float sc = 1.f;
+    if (F16) {
+        float inv;
+        row_scale(block_max(m, red), sc, inv);
+        if (threadIdx.x == 0) inv_scale[r] = inv;
+    }
+    uint4* d = dst + r * parts * per_row;
+#pragma unroll
+    for (int g = 0; g < kMergeGroups; ++g) {
+        const int64_t q = threadIdx.x + (int64_t)g * blockDim.x;
+        if (q >= per_row) continue;
+        uint4 hi, lo;
+        if (F16) split8_f16(val[g], sc, hi, lo);
+        else split8_bf16(val[g], hi, lo);
+        store3(d, q, per_row, pattern_b, parts, hi, lo);
+    }
+}
+
 // split_rows_kernel for a column permutation: the source row (cols values) is staged in shared
 // memory, its largest magnitude taken on the way, then split through colperm from there.
 template <bool F16>
@@ -501,6 +581,35 @@ gvt_status dense_merge_cols(float* S, int64_t lds, const float* Sd, int64_t ldsd
         merge_cols_kernel<<<(unsigned)std::min<int64_t>(Y, 152 * 8), 256, 0, s>>>(S, lds, Sd, ldsd, xrank, Y, X);
     }
     GVT_LAUNCH_CHECK("merge dense part of S");
+    return GVT_OK;
+}
+
+bool dense_merge_split_fits(int64_t X)
+{
+    return 4 * ((X + 3) / 4 * 4) <= kPermRowMax && dense_kp(X) <= 8 * kMergeGroups * kPermThreads;
+}
+
+gvt_status dense_merge_split(float* S, int64_t lds, const float* Sd, int64_t ldsd, const int32_t* xrank, int64_t Y,
+                             int64_t X, bool f16, int pattern_b, const DenseOperand& dst, cudaStream_t s,
+                             const int32_t* rowperm)
+{
+    if (Y <= 0 || X <= 0) return GVT_OK;
+    if (!dense_merge_split_fits(X) || dst.kp != dense_kp(X) || Y > INT32_MAX) {
+        set_error("merge and split of S: row too long");
+        return GVT_ERR_UNSUPPORTED;
+    }
+    const int64_t smem = 4 * ((X + 3) / 4 * 4);
+    const void* fn = f16 ? reinterpret_cast<const void*>(merge_split_rows_kernel<true>)
+                         : reinterpret_cast<const void*>(merge_split_rows_kernel<false>);
+    if (smem > 48 * 1024) GVT_CHECK(ensure_smem_attr(fn, (int)smem));
+    uint4* d = static_cast<uint4*>(dst.data);
+    if (f16)
+        merge_split_rows_kernel<true><<<(unsigned)Y, kPermThreads, (size_t)smem, s>>>(
+            S, lds, Sd, ldsd, xrank, X, pattern_b, d, dst.inv_scale, dst.kp, dst.parts, rowperm);
+    else
+        merge_split_rows_kernel<false><<<(unsigned)Y, kPermThreads, (size_t)smem, s>>>(
+            S, lds, Sd, ldsd, xrank, X, pattern_b, d, dst.inv_scale, dst.kp, dst.parts, rowperm);
+    GVT_LAUNCH_CHECK("merge and split of S");
     return GVT_OK;
 }
 

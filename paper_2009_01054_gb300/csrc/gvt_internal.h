@@ -383,6 +383,12 @@ gvt_status dense_densify_tiles(const S1Source& src, const int32_t* xperm, const 
 // S[y, x] += Sd[y, xrank[x]]
 gvt_status dense_merge_cols(float* S, int64_t lds, const float* Sd, int64_t ldsd, const int32_t* xrank, int64_t Y,
                             int64_t X, cudaStream_t s);
+// The merge followed by dense_split_rows of S (rows rowperm[r], all X columns) in one pass: S is
+// merged in place and split into dst.  Only for rows that fit (dense_merge_split_fits).
+bool dense_merge_split_fits(int64_t X);
+gvt_status dense_merge_split(float* S, int64_t lds, const float* Sd, int64_t ldsd, const int32_t* xrank, int64_t Y,
+                             int64_t X, bool f16, int pattern_b, const DenseOperand& dst, cudaStream_t s,
+                             const int32_t* rowperm);
 // W^T (X rows, [hi|lo|hi]) from the sources of a stage-1 group (keys[si][j] = column x of entry j)
 gvt_status dense_split_w(const S1Sources& srcs, const int32_t* const keys[kMaxSources], int64_t n, const float* v,
                          int64_t X, bool f16, const DenseOperand& dst, float* wide_scratch, cudaStream_t s);

@@ -387,6 +387,20 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
         return GVT_OK;
     };
     T* S = reinterpret_cast<T*>(base + off_S);
+    // S += S' of a per-tile stage 1 is left to the first reader of S: the per-tile stage 2 merges it
+    // in the same pass that splits S, any other reader has it merged first
+    struct PendingMerge {
+        const float* Sd = nullptr;
+        const int32_t* xrank = nullptr;
+        int64_t Y = 0, X = 0, lds = 0;
+    } pend;
+    auto flush_merge = [&]() -> gvt_status {
+        if (!pend.Sd) return GVT_OK;
+        GVT_CHECK(dense_merge_cols(reinterpret_cast<float*>(S), pend.lds, pend.Sd, pend.lds, pend.xrank, pend.Y,
+                                   pend.X, s));
+        pend.Sd = nullptr;
+        return GVT_OK;
+    };
     for (size_t gi = 0; gi < C.two.size(); ++gi) {
         if (done[gi]) continue;
         const TwoSided& g = C.two[gi];
@@ -450,8 +464,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                                      h->tc_pairs, h->tc_stall_cycles, &sp));
             }
             GVT_CHECK(aux_join(h, s));
-            GVT_CHECK(dense_merge_cols(reinterpret_cast<float*>(S), lds, reinterpret_cast<const float*>(Sd), lds,
-                                       h1->xrank, Y, X, s));
+            pend = PendingMerge{reinterpret_cast<const float*>(Sd), h1->xrank, Y, X, lds};
         } else if (tc1[gi]) {
             const int ib = g.recipe.begin()->first.second;
             const gvt_matrix* Bm = mats[base_matrix(g.fb, homo)];
@@ -500,6 +513,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 out_range(plan, g2.ob) != Y)
                 continue;
             done[gj] = true;
+            if (!(tc2[gj] == 2 && g2.fa != GVT_FACTOR_IDENTITY)) GVT_CHECK(flush_merge());
             const Order& oo = plan->out_by[g2.oa];
             S2Outputs outs{oo.key, (g2.oa == g2.ob) ? oo.key : oo.other, oo.perm, n_out};
             if (g2.fa == GVT_FACTOR_IDENTITY) {
@@ -518,15 +532,25 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 const gvt_matrix* Fa = mats[base_matrix(g2.fa, homo)];
                 DenseOperand a2, s2 = dense_operand_at(base + off_s2, Y, X, parts);
                 // single pass: the remainder's dots read the GEMM's own FP16 operands (A' and S', rows
-                // relabelled and scaled by powers of two), so the splits come first
+                // relabelled and scaled by powers of two), so the splits come first, S merged in the
+                // same pass that splits it; otherwise the remainder reads S in FP32 once it is merged,
+                // beside the splits and the GEMM
                 const bool rem16 = h2->eb == 2 && h2->n_r > 0;
                 auto split_operands = [&]() -> gvt_status {
                     GVT_CHECK(factor_operand(Fa, sq_mode(g2.fa), mb, X, a2, h2->aperm, nullptr));
-                    GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s,
-                                               h2->sperm, nullptr));
+                    if (pend.Sd && dense_merge_split_fits(X)) {
+                        GVT_CHECK(dense_merge_split(reinterpret_cast<float*>(S), lds, pend.Sd, pend.lds, pend.xrank,
+                                                    Y, X, f16, 1, s2, s, h2->sperm));
+                        pend.Sd = nullptr;
+                    } else {
+                        GVT_CHECK(flush_merge());
+                        GVT_CHECK(dense_split_rows(reinterpret_cast<const float*>(S), lds, Y, X, 0, f16, 1, s2, s,
+                                                   h2->sperm, nullptr));
+                    }
                     return GVT_OK;
                 };
                 if (rem16) GVT_CHECK(split_operands());
+                else GVT_CHECK(flush_merge());
                 // the remainder's sampled dots (HBM-bound) on the auxiliary stream beside the tile-list
                 // GEMM; they add into disjoint outputs of u
                 cudaStream_t sa = nullptr;
@@ -612,6 +636,7 @@ gvt_status pairwise_apply(gvt_plan* plan, const gvt_desc* desc, const gvt_matrix
                 GVT_CHECK(stage2_gather<T>(A.A, A.lda, sq_mode(g2.fa), S, lds, X, outs, 1.0, u, s));
             }
         }
+        GVT_CHECK(flush_merge());
     }
 
     // ---- one-sided groups; those on the same factor (data and square mode) share one pass over it
