@@ -529,8 +529,12 @@ def bench_products(args, gvt, torch, dev, name, p, K, W, ws, dist, local, flush,
     gvt.gvt_stats_enable(H.h, False)
     pts = pair_terms_per_step(p.n, kinds)
     step_ms_max, value = job_rate(step_ms, pts, ws, dist, dev)
-    # committed DRAM traffic is recorded per workload, and per engine other than the default
-    roof, tpipe = roofline(stats, K, peaks, peak_src, 4, name if args.engine == "auto" else name + "_" + args.engine)
+    # committed DRAM traffic is recorded per workload at its full size, and per engine other than the
+    # default (a reduced instance has no record)
+    tkey = name if args.engine == "auto" else name + "_" + args.engine
+    if name == "c5" and (p.m != 20000 or p.n != 10_000_000):
+        tkey += "_reduced"
+    roof, tpipe = roofline(stats, K, peaks, peak_src, 4, tkey)
     wl = WORKLOADS[name]
     if name == "c5" and (p.m != 20000 or p.n != 10_000_000):
         wl += " -- reduced instance of the same recipe: m=q=%d, n=%d" % (p.m, p.n)

@@ -2,11 +2,10 @@
 // kernels around them.
 //
 // Stage 1 (sparse, SIMT): S = B W, W holding v_j at (bcol_j, x_j), computed
-// column tile by column tile over input pairs sorted by x (segments).  A warp
-// reads 32 entries of a segment at a time and broadcasts each (row, weight)
-// with warp shuffles; every thread owns VEC consecutive output rows and TX
-// columns in registers and streams the needed row of B^T with one 16-byte
-// load per entry.
+// column tile by column tile over input pairs sorted by x (segments).  A block
+// stages the entries of its columns in shared memory as (row offset, weight)
+// records; every thread owns a few output rows of each of those columns in
+// registers and streams its part of the needed row of B^T with 16-byte loads.
 //
 // Stage 2 (sampled gather-dot): u_i = <A[arow_i, :], S[srow_i, :]>, one warp
 // per output pair, outputs sorted by arow so that consecutive warps share the
@@ -69,8 +68,12 @@ unsigned grid1d(int64_t n, int threads, int64_t cap = 152 * 32)
 }
 
 // ------------------------------------------------------------------ stage 1
-// Tile: blockDim = NT threads, each owning RPT consecutive rows y (RPT/VEC
-// 16-byte loads per entry), and kS1Cols consecutive columns x of S.  The
+// Tile: blockDim = NT threads, each owning RPT rows y (RPT/VEC 16-byte loads per
+// entry), and kS1Cols consecutive columns x of S.  A warp's rows are 32 * RPT
+// consecutive ones; its q-th load covers VEC rows per lane, lanes side by side,
+// so that one load instruction of the warp reads 512 contiguous bytes (with each
+// thread's RPT rows consecutive, a warp instruction spread over 1 KB in half
+// sectors and the L1 data pipe bound the kernel).  The
 // entries of the tile's columns are contiguous in every sorted source; they
 // are staged in shared memory as (row offset of B^T, weight) records, which
 // every warp reads with one broadcast load per entry.
@@ -100,9 +103,12 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
     __shared__ S1Entry<T> ent[kS1Chunk];
     __shared__ int32_t sseg[kMaxSources][kS1Cols + 1];
 
-    const int64_t y0 = (int64_t)blockIdx.y * (NT * RPT) + (int64_t)threadIdx.x * RPT;
+    // rows of this thread: acc index k <-> row y0 + (k / VEC) * 32 * VEC + k % VEC
+    constexpr int QS = 32 * VEC;   // distance between a thread's successive loads, in rows
+    const int64_t y0 = (int64_t)blockIdx.y * (NT * RPT) + (int64_t)(threadIdx.x >> 5) * (32 * RPT) +
+                       (int64_t)(threadIdx.x & 31) * VEC;
     const int64_t x0 = (int64_t)blockIdx.x * kS1Cols;
-    const bool vec_rows = (y0 + RPT <= Y) && (ldb % VEC == 0) && aligned16(Bt);
+    const bool vec_rows = (y0 + (NV - 1) * QS + VEC <= Y) && (ldb % VEC == 0) && aligned16(Bt);
     const T* __restrict__ by = Bt + y0;
 
     if (threadIdx.x < kMaxSources * (kS1Cols + 1)) {
@@ -152,10 +158,13 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
                         if (vec_rows) {
 #pragma unroll
                             for (int q = 0; q < NV; ++q)
-                                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(row) + q), &b[e][q * VEC]);
+                                Vec<T>::split(__ldg(reinterpret_cast<const VT*>(row + q * QS)), &b[e][q * VEC]);
                         } else {
 #pragma unroll
-                            for (int q = 0; q < RPT; ++q) b[e][q] = (y0 + q < Y) ? __ldg(row + q) : T(0);
+                            for (int q = 0; q < RPT; ++q) {
+                                const int64_t dy = (q / VEC) * QS + q % VEC;
+                                b[e][q] = (y0 + dy < Y) ? __ldg(row + dy) : T(0);
+                            }
                         }
                     }
 #pragma unroll
@@ -173,10 +182,13 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
                     if (vec_rows) {
 #pragma unroll
                         for (int q = 0; q < NV; ++q)
-                            Vec<T>::split(__ldg(reinterpret_cast<const VT*>(row) + q), &b[q * VEC]);
+                            Vec<T>::split(__ldg(reinterpret_cast<const VT*>(row + q * QS)), &b[q * VEC]);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < RPT; ++q) b[q] = (y0 + q < Y) ? __ldg(row + q) : T(0);
+                        for (int q = 0; q < RPT; ++q) {
+                            const int64_t dy = (q / VEC) * QS + q % VEC;
+                            b[q] = (y0 + dy < Y) ? __ldg(row + dy) : T(0);
+                        }
                     }
 #pragma unroll
                     for (int q = 0; q < RPT; ++q) {
@@ -191,7 +203,7 @@ stage1_sparse_kernel(const T* __restrict__ Bt, int64_t ldb, S1Sources srcs,
     const bool vec_cols = (x0 + kS1Cols <= X) && (lds % VEC == 0) && aligned16(S) && (x0 % VEC == 0);
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-        const int64_t y = y0 + q;
+        const int64_t y = y0 + (q / VEC) * QS + q % VEC;   // increasing in q
         if (y >= Y) break;
         T* srow = S + y * lds + x0;
         if (vec_cols) {
