@@ -249,13 +249,15 @@ constexpr int kS2Group = 4;      // outputs per warp, processed together
 // share their A row -- the common case, every A row serves ~n/m outputs --
 // each chunk of the A row is loaded once for the whole group, so a group
 // costs 1 + kS2Group row loads per chunk instead of 2 * kS2Group.
-// Three blocks per SM (at most 80 registers a thread, a few spilled): the kernel waits on its row
-// loads, and 24 warps per SM hide that latency better than the 16 that 114 registers allowed
-// (measured: 9.05 -> 7.67 ms for the kernel-filling remainder, 11.1 -> 9.5 ms at 0.2 % density).
+// The kernel waits on its row loads, so what counts is the loads in flight per SM: the chunk loop
+// is unrolled by two (two chunks' loads issued together) at two blocks per SM (128 registers),
+// which measured 5.72 ms for the kernel-filling remainder against 6.56 ms for one chunk at a time
+// at three blocks per SM (80 registers, a few spilled), 6.22 ms unrolled at three blocks, and
+// 7.67 ms for one chunk at two blocks.
 // FP16 storage (TB = __half): A and S rows scaled by powers of two, whose inverses (ascale,
 // sscale, one per row) multiply each finished dot.
 template <class T, class TB, int MODE>
-__global__ void __launch_bounds__(kS2Threads, 3)
+__global__ void __launch_bounds__(kS2Threads, 2)
 stage2_gather_kernel(const TB* __restrict__ A, int64_t lda, const float* __restrict__ ascale,
                     const TB* __restrict__ S, int64_t lds, const float* __restrict__ sscale,
                     int64_t X, S2Outputs outs, T coef, T* __restrict__ u)
@@ -292,6 +294,7 @@ stage2_gather_kernel(const TB* __restrict__ A, int64_t lda, const float* __restr
 #pragma unroll
         for (int g = 0; g < G; ++g) acc[g] = T(0);
         if (same) {
+#pragma unroll 2
             for (int64_t x = (int64_t)lane * VEC; x < xv; x += 32 * VEC) {
                 T a[VEC], sv[G][VEC];
                 Ld<TB, T>::split(__ldg(reinterpret_cast<const VT*>(arow[0] + x)), a);
@@ -305,6 +308,7 @@ stage2_gather_kernel(const TB* __restrict__ A, int64_t lda, const float* __restr
                 }
             }
         } else {
+#pragma unroll 2
             for (int64_t x = (int64_t)lane * VEC; x < xv; x += 32 * VEC) {
                 T a[G][VEC], sv[G][VEC];
 #pragma unroll
